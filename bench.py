@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark of one dual-gradient pass (the hot path) on the c2 workload.
+
+A step is one full dual evaluation through the C ABI (destination prologue,
+the edge pass, destination epilogue with the FP64 scalars) on the c2 matching
+LP: 1M sources x 10k destinations, Poisson(50) degrees clipped to [1, 500],
+Zipf(1.1) destinations, about 50M edges, seeded synthetic data.  The metric is
+edges per second per pass; the edge arrays (600 MB) exceed the 129 MB L2, so
+no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (the method is
+run on one GPU; there is no sharded path), value = edges of all ranks / max
+time.  ``--impl reference`` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges/s per dual-grad pass"
+UNIT = "edges/s"
+GAMMA = 1e-3
+LAM_SEED = 7
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2"])
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of c2's sources (debug)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(scale=1.0):
+    import synth
+
+    inst = synth.config("c2", scale=scale)
+    return inst
+
+
+def lam_for(inst):
+    return np.random.default_rng(LAM_SEED).uniform(0.0, 1.0, inst.J).astype(np.float32)
+
+
+def config_dict(inst, scale):
+    return {
+        "workload": ("c2: matching LP, 1M sources x 10k destinations, Poisson(50) degrees in "
+                     "[1,500], Zipf(1.1) destinations, c=-LogNormal(0,1), a~U(0.5,1.5), "
+                     "b=0.2*sum(a)" if scale == 1.0 else f"c2 at {scale:g} of the sources"),
+        "I": inst.I, "J": inst.J, "E": inst.E, "gamma": GAMMA,
+        "lambda": f"U(0,1) seed {LAM_SEED}",
+        "edge_bytes": 12 * inst.E,
+        "l2": "inputs larger than L2 (edges 12 B/edge > 129 MB); no flush",
+        "parallelism": "replicas" ,
+    }
+
+
+def algorithmic_bytes(inst):
+    # what one pass must move: 12 B/edge (dst, c, a), 8 B per
+    # source offset, and per destination: mu read, y / y_err accumulate
+    return 12 * inst.E + 8 * (inst.I + 1) + 12 * inst.J
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        load = [r for r in self.rows if (num(r[3]) or 0) > 0] or self.rows
+        sm = [num(r[0]) for r in load if num(r[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in load for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(load[0][1]), "reasons": reasons,
+                "samples": len(self.rows), "samples_under_load": len(load)}
+
+
+def cpu_baseline(inst, seconds):
+    """The FP64 oracle as it stands, all host cores, on a bounded source sample."""
+    import oracle
+
+    n = max(1, min(inst.I, int(inst.I * 0.05)))
+    sub = inst.subset_sources(np.arange(n))
+    cores = oracle.set_threads(0)
+    P = oracle.Problem(sub)
+    lam = lam_for(inst).astype(np.float64)
+    P.eval(lam, GAMMA)  # warm
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        P.eval(lam, GAMMA)
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": sub.E * reps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of {inst.I} sources ({sub.E} edges), {reps} FP64 evaluations "
+                      f"in {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    inst = workload(args.scale)
+    import oracle
+
+    n = max(1, min(inst.I, int(inst.I * 0.02)))
+    sub = inst.subset_sources(np.arange(n))
+    cores = oracle.set_threads(0)
+    P = oracle.Problem(sub)
+    lam = lam_for(inst).astype(np.float64)
+    for _ in range(args.warmup):
+        P.eval(lam, GAMMA)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.eval(lam, GAMMA)
+    dt = time.perf_counter() - t0
+    value = sub.E * args.steps / dt
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference", "config": config_dict(inst, args.scale),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"each step: first {n} sources of c2 ({sub.E} edges)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def time_to_gap(d, torch):
+    """dualip_solve to the 1e-4 relative gap on c2 with the paper's greedy-load budgets
+    (the sum-fraction budgets of c2 never bind, so lambda* = 0 there)."""
+    import synth
+
+    inst = synth.greedy_budgets(synth.config("c2"))
+    P = d.Problem.from_instance(inst)
+    P.solve(max_iters=20)  # warm: graph capture, row scale
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, res = P.solve()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    P.close()
+    return {"workload": "c2 graph and values with greedy-load budgets (App. B rule)",
+            "seconds": dt, "iters": res["iters"], "converged": res["converged"],
+            "gap_rel": res["gap_rel"], "infeas_rel": res["infeas_rel"],
+            "dual_obj": res["dual_obj"]}
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2603_04621_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    import paper_2603_04621_gb300 as d
+
+    inst = workload(args.scale)
+    P = d.Problem.from_instance(inst)
+    lam_h = lam_for(inst)
+    lam = torch.from_numpy(lam_h).cuda()
+    grad = torch.empty(inst.J, dtype=torch.float32, device="cuda")
+    out_dev = torch.empty(8, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+
+    def step():
+        d.dualip_dual_grad_async(P.h, lam.data_ptr(), GAMMA, grad.data_ptr(), out_dev.data_ptr(),
+                                 sp)
+
+    with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
+        # keep the GPU busy ~1 s before timing so clocks are sampled under load
+        torch.cuda.synchronize()
+        t_end = time.perf_counter() + 1.0
+        while time.perf_counter() < t_end:
+            for _ in range(50):
+                step()
+            torch.cuda.synchronize()
+        d.dualip_check_device_status(P.h, sp)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        d.dualip_profile_enable(P.h, args.steps)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = d.dualip_profile_collect(P.h)
+        d.dualip_check_device_status(P.h, sp)
+        if ws > 1:
+            t = torch.tensor([ms], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        # end to end through the public API with host buffers (pinned)
+        lam_pin = torch.from_numpy(lam_h).pin_memory()
+        grad_pin = torch.empty(inst.J, dtype=torch.float32).pin_memory()
+        for _ in range(3):
+            d.dualip_dual_grad_host(P.h, lam_pin.data_ptr(), GAMMA, grad_pin.data_ptr(), sp)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            d.dualip_dual_grad_host(P.h, lam_pin.data_ptr(), GAMMA, grad_pin.data_ptr(), sp)
+        e2e_s = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+    ttg = None
+    if not args.no_solve and rank == 0 and args.scale == 1.0:
+        ttg = time_to_gap(d, torch)
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+        return 0
+
+    E = inst.E
+    value = E * args.steps * ws / (ms / 1e3)
+    pass_ms = prof["ms_pass"] / max(prof["count"], 1)
+    alg = algorithmic_bytes(inst)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_note = "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+    if not peak:
+        peak, peak_note = 6800.0, "fallback 6.8 TB/s"
+    achieved = alg / (pass_ms / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(inst, args.scale),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "dualgrad_pass_kernel",
+                     "kernel_ms": pass_ms, "algorithmic_bytes": alg, "peak_source": peak_note},
+        "kernel_ms": {"prologue": prof["ms_prologue"] / max(prof["count"], 1), "pass": pass_ms,
+                      "epilogue": prof["ms_epilogue"] / max(prof["count"], 1)},
+        "hbm_roofline_pct": 100.0 * achieved / peak,
+        "e2e": {"value": E * args.steps * ws / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 4 * inst.J, "d2h_bytes_per_step": 4 * inst.J + 40,
+                "api": "dualip_dual_grad_host (lambda in, grad + FP64 scalars out, pinned)"},
+        "clocks": clk.summary(),
+        "gpu_launches": 3 * args.steps,
+        "time_to_gap": ttg,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.barrier()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

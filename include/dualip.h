@@ -1,0 +1,217 @@
+/*
+ * dualip.h -- C ABI of a GB300-native (sm_103a) dual-gradient engine for the
+ * ridge-regularised dual of matching linear programs (DuaLip-GPU technical
+ * report, arXiv 2603.04621).
+ *
+ * The problem (Section 3.1, Eq. 1, with the matching structure of Section 3.2):
+ *     min  c^T x   s.t.  A x <= b,  x_i in {x_i >= 0, sum_j x_ij <= 1} for every source i
+ * where x has one variable per edge (i, j) and (A x)_j = sum_i a_ij x_ij
+ * (Eq. 3, Definition 1 with one constraint family).  The library evaluates the
+ * smoothed dual of Eq. 2,
+ *     g(lambda) = min_{x in C} c^T x + (gamma/2) sum_e w_e x_e^2 + lambda^T (A x - b),
+ * its Danskin gradient grad g(lambda) = A x*(lambda) - b (Section 3.1) with
+ * x*(lambda) = Pi_C(-(A^T lambda + c) / gamma) computed per source, and runs
+ * the dual ascent of Section 5 / Appendix B.  w_e = 1, or w_e = a_e^2 (1 where
+ * a_e = 0) when primal scaling (Section 5.1, view (i) with v = |a|) is on.
+ *
+ * Conventions shared by every call:
+ *  - Every entry point returns a dualip_status; nothing throws, aborts or traps.
+ *    On failure dualip_last_error() returns a message for the calling thread.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work is ordered on that stream.
+ *  - Pointers documented as "device" must be device (or managed) memory of the
+ *    current CUDA device; "host" pointers are ordinary host memory (pinned
+ *    host memory makes the copies asynchronous).
+ *  - lambda and grad are always in the caller's destination numbering and
+ *    original (unnormalised) coordinates.
+ *  - A problem handle is not thread safe: calls on one handle must not overlap.
+ */
+#ifndef DUALIP_H
+#define DUALIP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DUALIP_OK = 0,
+  DUALIP_EINVAL = 1,        /* invalid argument or input data; nothing was changed */
+  DUALIP_ENOMEM = 2,        /* a device or host allocation failed */
+  DUALIP_ECUDA = 3,         /* a CUDA runtime call failed */
+  DUALIP_ETIMEOUT = 4,      /* a bounded device-side wait gave up; results are invalid */
+  DUALIP_EBUSY = 5,         /* the resource is in use (e.g. serving slots full) */
+  DUALIP_ENOTCONVERGED = 6, /* dualip_solve stopped at max_iters before the tolerances */
+  DUALIP_EDEVICE = 7        /* a device-side consistency check failed */
+} dualip_status;
+
+typedef enum { DUALIP_EDGE_F32 = 0, DUALIP_EDGE_BF16 = 1 } dualip_edge_dtype;
+
+/*
+ * Source-major edge list (the paper's CSC tensor T of Section 6, "Sparse
+ * tensor computation": one column per source i holding diag(D_i), so the
+ * edges of a source are contiguous).
+ *   num_sources  I >= 0
+ *   num_edges    E >= 0; must equal src_offsets[I]
+ *   num_dests    J >= 1
+ *   src_offsets  [I+1] int64, src_offsets[0] = 0, nondecreasing; the edges of
+ *                source i are src_offsets[i] .. src_offsets[i+1]-1
+ *   dst          [E] int32, 0 <= dst[e] < J (repeated (i, j) pairs are separate variables)
+ *   c            [E] float, cost of the edge (minimisation sign), finite
+ *   a            [E] float, coefficient a_ij of the edge in row j of A, finite
+ *   b            [J] float, budgets, finite
+ *   inputs_on_device  0: the five arrays are host pointers; 1: device pointers
+ *   storage      DUALIP_EDGE_F32 keeps c and a in FP32; DUALIP_EDGE_BF16 stores
+ *                them as bfloat16 (round to nearest even) and computes in FP32
+ *   primal_scaling  0: w_e = 1; 1: w_e = a_e^2 (1 where a_e = 0)
+ * dualip_create copies everything into library-owned device memory; the
+ * caller keeps ownership of its arrays and may free them on return.
+ */
+typedef struct {
+  int64_t num_sources;
+  int64_t num_edges;
+  int32_t num_dests;
+  const int64_t* src_offsets;
+  const int32_t* dst;
+  const float* c;
+  const float* a;
+  const float* b;
+  int32_t inputs_on_device;
+  int32_t storage;
+  int32_t primal_scaling;
+} dualip_problem_desc;
+
+/* Scalars of one dual evaluation, computed on the GPU in FP64 (Section 6: the
+ * "local objective value and local regularization penalty"; Appendix A for
+ * the infeasibility). */
+typedef struct {
+  double dual_obj;        /* g(lambda) of Eq. 2 */
+  double primal_obj;      /* c^T x*(lambda) */
+  double reg;             /* (gamma/2) sum_e w_e x_e^2 */
+  double infeas_l2;       /* ||(A x* - b)_+||_2 */
+  double lambda_dot_grad; /* lambda^T (A x* - b) */
+} dualip_eval;
+
+typedef struct dualip_problem dualip_problem;
+
+/* Build a problem handle from a desc (validated: offsets, destination range,
+ * finiteness).  Work is queued on `stream` and finished before return.
+ * Errors: DUALIP_EINVAL (bad desc or data), DUALIP_ENOMEM, DUALIP_ECUDA.
+ * On success *out owns device memory of about E * (4 + bytes of c and a)
+ * + 8 I + 40 J bytes; free it with dualip_destroy. */
+dualip_status dualip_create(const dualip_problem_desc* desc, void* stream, dualip_problem** out);
+
+/* Release a handle (NULL is ignored).  Synchronises the handle's last stream. */
+void dualip_destroy(dualip_problem* p);
+
+/*
+ * One dual-gradient evaluation (Section 3.1, Eq. 2 and Danskin's theorem):
+ *   lambda  [J] float, device: dual point (any sign is accepted)
+ *   gamma   ridge parameter, > 0
+ *   grad    [J] float, device, written: A x*(lambda) - b
+ *   out     host, may be NULL: the scalars of this evaluation; when non-NULL
+ *           the call waits for `stream` to finish before returning
+ * Errors: DUALIP_EINVAL (NULL handle/pointers, gamma <= 0 or not finite),
+ * DUALIP_ECUDA, DUALIP_ETIMEOUT / DUALIP_EDEVICE (device-side check; the
+ * outputs are then invalid).
+ */
+dualip_status dualip_dual_grad(dualip_problem* p, const float* lambda, double gamma, float* grad,
+                               dualip_eval* out, void* stream);
+
+/* Same as dualip_dual_grad, but never synchronises: the scalars are written
+ * to `out_dev` (device, 5 doubles in dualip_eval order) and device-side error
+ * reporting is deferred to dualip_check_device_status.  Safe to capture in a
+ * CUDA graph. */
+dualip_status dualip_dual_grad_async(dualip_problem* p, const float* lambda, double gamma,
+                                     float* grad, double* out_dev, void* stream);
+
+/* dualip_dual_grad with host buffers: copies lambda in and grad and the
+ * scalars out inside the call (pinned host memory makes the copies fastest).
+ * Waits for `stream`. */
+dualip_status dualip_dual_grad_host(dualip_problem* p, const float* lambda_host, double gamma,
+                                    float* grad_host, dualip_eval* out, void* stream);
+
+/* The primal minimiser x*(lambda) of Section 3.1 for every edge, in edge order:
+ *   x  [E] float, device, written.  Other arguments as dualip_dual_grad. */
+dualip_status dualip_get_primal(dualip_problem* p, const float* lambda, double gamma, float* x,
+                                void* stream);
+
+/* Reads (and clears) the device-side error word of the handle; waits for
+ * `stream`.  Returns DUALIP_OK, DUALIP_ETIMEOUT or DUALIP_EDEVICE. */
+dualip_status dualip_check_device_status(dualip_problem* p, void* stream);
+
+/* Kernel timing for measurement.  After dualip_profile_enable, each of the
+ * next max_evals evaluations on the handle records CUDA events on its stream
+ * around its three kernels (destination prologue, edge pass, destination
+ * epilogue).  dualip_profile_collect waits for those events, returns the
+ * summed durations in milliseconds and the number of evaluations recorded,
+ * and turns recording off.  Errors: DUALIP_EINVAL, DUALIP_ENOMEM, DUALIP_ECUDA. */
+dualip_status dualip_profile_enable(dualip_problem* p, int32_t max_evals);
+dualip_status dualip_profile_collect(dualip_problem* p, double* ms_prologue, double* ms_pass,
+                                     double* ms_epilogue, int32_t* count);
+
+/* Sizes of a handle: I, J, E and the number of edge tiles of the pass. */
+dualip_status dualip_get_info(const dualip_problem* p, int64_t* num_sources, int32_t* num_dests,
+                              int64_t* num_edges, int64_t* num_tiles);
+
+/*
+ * Dual ascent (Section 5, Appendix B): accelerated projected ascent on the
+ * Jacobi row-normalised dual (Section 5.1) with gamma continuation
+ * gamma_k = max(gamma_final, gamma0 * 2^-floor(k / halve_every)) and the step
+ * cap scaled in proportion to gamma (Section 5.1, "Regularization decay").
+ * Step: eta_k = min(max_step * gamma_k / gamma0, secant estimate
+ * ||y_k - y_{k-1}|| / ||G_k - G_{k-1}||), init_step right after a (re)start;
+ * momentum restarts when gamma changes (restart_on_gamma_change).
+ * Stopping, tested every check_every iterations at gamma_final:
+ *   |lambda^T (A x - b)| / max(1, |p|, |g|) <= tol_gap  (p = c^T x + ridge term)
+ *   ||(A x - b)_+||_2 / max(1, ||b||_2)     <= tol_infeas.
+ */
+typedef struct {
+  double gamma0;            /* > 0 */
+  double gamma_final;       /* > 0, <= gamma0 */
+  int32_t halve_every;      /* iterations per halving of gamma; <= 0 keeps gamma0 */
+  double max_step;          /* step cap at gamma0 (scaled by gamma_k / gamma0) */
+  double init_step;         /* first step after a (re)start */
+  int32_t max_iters;        /* >= 1 */
+  double tol_gap;
+  double tol_infeas;
+  int32_t check_every;      /* >= 1; scalars are read back every check_every iterations */
+  int32_t row_normalize;    /* 1: Jacobi row normalisation (default), 0: off */
+  int32_t restart_on_gamma_change; /* 1 (default) */
+  int32_t stop_on_tol;      /* 1: stop at the tolerances; 0: run exactly max_iters */
+  int32_t use_graph;        /* 1: capture check_every iterations in one CUDA graph */
+} dualip_solve_opts;
+
+typedef struct {
+  int32_t iters;      /* evaluations performed */
+  int32_t converged;  /* 1 if both tolerances held at a check */
+  dualip_eval last;   /* scalars at the returned lambda */
+  double gap_rel;
+  double infeas_rel;
+  double gamma;       /* gamma of the last evaluation */
+} dualip_solve_result;
+
+/* Fill opts with the defaults: gamma0 0.1, gamma_final 1e-3, halve_every 25,
+ * max_step 10, init_step 1e-5, max_iters 5000, tolerances 1e-4,
+ * check_every 10, row_normalize 1, restart 1, stop_on_tol 1, use_graph 1. */
+void dualip_solve_opts_default(dualip_solve_opts* opts);
+
+/*
+ * Run the ascent from lambda_inout (device, [J], clamped at 0 on entry) and
+ * write the last evaluated dual point back into it.  `trace` (device, may be
+ * NULL) receives 8 doubles per iteration: gamma, g, p, infeas, gap_rel,
+ * infeas_rel, step, lambda^T grad.  Returns DUALIP_OK when converged,
+ * DUALIP_ENOTCONVERGED when max_iters ran out (result filled in both cases).
+ */
+dualip_status dualip_solve(dualip_problem* p, const dualip_solve_opts* opts, float* lambda_inout,
+                           dualip_solve_result* result, double* trace, void* stream);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* dualip_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DUALIP_H */

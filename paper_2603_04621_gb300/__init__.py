@@ -1,0 +1,306 @@
+"""Python binding of the dualip C ABI (include/dualip.h).
+
+Argument marshalling only: every step of the dual evaluation and of the solve
+runs in the CUDA kernels of ``libdualip.so`` (built in-tree by
+:func:`paper_2603_04621_gb300.build.build`).  PyTorch provides device memory
+and streams.  There is no CPU fallback: importing works without the library,
+but every call raises if ``libdualip.so`` is missing or no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdualip.so")
+_lib = None
+
+DUALIP_OK, DUALIP_EINVAL, DUALIP_ENOMEM, DUALIP_ECUDA = 0, 1, 2, 3
+DUALIP_ETIMEOUT, DUALIP_EBUSY, DUALIP_ENOTCONVERGED, DUALIP_EDEVICE = 4, 5, 6, 7
+DUALIP_EDGE_F32, DUALIP_EDGE_BF16 = 0, 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY",
+                6: "ENOTCONVERGED", 7: "EDEVICE"}
+
+# every entry point declared in include/dualip.h
+EXPORTS = [
+    "dualip_create", "dualip_destroy", "dualip_dual_grad", "dualip_dual_grad_async",
+    "dualip_dual_grad_host", "dualip_get_primal", "dualip_check_device_status",
+    "dualip_get_info", "dualip_solve_opts_default", "dualip_solve", "dualip_last_error",
+    "dualip_profile_enable", "dualip_profile_collect",
+]
+
+
+class DualipError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dualip {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("num_sources", ctypes.c_int64), ("num_edges", ctypes.c_int64),
+                ("num_dests", ctypes.c_int32), ("src_offsets", ctypes.c_void_p),
+                ("dst", ctypes.c_void_p), ("c", ctypes.c_void_p), ("a", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("inputs_on_device", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("primal_scaling", ctypes.c_int32)]
+
+
+class Eval(ctypes.Structure):
+    _fields_ = [("dual_obj", ctypes.c_double), ("primal_obj", ctypes.c_double),
+                ("reg", ctypes.c_double), ("infeas_l2", ctypes.c_double),
+                ("lambda_dot_grad", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("gamma0", ctypes.c_double), ("gamma_final", ctypes.c_double),
+                ("halve_every", ctypes.c_int32), ("max_step", ctypes.c_double),
+                ("init_step", ctypes.c_double), ("max_iters", ctypes.c_int32),
+                ("tol_gap", ctypes.c_double), ("tol_infeas", ctypes.c_double),
+                ("check_every", ctypes.c_int32), ("row_normalize", ctypes.c_int32),
+                ("restart_on_gamma_change", ctypes.c_int32), ("stop_on_tol", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
+class SolveResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("last", Eval),
+                ("gap_rel", ctypes.c_double), ("infeas_rel", ctypes.c_double),
+                ("gamma", ctypes.c_double)]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdualip.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2603_04621_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        st = ctypes.c_int
+        L.dualip_create.argtypes = [ctypes.POINTER(ProblemDesc), vp, ctypes.POINTER(vp)]
+        L.dualip_create.restype = st
+        L.dualip_destroy.argtypes = [vp]
+        L.dualip_destroy.restype = None
+        L.dualip_dual_grad.argtypes = [vp, vp, dbl, vp, ctypes.POINTER(Eval), vp]
+        L.dualip_dual_grad.restype = st
+        L.dualip_dual_grad_async.argtypes = [vp, vp, dbl, vp, vp, vp]
+        L.dualip_dual_grad_async.restype = st
+        L.dualip_dual_grad_host.argtypes = [vp, vp, dbl, vp, ctypes.POINTER(Eval), vp]
+        L.dualip_dual_grad_host.restype = st
+        L.dualip_get_primal.argtypes = [vp, vp, dbl, vp, vp]
+        L.dualip_get_primal.restype = st
+        L.dualip_check_device_status.argtypes = [vp, vp]
+        L.dualip_check_device_status.restype = st
+        L.dualip_get_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.dualip_get_info.restype = st
+        L.dualip_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
+        L.dualip_solve_opts_default.restype = None
+        L.dualip_solve.argtypes = [vp, ctypes.POINTER(SolveOpts), vp, ctypes.POINTER(SolveResult),
+                                   vp, vp]
+        L.dualip_solve.restype = st
+        L.dualip_profile_enable.argtypes = [vp, i32]
+        L.dualip_profile_enable.restype = st
+        pd = ctypes.POINTER(dbl)
+        L.dualip_profile_collect.argtypes = [vp, pd, pd, pd, ctypes.POINTER(i32)]
+        L.dualip_profile_collect.restype = st
+        L.dualip_last_error.argtypes = []
+        L.dualip_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, ok=(DUALIP_OK,)) -> int:
+    if status not in ok:
+        raise DualipError(status, lib().dualip_last_error().decode())
+    return status
+
+
+def _stream(stream=None) -> int:
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _ptr(x) -> int:
+    """Address of a contiguous numpy array or torch tensor."""
+    if x is None:
+        return 0
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return int(x.ctypes.data)
+    assert x.is_contiguous()
+    return int(x.data_ptr())
+
+
+# ------------------------------------------------------------ C ABI, 1:1 ----
+def dualip_create(desc: ProblemDesc, stream: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().dualip_create(ctypes.byref(desc), stream, ctypes.byref(h)))
+    return int(h.value)
+
+
+def dualip_destroy(h: int) -> None:
+    if h:
+        lib().dualip_destroy(h)
+
+
+def dualip_dual_grad(h: int, lam_ptr: int, gamma: float, grad_ptr: int, stream: int,
+                     want_eval: bool = True):
+    ev = Eval()
+    _check(lib().dualip_dual_grad(h, lam_ptr, gamma, grad_ptr,
+                                  ctypes.byref(ev) if want_eval else None, stream))
+    return ev if want_eval else None
+
+
+def dualip_dual_grad_async(h: int, lam_ptr: int, gamma: float, grad_ptr: int, out_ptr: int,
+                           stream: int) -> None:
+    _check(lib().dualip_dual_grad_async(h, lam_ptr, gamma, grad_ptr, out_ptr, stream))
+
+
+def dualip_dual_grad_host(h: int, lam_host_ptr: int, gamma: float, grad_host_ptr: int,
+                          stream: int) -> Eval:
+    ev = Eval()
+    _check(lib().dualip_dual_grad_host(h, lam_host_ptr, gamma, grad_host_ptr, ctypes.byref(ev),
+                                       stream))
+    return ev
+
+
+def dualip_get_primal(h: int, lam_ptr: int, gamma: float, x_ptr: int, stream: int) -> None:
+    _check(lib().dualip_get_primal(h, lam_ptr, gamma, x_ptr, stream))
+
+
+def dualip_check_device_status(h: int, stream: int) -> None:
+    _check(lib().dualip_check_device_status(h, stream))
+
+
+def dualip_get_info(h: int) -> dict:
+    I, J, E, T = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().dualip_get_info(h, ctypes.byref(I), ctypes.byref(J), ctypes.byref(E),
+                                 ctypes.byref(T)))
+    return dict(I=I.value, J=J.value, E=E.value, tiles=T.value)
+
+
+def dualip_profile_enable(h: int, max_evals: int) -> None:
+    _check(lib().dualip_profile_enable(h, int(max_evals)))
+
+
+def dualip_profile_collect(h: int) -> dict:
+    a, b, c, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(lib().dualip_profile_collect(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                        ctypes.byref(n)))
+    return dict(ms_prologue=a.value, ms_pass=b.value, ms_epilogue=c.value, count=n.value)
+
+
+def dualip_solve_opts_default() -> SolveOpts:
+    o = SolveOpts()
+    lib().dualip_solve_opts_default(ctypes.byref(o))
+    return o
+
+
+def dualip_solve(h: int, opts: SolveOpts, lam_ptr: int, trace_ptr: int, stream: int):
+    r = SolveResult()
+    st = lib().dualip_solve(h, ctypes.byref(opts), lam_ptr, ctypes.byref(r), trace_ptr, stream)
+    _check(st, ok=(DUALIP_OK, DUALIP_ENOTCONVERGED))
+    return r
+
+
+# ------------------------------------------------- convenience (marshalling) ----
+class Problem:
+    """Owns one dualip handle built from host (numpy) or device (torch) arrays.
+
+    ``off`` int64 [I+1], ``dst`` int32 [E], ``c``/``a`` float32 [E], ``b`` float32 [J].
+    """
+
+    def __init__(self, off, dst, c, a, b, J: int, storage: str = "f32",
+                 primal_scaling: bool = False, stream=None):
+        import torch
+
+        on_dev = isinstance(off, torch.Tensor) and off.is_cuda
+        if not on_dev:
+            off = np.ascontiguousarray(off, dtype=np.int64)
+            dst = np.ascontiguousarray(dst, dtype=np.int32)
+            c = np.ascontiguousarray(c, dtype=np.float32)
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            b = np.ascontiguousarray(b, dtype=np.float32)
+        self._keep = (off, dst, c, a, b)
+        I = int(off.shape[0]) - 1
+        E = int(dst.shape[0])
+        self.I, self.J, self.E = I, int(J), E
+        self.storage = storage
+        d = ProblemDesc(I, E, int(J), _ptr(off), _ptr(dst), _ptr(c), _ptr(a), _ptr(b),
+                        1 if on_dev else 0,
+                        DUALIP_EDGE_BF16 if storage == "bf16" else DUALIP_EDGE_F32,
+                        1 if primal_scaling else 0)
+        self.h = dualip_create(d, _stream(stream))
+        self._keep = None
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @classmethod
+    def from_instance(cls, inst, **kw) -> "Problem":
+        return cls(inst.off, inst.dst, inst.c, inst.a, inst.b, inst.J, **kw)
+
+    def close(self):
+        if getattr(self, "h", 0):
+            dualip_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return dualip_get_info(self.h)
+
+    def _dev_vec(self, v, n):
+        import torch
+
+        if isinstance(v, torch.Tensor):
+            assert v.is_cuda and v.dtype == torch.float32 and v.numel() == n
+            return v.contiguous()
+        return torch.as_tensor(np.asarray(v, dtype=np.float32), device=self.device)
+
+    def dual_grad(self, lam, gamma: float, grad=None, stream=None):
+        """grad = A x*(lam) - b on the device and the FP64 scalars (dict)."""
+        import torch
+
+        lam = self._dev_vec(lam, self.J)
+        if grad is None:
+            grad = torch.empty(self.J, dtype=torch.float32, device=self.device)
+        ev = dualip_dual_grad(self.h, _ptr(lam), float(gamma), _ptr(grad), _stream(stream))
+        return grad, ev.as_dict()
+
+    def primal(self, lam, gamma: float, stream=None):
+        import torch
+
+        lam = self._dev_vec(lam, self.J)
+        x = torch.empty(self.E, dtype=torch.float32, device=self.device)
+        dualip_get_primal(self.h, _ptr(lam), float(gamma), _ptr(x), _stream(stream))
+        return x
+
+    def solve(self, lam0=None, trace: bool = False, stream=None, **opts):
+        """Run dualip_solve; returns (lam tensor, result dict[, trace ndarray])."""
+        import torch
+
+        o = dualip_solve_opts_default()
+        for k, v in opts.items():
+            if k == "restart":
+                k = "restart_on_gamma_change"
+            setattr(o, k, v)
+        lam = (torch.zeros(self.J, dtype=torch.float32, device=self.device) if lam0 is None
+               else self._dev_vec(lam0, self.J).clone())
+        tr = torch.zeros((max(o.max_iters, 1), 8), dtype=torch.float64, device=self.device) \
+            if trace else None
+        r = dualip_solve(self.h, o, _ptr(lam), _ptr(tr), _stream(stream))
+        res = dict(iters=r.iters, converged=bool(r.converged), gap_rel=r.gap_rel,
+                   infeas_rel=r.infeas_rel, gamma=r.gamma, **r.last.as_dict())
+        if trace:
+            return lam, res, tr[: r.iters].cpu().numpy()
+        return lam, res

@@ -1,0 +1,471 @@
+// C ABI of the dual-gradient engine: validation, problem construction and
+// the single-evaluation entry points.  Every device step runs in this
+// library's kernels (pass.cu, solve.cu); nothing falls back to the host.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace dualip {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+dualip_status fail(dualip_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+dualip_status cuda_fail(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  set_error(m);
+  return e == cudaErrorMemoryAllocation ? DUALIP_ENOMEM : DUALIP_ECUDA;
+}
+
+namespace {
+
+template <class T>
+cudaError_t dev_alloc(Problem& P, T** ptr, size_t count) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  P.allocations.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return cudaSuccess;
+}
+
+void free_events(Problem& P) {
+  for (cudaEvent_t ev : P.prof_ev) cudaEventDestroy(ev);
+  P.prof_ev.clear();
+  P.prof_max = P.prof_used = 0;
+}
+
+void free_all(Problem& P) {
+  solve_ctx_free(P);
+  free_events(P);
+  for (void* p : P.allocations) cudaFree(p);
+  P.allocations.clear();
+  if (P.eval_host) cudaFreeHost(P.eval_host);
+  P.eval_host = nullptr;
+}
+
+// Greedy tiling: consecutive whole sources while the edge count stays within
+// kTileEdges and the source count within kTileSources; a source larger than
+// a tile forms a tile of its own (projected from global memory).
+void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
+                 std::vector<int64_t>& tile_e) {
+  const int64_t I = (int64_t)off.size() - 1;
+  tiles.clear();
+  tile_e.clear();
+  int64_t s = 0;
+  while (s < I) {
+    tiles.push_back(s);
+    tile_e.push_back(off[s]);
+    int64_t e = 0, n = 0;
+    if (off[s + 1] - off[s] > kTileEdges) {
+      ++s;
+      continue;
+    }
+    while (s < I && n < kTileSources && e + (off[s + 1] - off[s]) <= kTileEdges) {
+      e += off[s + 1] - off[s];
+      ++n;
+      ++s;
+    }
+  }
+  tiles.push_back(I);
+  tile_e.push_back(off[I]);
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+dualip_status read_status(Problem& P, cudaStream_t s) {
+  DeviceStatus h{};
+  cudaError_t e = cudaMemcpyAsync(&h, P.status, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
+  if (h.err == 0) return DUALIP_OK;
+  DeviceStatus z{};
+  cudaMemcpyAsync(P.status, &z, sizeof(z), cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+  if (h.err & kErrTimeout)
+    return fail(DUALIP_ETIMEOUT, "a bounded device wait gave up (site " + std::to_string(h.where) +
+                                     "); results of the call are invalid");
+  return fail(DUALIP_EDEVICE, "a device-side consistency check failed; results are invalid");
+}
+
+dualip_status check_eval_args(dualip_problem* h, const void* lambda, double gamma, const void* out) {
+  if (!h) return fail(DUALIP_EINVAL, "problem handle is NULL");
+  if (!lambda || !out) return fail(DUALIP_EINVAL, "lambda and output pointers must be non-NULL");
+  if (!std::isfinite(gamma) || !(gamma >= 1e-30) || !(gamma <= 1e30))
+    return fail(DUALIP_EINVAL, "gamma must be finite and in [1e-30, 1e30]");
+  return DUALIP_OK;
+}
+
+}  // namespace
+
+// One evaluation: prologue (renumbered mu), pass, epilogue.
+static cudaError_t enqueue_eval(Problem& P, const float* lambda, double gamma, float* grad,
+                                double* eval_out, float* x_out, cudaStream_t s) {
+  cudaError_t e;
+  cudaEvent_t* ev = nullptr;
+  if (P.prof_used < P.prof_max) ev = &P.prof_ev[4 * (size_t)P.prof_used++];
+  if (ev && (e = cudaEventRecord(ev[0], s))) return e;
+  if ((e = launch_prep(P, lambda, nullptr, s))) return e;
+  if (ev && (e = cudaEventRecord(ev[1], s))) return e;
+  if ((e = launch_pass(P, nullptr, (float)gamma, x_out, s))) return e;
+  if (ev && (e = cudaEventRecord(ev[2], s))) return e;
+  if ((e = launch_epilogue(P, nullptr, grad, nullptr, gamma, eval_out, s))) return e;
+  if (ev && (e = cudaEventRecord(ev[3], s))) return e;
+  return cudaSuccess;
+}
+
+}  // namespace dualip
+
+using namespace dualip;
+
+extern "C" {
+
+const char* dualip_last_error(void) { return g_last_error.c_str(); }
+
+dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_problem** out) {
+  if (!out) return fail(DUALIP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(DUALIP_EINVAL, "desc is NULL");
+  const int64_t I = d->num_sources, E = d->num_edges;
+  const int32_t J = d->num_dests;
+  if (I < 0 || E < 0 || J < 1) return fail(DUALIP_EINVAL, "need I >= 0, E >= 0, J >= 1");
+  if (!d->src_offsets || !d->b || (E > 0 && (!d->dst || !d->c || !d->a)))
+    return fail(DUALIP_EINVAL, "input arrays must be non-NULL");
+  if (d->storage != DUALIP_EDGE_F32 && d->storage != DUALIP_EDGE_BF16)
+    return fail(DUALIP_EINVAL, "unknown edge storage");
+  if (d->primal_scaling != 0 && d->primal_scaling != 1)
+    return fail(DUALIP_EINVAL, "primal_scaling must be 0 or 1");
+  if (d->inputs_on_device != 0 && d->inputs_on_device != 1)
+    return fail(DUALIP_EINVAL, "inputs_on_device must be 0 or 1");
+  cudaStream_t s = as_stream(stream);
+  const cudaMemcpyKind h2d = d->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e;
+
+  // offsets on the host: validation and tiling
+  std::vector<int64_t> off((size_t)I + 1);
+  if (d->inputs_on_device) {
+    e = cudaMemcpyAsync(off.data(), d->src_offsets, sizeof(int64_t) * (I + 1),
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading src_offsets");
+  } else {
+    std::memcpy(off.data(), d->src_offsets, sizeof(int64_t) * (I + 1));
+  }
+  if (off[0] != 0) return fail(DUALIP_EINVAL, "src_offsets[0] must be 0");
+  for (int64_t i = 0; i < I; ++i)
+    if (off[i + 1] < off[i]) return fail(DUALIP_EINVAL, "src_offsets must be nondecreasing");
+  if (off[I] != E) return fail(DUALIP_EINVAL, "src_offsets[I] must equal num_edges");
+
+  auto* h = new (std::nothrow) dualip_problem();
+  if (!h) return fail(DUALIP_ENOMEM, "host allocation failed");
+  Problem& P = h->p;
+  P.I = I;
+  P.E = E;
+  P.J = J;
+  P.storage = d->storage;
+  P.weighted = d->primal_scaling;
+  P.last_stream = s;
+  auto bail = [&](dualip_status st) {
+    cudaStreamSynchronize(s);
+    free_all(P);
+    delete h;
+    return st;
+  };
+  if ((e = cudaGetDevice(&P.device))) return bail(cuda_fail(e, "cudaGetDevice"));
+  if ((e = cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, P.device)))
+    return bail(cuda_fail(e, "querying the SM count"));
+  static bool configured = false;
+  if (!configured) {
+    if ((e = configure_pass_kernels())) return bail(cuda_fail(e, "configuring the pass kernel"));
+    configured = true;
+  }
+
+  std::vector<int64_t> tiles, tile_e;
+  build_tiles(off, tiles, tile_e);
+  P.ntiles = (int64_t)tiles.size() - 1;
+  P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P.num_sms, P.ntiles));
+  P.h_mu = std::min(J, kMaxCachedDests);
+  P.h_y = std::min(J, kMaxPrivDests);
+  P.epi_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((J + 255) / 256, 2 * P.num_sms));
+
+  const size_t e_pad = (size_t)((E + 3) & ~int64_t(3)) + 4;
+  const size_t i_pad = (size_t)I + 4;
+  std::vector<int64_t> off_pad(i_pad, E);
+  std::copy(off.begin(), off.end(), off_pad.begin());
+
+  if ((e = dev_alloc(P, &P.off, i_pad)) || (e = dev_alloc(P, &P.dst, e_pad)) ||
+      (e = dev_alloc(P, &P.tiles, tiles.size())) || (e = dev_alloc(P, &P.tile_e, tiles.size())) ||
+      (e = dev_alloc(P, &P.b_r, J)) || (e = dev_alloc(P, &P.orig_of, J)) ||
+      (e = dev_alloc(P, &P.new_of, J)) || (e = dev_alloc(P, &P.mu_r, J)) ||
+      (e = dev_alloc(P, &P.y, J)) || (e = dev_alloc(P, &P.yerr, J)) ||
+      (e = dev_alloc(P, &P.part, 2 * (size_t)P.grid)) ||
+      (e = dev_alloc(P, &P.epi_part, 2 * (size_t)P.epi_blocks)) ||
+      (e = dev_alloc(P, &P.eval_dev, 8)) || (e = dev_alloc(P, &P.lam_stage, J)) ||
+      (e = dev_alloc(P, &P.grad_stage, J)) || (e = dev_alloc(P, &P.status, 1)))
+    return bail(cuda_fail(e, "allocating problem memory"));
+  if (P.storage == DUALIP_EDGE_F32) {
+    if ((e = dev_alloc(P, &P.c, e_pad)) || (e = dev_alloc(P, &P.a, e_pad)))
+      return bail(cuda_fail(e, "allocating edge memory"));
+  } else {
+    if ((e = dev_alloc(P, &P.ca, e_pad))) return bail(cuda_fail(e, "allocating edge memory"));
+  }
+  if ((e = cudaMallocHost(&P.eval_host, 16 * sizeof(double))))
+    return bail(cuda_fail(e, "allocating pinned memory"));
+
+  // zero everything that must start at zero (padding included)
+  if ((e = cudaMemsetAsync(P.dst, 0, e_pad * 4, s)) || (e = cudaMemsetAsync(P.y, 0, J * 4, s)) ||
+      (e = cudaMemsetAsync(P.yerr, 0, J * 4, s)) ||
+      (e = cudaMemsetAsync(P.status, 0, sizeof(DeviceStatus), s)))
+    return bail(cuda_fail(e, "clearing problem memory"));
+  if (P.c && ((e = cudaMemsetAsync(P.c, 0, e_pad * 4, s)) ||
+              (e = cudaMemsetAsync(P.a, 0, e_pad * 4, s))))
+    return bail(cuda_fail(e, "clearing edge memory"));
+  if (P.ca && (e = cudaMemsetAsync(P.ca, 0, e_pad * 4, s)))
+    return bail(cuda_fail(e, "clearing edge memory"));
+  if ((e = cudaMemcpyAsync(P.off, off_pad.data(), i_pad * 8, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(P.tiles, tiles.data(), tiles.size() * 8, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(P.tile_e, tile_e.data(), tile_e.size() * 8, cudaMemcpyHostToDevice, s)))
+    return bail(cuda_fail(e, "uploading offsets"));
+
+  // raw destinations -> in-degree histogram (validates the range)
+  const int32_t* dst_raw = d->dst;
+  int32_t* dst_tmp = nullptr;
+  unsigned* counts = nullptr;
+  if ((e = cudaMalloc(&counts, sizeof(unsigned) * J))) return bail(cuda_fail(e, "allocating"));
+  auto free_tmp = [&]() {
+    cudaStreamSynchronize(s);
+    if (dst_tmp) cudaFree(dst_tmp);
+    if (counts) cudaFree(counts);
+    dst_tmp = nullptr;
+    counts = nullptr;
+  };
+  if (!d->inputs_on_device && E > 0) {
+    if ((e = cudaMalloc(&dst_tmp, sizeof(int32_t) * E)) ||
+        (e = cudaMemcpyAsync(dst_tmp, d->dst, sizeof(int32_t) * E, cudaMemcpyHostToDevice, s))) {
+      free_tmp();
+      return bail(cuda_fail(e, "uploading dst"));
+    }
+    dst_raw = dst_tmp;
+  }
+  std::vector<unsigned> cnt(J);
+  if ((e = cudaMemsetAsync(counts, 0, sizeof(unsigned) * J, s)) ||
+      (E > 0 && (e = launch_histogram(dst_raw, E, J, counts, P.status, s))) ||
+      (e = cudaMemcpyAsync(cnt.data(), counts, sizeof(unsigned) * J, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s))) {
+    free_tmp();
+    return bail(cuda_fail(e, "counting in-degrees"));
+  }
+  // renumber destinations by decreasing in-degree (ties by id): the hot ones
+  // get the smallest ids, which the pass caches in shared memory
+  std::vector<int32_t> orig_of(J), new_of(J);
+  std::iota(orig_of.begin(), orig_of.end(), 0);
+  std::stable_sort(orig_of.begin(), orig_of.end(),
+                   [&](int32_t x, int32_t y) { return cnt[x] > cnt[y]; });
+  for (int32_t r = 0; r < J; ++r) new_of[orig_of[r]] = r;
+  std::vector<float> b_host(J), b_r(J);
+  if ((e = cudaMemcpyAsync(b_host.data(), d->b, sizeof(float) * J,
+                           d->inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                           s)) ||
+      (e = cudaStreamSynchronize(s))) {
+    free_tmp();
+    return bail(cuda_fail(e, "reading b"));
+  }
+  double bn = 0.0;
+  for (int32_t j = 0; j < J; ++j) bn += (double)b_host[j] * (double)b_host[j];
+  P.bnorm = std::sqrt(bn);
+  for (int32_t r = 0; r < J; ++r) {
+    b_r[r] = b_host[orig_of[r]];
+    if (!std::isfinite(b_r[r])) {
+      free_tmp();
+      return bail(fail(DUALIP_EINVAL, "b must be finite"));
+    }
+  }
+  if ((e = cudaMemcpyAsync(P.orig_of, orig_of.data(), 4 * (size_t)J, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(P.new_of, new_of.data(), 4 * (size_t)J, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(P.b_r, b_r.data(), 4 * (size_t)J, cudaMemcpyHostToDevice, s)) ||
+      (E > 0 && (e = launch_renumber(dst_raw, P.dst, P.new_of, E, J, P.status, s)))) {
+    free_tmp();
+    return bail(cuda_fail(e, "renumbering destinations"));
+  }
+  free_tmp();
+
+  // edge values
+  if (E > 0) {
+    float *c_tmp = nullptr, *a_tmp = nullptr;
+    const float *c_src = d->c, *a_src = d->a;
+    if (P.storage == DUALIP_EDGE_F32) {
+      if ((e = cudaMemcpyAsync(P.c, d->c, 4 * (size_t)E, h2d, s)) ||
+          (e = cudaMemcpyAsync(P.a, d->a, 4 * (size_t)E, h2d, s)))
+        return bail(cuda_fail(e, "uploading c and a"));
+      c_src = P.c;
+      a_src = P.a;
+    } else if (!d->inputs_on_device) {
+      if ((e = cudaMalloc(&c_tmp, 4 * (size_t)E)) || (e = cudaMalloc(&a_tmp, 4 * (size_t)E)) ||
+          (e = cudaMemcpyAsync(c_tmp, d->c, 4 * (size_t)E, h2d, s)) ||
+          (e = cudaMemcpyAsync(a_tmp, d->a, 4 * (size_t)E, h2d, s))) {
+        cudaStreamSynchronize(s);
+        cudaFree(c_tmp);
+        cudaFree(a_tmp);
+        return bail(cuda_fail(e, "uploading c and a"));
+      }
+      c_src = c_tmp;
+      a_src = a_tmp;
+    }
+    if ((e = launch_check_finite(c_src, E, P.status, s)) ||
+        (e = launch_check_finite(a_src, E, P.status, s)) ||
+        (P.storage == DUALIP_EDGE_BF16 && (e = launch_pack_bf16(c_src, a_src, P.ca, E, s)))) {
+      cudaStreamSynchronize(s);
+      cudaFree(c_tmp);
+      cudaFree(a_tmp);
+      return bail(cuda_fail(e, "checking edge values"));
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(c_tmp);
+    cudaFree(a_tmp);
+  }
+  if ((e = cudaStreamSynchronize(s))) return bail(cuda_fail(e, "building the problem"));
+  DeviceStatus st{};
+  if ((e = cudaMemcpy(&st, P.status, sizeof(st), cudaMemcpyDeviceToHost)))
+    return bail(cuda_fail(e, "reading the device status"));
+  if (st.err) return bail(fail(DUALIP_EINVAL, "dst out of [0, J) or non-finite c / a"));
+  *out = h;
+  return DUALIP_OK;
+}
+
+void dualip_destroy(dualip_problem* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->p.last_stream);
+  free_all(h->p);
+  delete h;
+}
+
+dualip_status dualip_get_info(const dualip_problem* h, int64_t* I, int32_t* J, int64_t* E,
+                              int64_t* ntiles) {
+  if (!h) return fail(DUALIP_EINVAL, "problem handle is NULL");
+  if (I) *I = h->p.I;
+  if (J) *J = h->p.J;
+  if (E) *E = h->p.E;
+  if (ntiles) *ntiles = h->p.ntiles;
+  return DUALIP_OK;
+}
+
+dualip_status dualip_dual_grad_async(dualip_problem* h, const float* lambda, double gamma,
+                                     float* grad, double* out_dev, void* stream) {
+  dualip_status st = check_eval_args(h, lambda, gamma, grad);
+  if (st) return st;
+  if (!out_dev) return fail(DUALIP_EINVAL, "out_dev is NULL");
+  cudaStream_t s = as_stream(stream);
+  h->p.last_stream = s;
+  cudaError_t e = enqueue_eval(h->p, lambda, gamma, grad, out_dev, nullptr, s);
+  return e ? cuda_fail(e, "launching the dual evaluation") : DUALIP_OK;
+}
+
+dualip_status dualip_dual_grad(dualip_problem* h, const float* lambda, double gamma, float* grad,
+                               dualip_eval* out, void* stream) {
+  dualip_status st = check_eval_args(h, lambda, gamma, grad);
+  if (st) return st;
+  Problem& P = h->p;
+  cudaStream_t s = as_stream(stream);
+  P.last_stream = s;
+  cudaError_t e = enqueue_eval(P, lambda, gamma, grad, P.eval_dev, nullptr, s);
+  if (e) return cuda_fail(e, "launching the dual evaluation");
+  if (!out) return DUALIP_OK;
+  if ((e = cudaMemcpyAsync(P.eval_host, P.eval_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, s)))
+    return cuda_fail(e, "reading the scalars");
+  if ((st = read_status(P, s))) return st;
+  std::memcpy(out, P.eval_host, sizeof(dualip_eval));
+  return DUALIP_OK;
+}
+
+dualip_status dualip_dual_grad_host(dualip_problem* h, const float* lambda_host, double gamma,
+                                    float* grad_host, dualip_eval* out, void* stream) {
+  dualip_status st = check_eval_args(h, lambda_host, gamma, grad_host);
+  if (st) return st;
+  Problem& P = h->p;
+  cudaStream_t s = as_stream(stream);
+  P.last_stream = s;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(P.lam_stage, lambda_host, 4 * (size_t)P.J, cudaMemcpyHostToDevice, s)))
+    return cuda_fail(e, "copying lambda in");
+  if ((e = enqueue_eval(P, P.lam_stage, gamma, P.grad_stage, P.eval_dev, nullptr, s)))
+    return cuda_fail(e, "launching the dual evaluation");
+  if ((e = cudaMemcpyAsync(grad_host, P.grad_stage, 4 * (size_t)P.J, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(P.eval_host, P.eval_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, s)))
+    return cuda_fail(e, "copying results out");
+  if ((st = read_status(P, s))) return st;
+  if (out) std::memcpy(out, P.eval_host, sizeof(dualip_eval));
+  return DUALIP_OK;
+}
+
+dualip_status dualip_get_primal(dualip_problem* h, const float* lambda, double gamma, float* x,
+                                void* stream) {
+  dualip_status st = check_eval_args(h, lambda, gamma, x);
+  if (st) return st;
+  Problem& P = h->p;
+  cudaStream_t s = as_stream(stream);
+  P.last_stream = s;
+  cudaError_t e = enqueue_eval(P, lambda, gamma, P.grad_stage, P.eval_dev, x, s);
+  return e ? cuda_fail(e, "launching the primal evaluation") : DUALIP_OK;
+}
+
+dualip_status dualip_profile_enable(dualip_problem* h, int32_t max_evals) {
+  if (!h || max_evals < 1) return fail(DUALIP_EINVAL, "need a handle and max_evals >= 1");
+  Problem& P = h->p;
+  free_events(P);
+  P.prof_ev.resize(4 * (size_t)max_evals, nullptr);
+  for (auto& ev : P.prof_ev) {
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e) {
+      ev = nullptr;
+      free_events(P);
+      return cuda_fail(e, "creating timing events");
+    }
+  }
+  P.prof_max = max_evals;
+  P.prof_used = 0;
+  return DUALIP_OK;
+}
+
+dualip_status dualip_profile_collect(dualip_problem* h, double* ms_prep, double* ms_pass,
+                                     double* ms_epi, int32_t* count) {
+  if (!h) return fail(DUALIP_EINVAL, "problem handle is NULL");
+  Problem& P = h->p;
+  double t[3] = {0, 0, 0};
+  for (int i = 0; i < P.prof_used; ++i) {
+    cudaEvent_t* ev = &P.prof_ev[4 * (size_t)i];
+    cudaError_t e = cudaEventSynchronize(ev[3]);
+    for (int k = 0; k < 3 && !e; ++k) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      t[k] += ms;
+    }
+    if (e) {
+      free_events(P);
+      return cuda_fail(e, "reading timing events");
+    }
+  }
+  if (ms_prep) *ms_prep = t[0];
+  if (ms_pass) *ms_pass = t[1];
+  if (ms_epi) *ms_epi = t[2];
+  if (count) *count = P.prof_used;
+  free_events(P);
+  return DUALIP_OK;
+}
+
+dualip_status dualip_check_device_status(dualip_problem* h, void* stream) {
+  if (!h) return fail(DUALIP_EINVAL, "problem handle is NULL");
+  return read_status(h->p, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dualip.h"
+
+namespace dualip {
+
+// ---- pass geometry --------------------------------------------------------
+// A tile is a run of whole sources whose edges fit one shared-memory stage.
+constexpr int kTileEdges = 2048;       // edge capacity of a stage
+constexpr int kTileSources = 512;      // source capacity of a stage
+constexpr int kStages = 4;             // depth of the staging ring
+constexpr int kConsumerWarps = 16;     // warps that project sources
+constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
+constexpr int kMaxCachedDests = 10240; // hot destinations whose mu lives in smem
+constexpr int kMaxPrivDests = 4096;    // hot destinations accumulated in smem
+constexpr int kRegMaxDeg = 128;        // degrees held in registers (4 per lane)
+constexpr int kStageEdgeSlots = kTileEdges + 8;      // + 16-byte alignment slack
+constexpr int kStageOffSlots = kTileSources + 4;
+
+// device error word bits
+constexpr int kErrTimeout = 1;
+constexpr int kErrBounds = 2;
+
+struct DeviceStatus {
+  int err;        // OR of kErr* bits
+  int where;      // first wait site that timed out
+  unsigned ticket;  // last-block counter of the epilogue (reset by the last block)
+  int pad;
+};
+
+// Kernel parameters of one pass (one dual evaluation).
+struct PassParams {
+  // edges
+  const int64_t* off;     // [I+1 (+ padding)]
+  const int32_t* dst;     // [E_pad] renumbered destinations
+  const float* c;         // [E_pad] (f32 storage)
+  const float* a;         // [E_pad] (f32 storage)
+  const uint32_t* ca;     // [E_pad] packed bf16 (c | a << 16) (bf16 storage)
+  const int64_t* tiles;   // [ntiles+1] first source of each tile
+  const int64_t* tile_e;  // [ntiles+1] first edge of each tile (= off[tiles[t]])
+  int64_t ntiles;
+  int64_t I;
+  int32_t J;
+  int32_t h_mu;           // destinations [0, h_mu) have their mu cached in smem
+  int32_t h_y;            // destinations [0, h_y) accumulate in smem
+  // dual point, renumbered: mu_r[jr]
+  const float* mu_r;
+  const float* gamma_dev;  // if non-null, gamma is read here (solver)
+  float gamma;
+  // outputs / scratch
+  float* y;               // [J] FP32 sum of a x (renumbered)
+  float* yerr;            // [J] compensation of y
+  double* part;           // [gridDim.x * 2] per-CTA (sum c x, sum w x^2)
+  float* x_out;           // [E] optional primal output (edge order)
+  DeviceStatus* status;
+};
+
+// Kernel parameters of the J-length epilogue.
+struct EpiParams {
+  int32_t J;
+  const int32_t* orig_of;  // renumbered -> caller's destination id
+  const float* b_r;        // [J] budgets, renumbered
+  const float* mu_r;       // [J] renumbered dual point used by the pass
+  const float* D;          // [J] optional row scale in caller numbering (solver)
+  float* y;                // [J] reset to 0 after reading
+  float* yerr;             // [J] reset to 0 after reading
+  float* grad;             // [J] caller numbering: D (A x - b) (D = 1 if null)
+  const double* part;      // per-CTA partials of the pass
+  int npart;
+  double* epi_part;        // [gridDim.x * 4] per-block partials of the epilogue
+  const float* gamma_dev;
+  double gamma;
+  double* eval_out;        // [5] dualip_eval order
+  DeviceStatus* status;
+};
+
+struct Problem {
+  int64_t I = 0, E = 0;
+  int32_t J = 0;
+  int storage = DUALIP_EDGE_F32;
+  int weighted = 0;
+  int64_t ntiles = 0;
+  int h_mu = 0, h_y = 0;
+  int num_sms = 0, grid = 0;
+  int device = 0;
+  // device buffers (owned)
+  int64_t* off = nullptr;
+  int32_t* dst = nullptr;
+  float* c = nullptr;
+  float* a = nullptr;
+  uint32_t* ca = nullptr;
+  int64_t* tiles = nullptr;
+  int64_t* tile_e = nullptr;
+  float* b_r = nullptr;
+  int32_t* orig_of = nullptr;
+  int32_t* new_of = nullptr;
+  float* mu_r = nullptr;
+  float* y = nullptr;
+  float* yerr = nullptr;
+  double* part = nullptr;
+  int epi_blocks = 0;
+  double* epi_part = nullptr;
+  double* eval_dev = nullptr;
+  float* lam_stage = nullptr;   // [J] staging for host-buffer calls
+  float* grad_stage = nullptr;  // [J]
+  DeviceStatus* status = nullptr;
+  double* eval_host = nullptr;  // pinned [8]
+  cudaStream_t last_stream = nullptr;
+  double bnorm = 0.0;           // ||b||_2
+  void* solve_ctx = nullptr;    // solver state, created by the first dualip_solve
+  std::vector<cudaEvent_t> prof_ev;  // 4 per recorded evaluation
+  int prof_max = 0, prof_used = 0;
+  std::vector<void*> allocations;
+};
+
+// pass.cu
+size_t pass_smem_bytes(int storage);
+cudaError_t configure_pass_kernels();
+cudaError_t launch_prep(const Problem& P, const float* lambda, const float* D, cudaStream_t s);
+cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, float* x_out,
+                        cudaStream_t s);
+cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const float* gamma_dev,
+                            double gamma, double* eval_out, cudaStream_t s, bool identity = false);
+cudaError_t launch_renumber(const int32_t* dst_in, int32_t* dst_out, const int32_t* new_of,
+                            int64_t E, int32_t J, DeviceStatus* st, cudaStream_t s);
+cudaError_t launch_histogram(const int32_t* dst, int64_t E, int32_t J, unsigned* counts,
+                             DeviceStatus* st, cudaStream_t s);
+cudaError_t launch_pack_bf16(const float* c, const float* a, uint32_t* ca, int64_t E,
+                             cudaStream_t s);
+cudaError_t launch_check_finite(const float* v, int64_t n, DeviceStatus* st, cudaStream_t s);
+
+// solve.cu
+void solve_ctx_free(Problem& P);
+
+// api.cu helpers
+void set_error(const std::string& msg);
+dualip_status fail(dualip_status st, const std::string& msg);
+dualip_status cuda_fail(cudaError_t e, const char* what);
+
+}  // namespace dualip
+
+struct dualip_problem {
+  dualip::Problem p;
+};

@@ -1,0 +1,428 @@
+// Dual ascent on the GPU (Section 5 and Appendix B of the DuaLip-GPU report).
+//
+// The iteration lives entirely on the device so that check_every iterations
+// can be replayed as one CUDA graph with no host synchronisation:
+//   prep   (J)  gamma_k from k; momentum restart on a gamma change; mu = D y
+//   pass        projection + A x (pass.cu), gamma read from the state
+//   epi    (J)  G = D (A x - b) and the FP64 scalars (pass.cu)
+//   norms  (J)  ||y - y_prev||, ||G - G_prev|| in FP64; the last block picks
+//               the step (secant estimate capped by max_step * gamma / gamma0),
+//               the momentum weight, the stopping scalars and the trace row
+//   step   (J)  lam+ = max(0, y + eta G); y+ = max(0, lam+ + beta (lam+ - lam))
+// Vectors are kept in the renumbered destination order and in the
+// normalised coordinates lam' of Section 5.1 (mu = D lam').
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace dualip {
+namespace {
+
+struct SolveState {
+  // options (read-only during the run)
+  double gamma0, gamma_final, max_step, init_step, bnorm;
+  int32_t halve_every, restart;
+  double* trace;
+  // iteration state
+  int32_t k;
+  int32_t last_k;
+  float gamma_f;  // gamma of the current iteration, read by the pass
+  float pad;
+  double t, eta, beta;
+  double gap_rel, infeas_rel, last_gamma;
+  double eval[5];  // written by the epilogue
+  unsigned ticket;
+  int32_t pad2;
+};
+
+__host__ __device__ inline double gamma_at(const SolveState& s, int32_t k) {
+  double g = s.gamma0;
+  if (s.halve_every > 0) g = ldexp(s.gamma0, -(k / s.halve_every));
+  return g > s.gamma_final ? g : s.gamma_final;
+}
+__device__ inline bool restart_at(const SolveState& s, int32_t k) {
+  return s.restart && k > 0 && gamma_at(s, k) != gamma_at(s, k - 1);
+}
+
+struct Vecs {
+  float *lam, *y, *yp, *G, *Gp, *D;
+};
+
+__global__ void solve_init_kernel(int32_t J, const float* __restrict__ lam_in,
+                                  const int32_t* __restrict__ orig_of, Vecs v) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const float l = lam_in[orig_of[j]] / v.D[j];
+    const float c = l > 0.f ? l : 0.f;
+    v.lam[j] = c;
+    v.y[j] = c;
+    v.yp[j] = c;
+    v.G[j] = 0.f;
+    v.Gp[j] = 0.f;
+  }
+}
+
+__global__ void solve_prep_kernel(int32_t J, SolveState* st, Vecs v, float* __restrict__ mu_r) {
+  const int32_t k = st->k;
+  const bool rs = restart_at(*st, k);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    float yj = v.y[j];
+    if (rs) {
+      yj = v.lam[j];
+      v.y[j] = yj;
+    }
+    mu_r[j] = __fmul_rn(v.D[j], yj);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->gamma_f = (float)gamma_at(*st, k);
+}
+
+__global__ void solve_norms_kernel(int32_t J, SolveState* st, Vecs v, double* part) {
+  const int32_t k = st->k;
+  const bool have_prev = k > 0 && !restart_at(*st, k);
+  double dy = 0.0, dg = 0.0;
+  if (have_prev) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
+         j += (int64_t)gridDim.x * blockDim.x) {
+      const double u = (double)v.y[j] - (double)v.yp[j];
+      const double w = (double)v.G[j] - (double)v.Gp[j];
+      dy += u * u;
+      dg += w * w;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    dy += __shfl_xor_sync(0xffffffffu, dy, o);
+    dg += __shfl_xor_sync(0xffffffffu, dg, o);
+  }
+  __shared__ double red[2][32];
+  __shared__ bool last;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[0][w] = dy;
+    red[1][w] = dg;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a += red[0][i];
+      b += red[1][i];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+    __threadfence();
+    last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double sdy = 0.0, sdg = 0.0;
+  for (unsigned i = 0; i < gridDim.x; ++i) {
+    sdy += part[2 * i];
+    sdg += part[2 * i + 1];
+  }
+  const double gk = gamma_at(*st, k);
+  const double eta_max = st->max_step * gk / st->gamma0;
+  double eta;
+  if (have_prev) eta = sdg > 0.0 ? fmin(eta_max, sqrt(sdy) / sqrt(sdg)) : eta_max;
+  else eta = fmin(st->init_step, eta_max);
+  const double t = restart_at(*st, k) ? 1.0 : st->t;
+  const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+  st->eta = eta;
+  st->beta = (t - 1.0) / tn;
+  st->t = tn;
+  const double g = st->eval[0], p = st->eval[1] + st->eval[2];
+  const double den = fmax(1.0, fmax(fabs(p), fabs(g)));
+  st->gap_rel = fabs(st->eval[4]) / den;
+  st->infeas_rel = st->eval[3] / fmax(1.0, st->bnorm);
+  st->last_k = k;
+  st->last_gamma = gk;
+  if (st->trace) {
+    double* tr = st->trace + 8 * (size_t)k;
+    tr[0] = gk;
+    tr[1] = g;
+    tr[2] = p;
+    tr[3] = st->eval[3];
+    tr[4] = st->gap_rel;
+    tr[5] = st->infeas_rel;
+    tr[6] = eta;
+    tr[7] = st->eval[4];
+  }
+  st->k = k + 1;
+  st->ticket = 0u;
+}
+
+__global__ void solve_step_kernel(int32_t J, const SolveState* st, Vecs v) {
+  const float eta = (float)st->eta, beta = (float)st->beta;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const float yk = v.y[j], g = v.G[j], lk = v.lam[j];
+    float ln = __fmaf_rn(eta, g, yk);
+    ln = ln > 0.f ? ln : 0.f;
+    float yn = __fmaf_rn(beta, __fsub_rn(ln, lk), ln);
+    yn = yn > 0.f ? yn : 0.f;
+    v.yp[j] = yk;
+    v.Gp[j] = g;
+    v.lam[j] = ln;
+    v.y[j] = yn;
+  }
+}
+
+__global__ void solve_final_kernel(int32_t J, Vecs v, const int32_t* __restrict__ orig_of,
+                                   float* __restrict__ lam_out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
+       j += (int64_t)gridDim.x * blockDim.x)
+    lam_out[orig_of[j]] = __fmul_rn(v.D[j], v.yp[j]);
+}
+
+// D_j = (sum_{e -> j} a_e^2 / w_e)^(-1/2), 1 for a zero row (Section 5.1)
+__global__ void row_norm_kernel(const int32_t* __restrict__ dst, const float* __restrict__ a,
+                                const uint32_t* __restrict__ ca, int64_t E, int weighted,
+                                double* __restrict__ acc) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float av = a ? a[e] : __uint_as_float(ca[e] & 0xffff0000u);
+    double v = (double)av * (double)av;
+    if (weighted) v = av != 0.f ? 1.0 : 0.0;
+    if (v != 0.0) atomicAdd(acc + dst[e], v);
+  }
+}
+__global__ void row_scale_kernel(int32_t J, const double* __restrict__ acc, float* __restrict__ D) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
+       j += (int64_t)gridDim.x * blockDim.x)
+    D[j] = acc[j] > 0.0 ? (float)(1.0 / sqrt(acc[j])) : 1.0f;
+}
+__global__ void fill_kernel(int32_t J, float* __restrict__ D, float v) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
+       j += (int64_t)gridDim.x * blockDim.x)
+    D[j] = v;
+}
+
+}  // namespace
+
+struct SolveCtx {
+  int row_normalize = -1;  // row scale currently held in D (-1: none yet)
+  float *lam = nullptr, *y = nullptr, *yp = nullptr, *G = nullptr, *Gp = nullptr, *D = nullptr;
+  double* part = nullptr;
+  SolveState* st = nullptr;
+  SolveState* st_host = nullptr;  // pinned
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  int blocks = 0;
+};
+
+void solve_ctx_free(Problem& P) {
+  SolveCtx* C = static_cast<SolveCtx*>(P.solve_ctx);
+  if (!C) return;
+  if (C->stream) cudaStreamSynchronize(C->stream);
+  if (C->graph) cudaGraphExecDestroy(C->graph);
+  void* bufs[] = {C->lam, C->y, C->yp, C->G, C->Gp, C->D, C->part, C->st};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (C->st_host) cudaFreeHost(C->st_host);
+  if (C->ev) cudaEventDestroy(C->ev);
+  if (C->stream) cudaStreamDestroy(C->stream);
+  delete C;
+  P.solve_ctx = nullptr;
+}
+
+static cudaError_t solve_ctx_get(Problem& P, SolveCtx** out) {
+  if (P.solve_ctx) {
+    *out = static_cast<SolveCtx*>(P.solve_ctx);
+    return cudaSuccess;
+  }
+  SolveCtx* C = new SolveCtx();
+  P.solve_ctx = C;
+  const size_t n = (size_t)P.J * sizeof(float);
+  cudaError_t e;
+  if ((e = cudaMalloc(&C->lam, n)) || (e = cudaMalloc(&C->y, n)) || (e = cudaMalloc(&C->yp, n)) ||
+      (e = cudaMalloc(&C->G, n)) || (e = cudaMalloc(&C->Gp, n)) || (e = cudaMalloc(&C->D, n)))
+    return e;
+  C->blocks = (int)std::max<int64_t>(1, std::min<int64_t>((P.J + 255) / 256, 2 * P.num_sms));
+  if ((e = cudaMalloc(&C->part, sizeof(double) * 2 * C->blocks)) ||
+      (e = cudaMalloc(&C->st, sizeof(SolveState))) ||
+      (e = cudaMallocHost(&C->st_host, sizeof(SolveState))) ||
+      (e = cudaStreamCreateWithFlags(&C->stream, cudaStreamNonBlocking)) ||
+      (e = cudaEventCreateWithFlags(&C->ev, cudaEventDisableTiming)))
+    return e;
+  *out = C;
+  return cudaSuccess;
+}
+
+static cudaError_t ensure_row_scale(Problem& P, SolveCtx& C, int row_normalize, cudaStream_t s) {
+  if (C.row_normalize == row_normalize) return cudaSuccess;
+  cudaError_t e;
+  if (!row_normalize) {
+    fill_kernel<<<C.blocks, 256, 0, s>>>(P.J, C.D, 1.0f);
+    if ((e = cudaGetLastError())) return e;
+  } else {
+    double* acc = nullptr;
+    if ((e = cudaMalloc(&acc, sizeof(double) * P.J))) return e;
+    e = cudaMemsetAsync(acc, 0, sizeof(double) * P.J, s);
+    if (!e && P.E > 0) {
+      const int64_t g = std::min<int64_t>((P.E + 255) / 256, 8192);
+      row_norm_kernel<<<(int)g, 256, 0, s>>>(P.dst, P.a, P.ca, P.E, P.weighted, acc);
+      e = cudaGetLastError();
+    }
+    if (!e) {
+      row_scale_kernel<<<C.blocks, 256, 0, s>>>(P.J, acc, C.D);
+      e = cudaGetLastError();
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(acc);
+    if (e) return e;
+  }
+  C.row_normalize = row_normalize;
+  return cudaSuccess;
+}
+
+static cudaError_t enqueue_iteration(Problem& P, SolveCtx& C, cudaStream_t s) {
+  Vecs v{C.lam, C.y, C.yp, C.G, C.Gp, C.D};
+  cudaError_t e;
+  solve_prep_kernel<<<C.blocks, 256, 0, s>>>(P.J, C.st, v, P.mu_r);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = launch_pass(P, &C.st->gamma_f, 0.f, nullptr, s))) return e;
+  if ((e = launch_epilogue(P, C.D, C.G, &C.st->gamma_f, 0.0, C.st->eval, s, true))) return e;
+  solve_norms_kernel<<<C.blocks, 256, 0, s>>>(P.J, C.st, v, C.part);
+  if ((e = cudaGetLastError())) return e;
+  solve_step_kernel<<<C.blocks, 256, 0, s>>>(P.J, C.st, v);
+  return cudaGetLastError();
+}
+
+static cudaError_t run_chunk(Problem& P, SolveCtx& C, int n, bool use_graph) {
+  cudaError_t e;
+  if (use_graph) {
+    if (!C.graph || C.graph_len != n) {
+      if (C.graph) cudaGraphExecDestroy(C.graph);
+      C.graph = nullptr;
+      cudaGraph_t g = nullptr;
+      if ((e = cudaStreamBeginCapture(C.stream, cudaStreamCaptureModeThreadLocal))) return e;
+      for (int i = 0; i < n; ++i) {
+        e = enqueue_iteration(P, C, C.stream);
+        if (e) break;
+      }
+      cudaError_t e2 = cudaStreamEndCapture(C.stream, &g);
+      if (e) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+      }
+      if (e2) return e2;
+      e = cudaGraphInstantiate(&C.graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e) return e;
+      C.graph_len = n;
+    }
+    return cudaGraphLaunch(C.graph, C.stream);
+  }
+  for (int i = 0; i < n; ++i)
+    if ((e = enqueue_iteration(P, C, C.stream))) return e;
+  return cudaSuccess;
+}
+
+}  // namespace dualip
+
+using namespace dualip;
+
+extern "C" {
+
+void dualip_solve_opts_default(dualip_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->gamma0 = 0.1;
+  o->gamma_final = 1e-3;
+  o->halve_every = 25;
+  o->max_step = 10.0;
+  o->init_step = 1e-5;
+  o->max_iters = 5000;
+  o->tol_gap = 1e-4;
+  o->tol_infeas = 1e-4;
+  o->check_every = 10;
+  o->row_normalize = 1;
+  o->restart_on_gamma_change = 1;
+  o->stop_on_tol = 1;
+  o->use_graph = 1;
+}
+
+dualip_status dualip_solve(dualip_problem* h, const dualip_solve_opts* o, float* lambda_io,
+                           dualip_solve_result* res, double* trace, void* stream) {
+  if (!h || !o || !lambda_io) return fail(DUALIP_EINVAL, "handle, opts and lambda must be non-NULL");
+  if (!(o->gamma0 > 0) || !(o->gamma_final > 0) || !std::isfinite(o->gamma0) ||
+      o->gamma_final > o->gamma0 || o->gamma_final < 1e-30)
+    return fail(DUALIP_EINVAL, "need 1e-30 <= gamma_final <= gamma0 < inf");
+  if (o->max_iters < 1 || o->check_every < 1 || !(o->max_step > 0) || !(o->init_step > 0))
+    return fail(DUALIP_EINVAL, "need max_iters >= 1, check_every >= 1, positive steps");
+  Problem& P = h->p;
+  cudaStream_t us = static_cast<cudaStream_t>(stream);
+  P.last_stream = us;
+  SolveCtx* Cp = nullptr;
+  cudaError_t e = solve_ctx_get(P, &Cp);
+  if (e) return cuda_fail(e, "allocating solver state");
+  SolveCtx& C = *Cp;
+  // order the private stream after the caller's stream
+  if ((e = cudaEventRecord(C.ev, us)) || (e = cudaStreamWaitEvent(C.stream, C.ev, 0)))
+    return cuda_fail(e, "ordering streams");
+  if ((e = ensure_row_scale(P, C, o->row_normalize ? 1 : 0, C.stream)))
+    return cuda_fail(e, "computing the row scale");
+  SolveState& H = *C.st_host;
+  std::memset(&H, 0, sizeof(H));
+  H.gamma0 = o->gamma0;
+  H.gamma_final = o->gamma_final;
+  H.max_step = o->max_step;
+  H.init_step = o->init_step;
+  H.bnorm = P.bnorm;
+  H.halve_every = o->halve_every;
+  H.restart = o->restart_on_gamma_change ? 1 : 0;
+  H.trace = trace;
+  H.t = 1.0;
+  if ((e = cudaMemcpyAsync(C.st, &H, sizeof(H), cudaMemcpyHostToDevice, C.stream)))
+    return cuda_fail(e, "uploading solver state");
+  {
+    Vecs v{C.lam, C.y, C.yp, C.G, C.Gp, C.D};
+    solve_init_kernel<<<C.blocks, 256, 0, C.stream>>>(P.J, lambda_io, P.orig_of, v);
+    if ((e = cudaGetLastError())) return cuda_fail(e, "initialising the solver");
+  }
+  int done = 0;
+  bool converged = false;
+  dualip_status st = DUALIP_OK;
+  while (done < o->max_iters) {
+    const int n = std::min(o->check_every, o->max_iters - done);
+    if ((e = run_chunk(P, C, n, o->use_graph && n == o->check_every)))
+      return cuda_fail(e, "running solver iterations");
+    done += n;
+    if ((e = cudaMemcpyAsync(C.st_host, C.st, sizeof(SolveState), cudaMemcpyDeviceToHost,
+                             C.stream)) ||
+        (e = cudaStreamSynchronize(C.stream)))
+      return cuda_fail(e, "reading solver state");
+    if ((st = dualip_check_device_status(h, C.stream))) return st;
+    if (o->stop_on_tol && done % o->check_every == 0 && H.last_gamma == o->gamma_final &&
+        H.gap_rel <= o->tol_gap && H.infeas_rel <= o->tol_infeas) {
+      converged = true;
+      break;
+    }
+  }
+  {
+    Vecs v{C.lam, C.y, C.yp, C.G, C.Gp, C.D};
+    solve_final_kernel<<<C.blocks, 256, 0, C.stream>>>(P.J, v, P.orig_of, lambda_io);
+    if ((e = cudaGetLastError())) return cuda_fail(e, "writing lambda");
+  }
+  if ((e = cudaEventRecord(C.ev, C.stream)) || (e = cudaStreamWaitEvent(us, C.ev, 0)) ||
+      (e = cudaStreamSynchronize(C.stream)))
+    return cuda_fail(e, "finishing the solve");
+  if (res) {
+    res->iters = done;
+    res->converged = converged ? 1 : 0;
+    std::memcpy(&res->last, H.eval, sizeof(res->last));
+    res->gap_rel = H.gap_rel;
+    res->infeas_rel = H.infeas_rel;
+    res->gamma = H.last_gamma;
+  }
+  if (!converged && o->stop_on_tol)
+    return fail(DUALIP_ENOTCONVERGED, "max_iters reached before the tolerances held");
+  return DUALIP_OK;
+}
+
+}  // extern "C"

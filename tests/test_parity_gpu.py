@@ -1,0 +1,220 @@
+"""Parity of the CUDA dual evaluation (through the C ABI) with the FP64 oracle.
+
+Tolerances (the gradient bound is per entry, because A x - b cancels):
+  |grad_gpu_j - grad_oracle_j| <= 1e-5 * (|(A x)_j| + |b_j|) + 1e-6
+  |g_gpu - g_oracle| <= 1e-6 * max(1, |g|)     (same for c^T x, ridge term)
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GRAD_RTOL = 1e-5
+OBJ_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def dl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_04621_gb300 import build
+
+    build.build()
+    import paper_2603_04621_gb300 as d
+
+    return d
+
+
+def bf16_round(x):
+    """float32 -> bfloat16 (round to nearest even) -> float32, for finite x."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32)
+
+
+def decoded(inst):
+    return synth.Instance(inst.off, inst.dst, bf16_round(inst.c), bf16_round(inst.a), inst.b,
+                          inst.J, name=inst.name + "[bf16]")
+
+
+def check_eval(d, inst, lam, gamma, weighted=False, storage="f32", P=None, Po=None):
+    import torch
+
+    P = P or d.Problem.from_instance(inst, storage=storage, primal_scaling=weighted)
+    ref_inst = decoded(inst) if storage == "bf16" else inst
+    Po = Po or oracle.Problem(ref_inst, weighted=weighted)
+    lam32 = np.asarray(lam, dtype=np.float32)
+    grad, ev = P.dual_grad(torch.from_numpy(lam32).cuda(), gamma)
+    grad = grad.cpu().numpy().astype(np.float64)
+    eo = Po.eval(lam32.astype(np.float64), gamma)
+    tol = GRAD_RTOL * (np.abs(eo.ax) + np.abs(inst.b.astype(np.float64))) + 1e-6
+    err = np.abs(grad - eo.grad)
+    bad = np.nonzero(err > tol)[0]
+    assert bad.size == 0, (f"{bad.size} gradient entries out of tolerance; worst "
+                           f"{(err / tol).max():.3g}x at j={bad[:5]}, gpu={grad[bad[:5]]}, "
+                           f"oracle={eo.grad[bad[:5]]}")
+    for key, ref in (("dual_obj", eo.dual), ("primal_obj", eo.primal_lin), ("reg", eo.reg),
+                     ("lambda_dot_grad", eo.mu_dot_grad)):
+        assert abs(ev[key] - ref) <= OBJ_RTOL * max(1.0, abs(ref)), (key, ev[key], ref)
+    assert abs(ev["infeas_l2"] - eo.infeas) <= 1e-5 * max(1.0, eo.infeas) + 1e-6 * np.linalg.norm(
+        inst.b)
+    return P, Po, grad, ev
+
+
+def lam_points(inst, rng, n=3):
+    pts = [np.zeros(inst.J)]
+    for _ in range(n):
+        pts.append(rng.uniform(0.0, 2.0, inst.J))
+    return pts
+
+
+@pytest.mark.parametrize("gamma", [0.1, 1e-3])
+def test_c1_parity(dl, gamma):
+    inst = synth.config("c1")
+    rng = np.random.default_rng(1)
+    P = Po = None
+    for lam in lam_points(inst, rng):
+        P, Po, _, _ = check_eval(dl, inst, lam, gamma, P=P, Po=Po)
+
+
+@pytest.mark.parametrize("gamma", [0.1, 0.01, 1e-3])
+def test_c2_shape_parity(dl, gamma):
+    # the c2 laws at 2% of the sources: ~1M edges, >400 tiles, ragged tail
+    inst = synth.config("c2", scale=0.02)
+    rng = np.random.default_rng(2)
+    P = Po = None
+    for lam in lam_points(inst, rng, 2):
+        P, Po, _, _ = check_eval(dl, inst, lam, gamma, P=P, Po=Po)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_greedy_budget_parity_at_solver_points(dl, weighted):
+    inst = synth.greedy_budgets(synth.matching(20_000, 500, 7, ("poisson", 50, 1, 500)))
+    Po = oracle.Problem(inst, weighted=weighted)
+    res = Po.solve(max_iters=300, stop_on_tol=False)
+    P = None
+    for gamma in (0.1, 1e-3):
+        P, Po, _, _ = check_eval(dl, inst, res["mu"], gamma, weighted, P=P, Po=Po)
+
+
+def test_adversarial_degrees(dl):
+    # segment lengths around every class boundary of the kernel, plus
+    # sources larger than a shared-memory tile
+    degs = [0, 1, 31, 32, 33, 63, 64, 65, 96, 97, 127, 128, 129, 500, 1024, 1025, 2047, 2048,
+            2049, 5000, 0, 3, 0, 100_000, 7]
+    J = 120_000
+    inst = synth.from_degrees(np.array(degs), J, 11, synth.DST_UNIFORM, b_frac=0.5)
+    rng = np.random.default_rng(3)
+    P = Po = None
+    for gamma in (0.5, 1e-3, 1e-6):
+        for lam in (np.zeros(J), rng.uniform(0, 1, J)):
+            P, Po, _, _ = check_eval(dl, inst, lam, gamma, P=P, Po=Po)
+            P, Po, _, _ = check_eval(dl, inst, lam, gamma, P=P, Po=Po)  # reuse: scratch reset
+
+
+def test_many_tiny_sources_and_all_hot(dl):
+    # degree-1 sources (tile capped by the source count) into 3 destinations
+    inst = synth.from_degrees(np.ones(50_000, dtype=np.int64), 3, 12, synth.DST_UNIFORM,
+                              c_law=synth.C_NEG_UNIFORM, b_frac=0.3)
+    for gamma in (1.0, 1e-3):
+        check_eval(dl, inst, np.array([0.0, 0.5, 5.0]), gamma)
+
+
+def test_large_lambda_and_empty_rows(dl):
+    inst = synth.matching(3000, 400, 13, ("poisson", 20, 0, 60), "zipf")
+    assert np.bincount(inst.dst, minlength=inst.J).min() == 0  # some rows are empty
+    P, Po, grad, ev = check_eval(dl, inst, np.full(inst.J, 1e6), 1e-3)
+    assert ev["primal_obj"] == 0.0 and ev["reg"] == 0.0
+    assert np.array_equal(grad, -inst.b.astype(np.float64))
+
+
+def test_empty_problem(dl):
+    inst = synth.Instance(np.zeros(5, dtype=np.int64), np.zeros(0, np.int32),
+                          np.zeros(0, np.float32), np.zeros(0, np.float32),
+                          np.arange(4, dtype=np.float32), 4)
+    P, Po, grad, ev = check_eval(dl, inst, np.ones(4), 0.1)
+    assert np.array_equal(grad, -np.arange(4))
+    assert ev["dual_obj"] == pytest.approx(-6.0)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_bf16_storage_parity(dl, weighted):
+    inst = synth.config("c2", scale=0.01)
+    rng = np.random.default_rng(4)
+    for gamma in (0.1, 1e-3):
+        check_eval(dl, inst, rng.uniform(0, 2, inst.J), gamma, weighted, storage="bf16")
+
+
+def test_primal_matches_oracle(dl):
+    import torch
+
+    inst = synth.config("c2", scale=0.005)
+    Po = oracle.Problem(inst)
+    P = dl.Problem.from_instance(inst)
+    lam = np.random.default_rng(5).uniform(0, 2, inst.J).astype(np.float32)
+    for gamma in (0.2, 1e-3):
+        x = P.primal(torch.from_numpy(lam).cuda(), gamma).cpu().numpy()
+        xo = Po.eval(lam.astype(np.float64), gamma, want_x=True).x
+        assert np.all(x >= 0)
+        assert np.abs(x - xo).max() <= 2e-5, np.abs(x - xo).max()
+        sums = np.add.reduceat(x, inst.off[:-1]) if inst.E else x
+        assert sums.max() <= 1 + 1e-5
+
+
+def test_host_buffer_entry_point(dl):
+    inst = synth.config("c2", scale=0.005)
+    P = dl.Problem.from_instance(inst)
+    Po = oracle.Problem(inst)
+    lam = np.random.default_rng(6).uniform(0, 2, inst.J).astype(np.float32)
+    grad = np.empty(inst.J, dtype=np.float32)
+    import ctypes
+
+    ev = dl.dualip_dual_grad_host(P.h, lam.ctypes.data, 1e-2, grad.ctypes.data, dl._stream())
+    eo = Po.eval(lam.astype(np.float64), 1e-2)
+    tol = GRAD_RTOL * (np.abs(eo.ax) + np.abs(inst.b)) + 1e-6
+    assert np.all(np.abs(grad - eo.grad) <= tol)
+    assert abs(ev.dual_obj - eo.dual) <= OBJ_RTOL * abs(eo.dual)
+    del ctypes
+
+
+def test_invalid_inputs_are_rejected(dl):
+    import torch
+
+    inst = synth.config("c1")
+    bad = synth.Instance(inst.off, inst.dst.copy(), inst.c, inst.a, inst.b, inst.J)
+    bad.dst[17] = inst.J  # out of range
+    with pytest.raises(dl.DualipError) as ei:
+        dl.Problem.from_instance(bad)
+    assert ei.value.status == dl.DUALIP_EINVAL
+    nan = synth.Instance(inst.off, inst.dst, inst.c.copy(), inst.a, inst.b, inst.J)
+    nan.c[3] = np.nan
+    with pytest.raises(dl.DualipError):
+        dl.Problem.from_instance(nan)
+    P = dl.Problem.from_instance(inst)
+    lam = torch.zeros(inst.J, device="cuda")
+    for g in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(dl.DualipError):
+            P.dual_grad(lam, g)
+    # the handle stays usable after rejected calls
+    check_eval(dl, inst, np.zeros(inst.J), 0.1, P=P)
+
+
+def test_device_inputs(dl):
+    import torch
+
+    inst = synth.config("c2", scale=0.005)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    P = dl.Problem(t(inst.off), t(inst.dst), t(inst.c), t(inst.a), t(inst.b), inst.J)
+    check_eval(dl, inst, np.random.default_rng(8).uniform(0, 1, inst.J), 1e-2, P=P)
+
+
+def test_full_c2_parity(dl):
+    """The benchmark workload at full size, in the benchmark's launch configuration."""
+    inst = synth.config("c2")
+    rng = np.random.default_rng(9)
+    lam = rng.uniform(0, 1.0, inst.J)
+    check_eval(dl, inst, lam, 1e-3)
