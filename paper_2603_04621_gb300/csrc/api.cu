@@ -208,7 +208,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
       (e = dev_alloc(P, &P.tiles, tiles.size())) || (e = dev_alloc(P, &P.tile_e, tiles.size())) ||
       (e = dev_alloc(P, &P.b_r, J)) || (e = dev_alloc(P, &P.orig_of, J)) ||
       (e = dev_alloc(P, &P.new_of, J)) || (e = dev_alloc(P, &P.mu_r, J)) ||
-      (e = dev_alloc(P, &P.y, J)) || (e = dev_alloc(P, &P.yerr, J)) ||
+      (e = dev_alloc(P, &P.y, J)) ||
       (e = dev_alloc(P, &P.part, 2 * (size_t)P.grid)) ||
       (e = dev_alloc(P, &P.epi_part, 2 * (size_t)P.epi_blocks)) ||
       (e = dev_alloc(P, &P.eval_dev, 8)) || (e = dev_alloc(P, &P.lam_stage, J)) ||
@@ -224,8 +224,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     return bail(cuda_fail(e, "allocating pinned memory"));
 
   // zero everything that must start at zero (padding included)
-  if ((e = cudaMemsetAsync(P.dst, 0, e_pad * 4, s)) || (e = cudaMemsetAsync(P.y, 0, J * 4, s)) ||
-      (e = cudaMemsetAsync(P.yerr, 0, J * 4, s)) ||
+  if ((e = cudaMemsetAsync(P.dst, 0, e_pad * 4, s)) || (e = cudaMemsetAsync(P.y, 0, J * 8, s)) ||
       (e = cudaMemsetAsync(P.status, 0, sizeof(DeviceStatus), s)))
     return bail(cuda_fail(e, "clearing problem memory"));
   if (P.c && ((e = cudaMemsetAsync(P.c, 0, e_pad * 4, s)) ||
@@ -301,6 +300,9 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   free_tmp();
 
   // edge values
+  unsigned absmax[2] = {0u, 0u};  // bit patterns of max |c|, max |a|
+  unsigned* counts_max = nullptr;
+  if ((e = cudaMalloc(&counts_max, 2 * sizeof(unsigned)))) return bail(cuda_fail(e, "allocating"));
   if (E > 0) {
     float *c_tmp = nullptr, *a_tmp = nullptr;
     const float *c_src = d->c, *a_src = d->a;
@@ -324,6 +326,11 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     }
     if ((e = launch_check_finite(c_src, E, P.status, s)) ||
         (e = launch_check_finite(a_src, E, P.status, s)) ||
+        (e = cudaMemsetAsync(counts_max, 0, 2 * sizeof(unsigned), s)) ||
+        (e = launch_absmax(c_src, E, counts_max, s)) ||
+        (e = launch_absmax(a_src, E, counts_max + 1, s)) ||
+        (e = cudaMemcpyAsync(absmax, counts_max, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             s)) ||
         (P.storage == DUALIP_EDGE_BF16 && (e = launch_pack_bf16(c_src, a_src, P.ca, E, s)))) {
       cudaStreamSynchronize(s);
       cudaFree(c_tmp);
@@ -334,7 +341,28 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     cudaFree(c_tmp);
     cudaFree(a_tmp);
   }
-  if ((e = cudaStreamSynchronize(s))) return bail(cuda_fail(e, "building the problem"));
+  e = cudaStreamSynchronize(s);
+  cudaFree(counts_max);
+  if (e) return bail(cuda_fail(e, "building the problem"));
+  // Fixed-point scales 2^exp: every sum they carry stays below 2^61.
+  //   A x:      |(A x)_j| <= max in-degree * max |a|      (x <= 1)
+  //   c^T x:    |sum c x| <= I * max |c|                  (sum_j x_ij <= 1)
+  //   sum w x^2 <= I * max w                              (sum_j x_ij^2 <= 1)
+  {
+    float mc, ma;
+    std::memcpy(&mc, &absmax[0], 4);
+    std::memcpy(&ma, &absmax[1], 4);
+    const unsigned maxcnt = cnt.empty() ? 0u : *std::max_element(cnt.begin(), cnt.end());
+    const double mw = P.weighted ? std::max(1.0, (double)ma * ma) : 1.0;
+    auto pick = [](double bound) {
+      int ex = 0;
+      std::frexp(std::max(bound, 1e-30), &ex);  // bound < 2^ex
+      return std::max(-100, std::min(100, 61 - ex));
+    };
+    P.exp_y = pick((double)maxcnt * ma);
+    P.exp_c = pick((double)std::max<int64_t>(I, 1) * mc);
+    P.exp_w = pick((double)std::max<int64_t>(I, 1) * mw);
+  }
   DeviceStatus st{};
   if ((e = cudaMemcpy(&st, P.status, sizeof(st), cudaMemcpyDeviceToHost)))
     return bail(cuda_fail(e, "reading the device status"));

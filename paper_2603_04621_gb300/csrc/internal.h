@@ -13,13 +13,25 @@ namespace dualip {
 
 // ---- pass geometry --------------------------------------------------------
 // A tile is a run of whole sources whose edges fit one shared-memory stage.
-constexpr int kTileEdges = 2048;       // edge capacity of a stage
-constexpr int kTileSources = 512;      // source capacity of a stage
-constexpr int kStages = 4;             // depth of the staging ring
-constexpr int kConsumerWarps = 16;     // warps that project sources
+#ifndef DUALIP_TILE_EDGES
+#define DUALIP_TILE_EDGES 3072
+#endif
+#ifndef DUALIP_STAGES
+#define DUALIP_STAGES 3
+#endif
+#ifndef DUALIP_CONSUMER_WARPS
+#define DUALIP_CONSUMER_WARPS 16
+#endif
+#ifndef DUALIP_PRIV_DESTS
+#define DUALIP_PRIV_DESTS 4096
+#endif
+constexpr int kTileEdges = DUALIP_TILE_EDGES;       // edge capacity of a stage
+constexpr int kTileSources = 512;                    // source capacity of a stage
+constexpr int kStages = DUALIP_STAGES;               // depth of the staging ring
+constexpr int kConsumerWarps = DUALIP_CONSUMER_WARPS;  // warps that project sources
 constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
 constexpr int kMaxCachedDests = 10240; // hot destinations whose mu lives in smem
-constexpr int kMaxPrivDests = 4096;    // hot destinations accumulated in smem
+constexpr int kMaxPrivDests = DUALIP_PRIV_DESTS;  // hot destinations accumulated in smem
 constexpr int kRegMaxDeg = 128;        // degrees held in registers (4 per lane)
 constexpr int kStageEdgeSlots = kTileEdges + 8;      // + 16-byte alignment slack
 constexpr int kStageOffSlots = kTileSources + 4;
@@ -55,8 +67,9 @@ struct PassParams {
   const float* gamma_dev;  // if non-null, gamma is read here (solver)
   float gamma;
   // outputs / scratch
-  float* y;               // [J] FP32 sum of a x (renumbered)
-  float* yerr;            // [J] compensation of y
+  unsigned long long* y;  // [J] A x in fixed point (two's complement, scale 2^exp_y)
+  float sy, sc, sw;       // 2^exp_y, 2^exp_c, 2^exp_w
+  double inv_sc, inv_sw;  // 2^-exp_c, 2^-exp_w
   double* part;           // [gridDim.x * 2] per-CTA (sum c x, sum w x^2)
   float* x_out;           // [E] optional primal output (edge order)
   DeviceStatus* status;
@@ -69,8 +82,8 @@ struct EpiParams {
   const float* b_r;        // [J] budgets, renumbered
   const float* mu_r;       // [J] renumbered dual point used by the pass
   const float* D;          // [J] optional row scale in caller numbering (solver)
-  float* y;                // [J] reset to 0 after reading
-  float* yerr;             // [J] reset to 0 after reading
+  unsigned long long* y;   // [J] fixed-point A x, reset to 0 after reading
+  double inv_sy;           // 2^-exp_y
   float* grad;             // [J] caller numbering: D (A x - b) (D = 1 if null)
   const double* part;      // per-CTA partials of the pass
   int npart;
@@ -102,8 +115,8 @@ struct Problem {
   int32_t* orig_of = nullptr;
   int32_t* new_of = nullptr;
   float* mu_r = nullptr;
-  float* y = nullptr;
-  float* yerr = nullptr;
+  unsigned long long* y = nullptr;  // fixed-point accumulator of A x
+  int exp_y = 0, exp_c = 0, exp_w = 0;  // fixed-point scales (powers of two)
   double* part = nullptr;
   int epi_blocks = 0;
   double* epi_part = nullptr;
@@ -135,6 +148,7 @@ cudaError_t launch_histogram(const int32_t* dst, int64_t E, int32_t J, unsigned*
 cudaError_t launch_pack_bf16(const float* c, const float* a, uint32_t* ca, int64_t E,
                              cudaStream_t s);
 cudaError_t launch_check_finite(const float* v, int64_t n, DeviceStatus* st, cudaStream_t s);
+cudaError_t launch_absmax(const float* v, int64_t n, unsigned* out, cudaStream_t s);
 
 // solve.cu
 void solve_ctx_free(Problem& P);

@@ -116,30 +116,25 @@ __device__ __forceinline__ float two_sum_err(float u, float v, float s) {
   const float bp = __fsub_rn(s, u);
   return __fadd_rn(__fsub_rn(u, __fsub_rn(s, bp)), __fsub_rn(v, bp));
 }
-// r = -(c + a m) as hi + lo (TwoProduct by FMA, then TwoSum)
+// r = -(c + a m) as a normalised pair hi + lo with hi = fl(r): TwoProduct by
+// FMA, TwoSum, then a final TwoSum so that |lo| <= ulp(hi) / 2 even when
+// c and a m cancel.
 __device__ __forceinline__ void score(float c, float a, float m, float& hi, float& lo) {
   const float p = __fmul_rn(a, m);
   const float pe = __fmaf_rn(a, m, -p);
   const float s = __fadd_rn(c, p);
   const float se = two_sum_err(c, p, s);
-  hi = -s;
-  lo = -__fadd_rn(se, pe);
+  const float h0 = -s, l0 = -__fadd_rn(se, pe);
+  hi = __fadd_rn(h0, l0);
+  lo = two_sum_err(h0, l0, hi);
 }
 
-struct Acc {  // FP32 running sum with an exact TwoSum compensation term
-  float s = 0.f, e = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float t = __fadd_rn(s, v);
-    e = __fadd_rn(e, two_sum_err(s, v, t));
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s + (double)e; }
-};
-
-__device__ __forceinline__ void comp_atomic_add(float* y, float* ye, float v) {
-  const float old = atomicAdd(y, v);
-  const float err = two_sum_err(old, v, __fadd_rn(old, v));
-  if (err != 0.f) atomicAdd(ye, err);
+// Fixed-point accumulation: v * 2^S is exact in FP32 (a power-of-two scale)
+// and is rounded once to an integer; integer adds are exact and independent
+// of their order, so A x and the objective partials are reproducible bit for
+// bit.  The scales are chosen at create so that no sum can exceed 2^61.
+__device__ __forceinline__ long long to_fixed(float v, float scale) {
+  return __float2ll_rn(__fmul_rn(v, scale));
 }
 
 // --------------------------------------------------------- smem layout ----
@@ -159,8 +154,7 @@ struct Layout {
   static constexpr size_t kStageBytes = kOffBytes + kEdgeArr * (BF16 ? 2 : 3);
   static constexpr size_t kMu = kStages * kStageBytes;
   static constexpr size_t kY = kMu + sizeof(float) * kMaxCachedDests;
-  static constexpr size_t kYe = kY + sizeof(float) * kMaxPrivDests;
-  static constexpr size_t kBars = kYe + sizeof(float) * kMaxPrivDests;
+  static constexpr size_t kBars = kY + sizeof(unsigned long long) * kMaxPrivDests;
   static constexpr size_t kInfo = kBars + sizeof(uint64_t) * 2 * kStages;
   static constexpr size_t kMisc = kInfo + sizeof(StageInfo) * kStages;
   static constexpr size_t kTotal = kMisc + 512;
@@ -222,23 +216,24 @@ struct GlobalView {
 };
 
 // ------------------------------------------------------ per-thread state ----
+// Read-only context of a pass (passed by value to out-of-line paths).
 struct Ctx {
   const float* mu_s;
   const float* mu_g;
   int h_mu;
-  float* y_s;
-  float* ye_s;
+  unsigned long long* y_s;
   int h_y;
-  float* y;
-  float* ye;
+  unsigned long long* y;
   float gamma, inv_gamma;
+  float sy, sc, sw;
   float* x_out;
-  Acc cx, wxx;
 
   __device__ __forceinline__ float mu(int j) const { return j < h_mu ? mu_s[j] : __ldg(mu_g + j); }
-  __device__ __forceinline__ void scatter(int j, float v) {
-    if (j < h_y) comp_atomic_add(y_s + j, ye_s + j, v);
-    else comp_atomic_add(y + j, ye + j, v);
+  __device__ __forceinline__ void scatter(int j, float v) const {
+    const unsigned long long q = (unsigned long long)to_fixed(v, sy);
+    if (q == 0ull) return;
+    if (j < h_y) atomicAdd(y_s + j, q);
+    else atomicAdd(y + j, q);
   }
 };
 
@@ -251,96 +246,119 @@ __device__ __forceinline__ float edge_alpha(const Ctx& cx, float w) {
   return W ? __frcp_rn(__fmul_rn(cx.gamma, w)) : cx.inv_gamma;
 }
 
-__device__ __forceinline__ void account(Ctx& cx, int j, float c, float a, float w, float x) {
-  cx.scatter(j, __fmul_rn(a, x));
-  cx.cx.add(__fmul_rn(c, x));
-  cx.wxx.add(__fmul_rn(w, __fmul_rn(x, x)));
+// Per-lane objective partials sum c x and sum w x^2, in fixed point.
+struct Sums {
+  long long cx = 0, wxx = 0;
+  __device__ __forceinline__ void account(const Ctx& c, int j, float cv, float a, float w,
+                                          float x) {
+    c.scatter(j, __fmul_rn(a, x));
+    cx += to_fixed(__fmul_rn(cv, x), c.sc);
+    wxx += to_fixed(__fmul_rn(w, __fmul_rn(x, x)), c.sw);
+  }
+  __device__ __forceinline__ void merge(const Sums& o) {
+    cx += o.cx;
+    wxx += o.wxx;
+  }
+};
+
+// ------------------------------------- group projection, registers ----
+// G lanes own one source (32/G sources per warp), each lane holds up to K of
+// its edges.  Every lane executes every shuffle (full mask; xor offsets stay
+// inside a group).
+template <int G>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+  for (int o = G / 2; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <int G>
+__device__ __forceinline__ void group_sum2(float& u, float& v) {
+#pragma unroll
+  for (int o = G / 2; o; o >>= 1) {
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+    v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
 }
 
-// ------------------------------------------ warp projection, registers ----
-template <int K, bool BF16, bool W>
-__device__ __forceinline__ void project_regs(const StageView<BF16>& sv, int base, int d,
-                                             int64_t e_glob, int lane, Ctx& cx) {
-  float hi[K], lo[K], rf[K], av[K], cv[K], al[K];
-  int jj[K];
-  float rmax = -CUDART_INF_F;
+template <int G>
+__device__ __forceinline__ int group_isum(int v) {
+#pragma unroll
+  for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The hot path: 32/G sources per warp, G lanes per source, K edges per lane
+// (degree <= G K).  Plain FP32 scores (FMA), one fused group reduction (max,
+// saturation sum, weighted bound), a per-lane count of the candidates near
+// the top, and x = 1 for a saturated source with a single candidate.
+// Returns (warp-uniform) bit q set for every source li + q of the batch that
+// is unsaturated or has near-ties at the top; those take the general path.
+template <int G, int K, bool BF16, bool W, bool MU_SMEM>
+__device__ __forceinline__ unsigned project_lean(const StageView<BF16>& sv, int li, int nsrc,
+                                                 int64_t a0, int lane, const Ctx& cx,
+                                                 Sums& acc) {
+  const int g = lane / G, l = lane % G;
+  const bool gvalid = g < nsrc;
+  const int lis = gvalid ? li + g : li;
+  const int64_t eb = sv.off[lis];
+  const int d = gvalid ? (int)(sv.off[lis + 1] - eb) : 0;
+  const int base = (int)(eb - a0);
+  float rf[K];
+  float rmax = -CUDART_INF_F, s0 = 0.f, m2 = -CUDART_INF_F;
+  // branch-free: out-of-range slots re-read the group's last edge (or the
+  // first staged slot of an empty group, still inside the stage) and are
+  // masked with -inf
+  const int dl = d > 0 ? d - 1 : 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int idx = lane + 32 * k;
-    if (idx < d) {
-      float c, a;
-      int j;
-      sv.edge(base + idx, j, c, a);
-      score(c, a, cx.mu(j), hi[k], lo[k]);
-      rf[k] = __fadd_rn(hi[k], lo[k]);
-      jj[k] = j;
-      cv[k] = c;
-      av[k] = a;
-    } else {
-      hi[k] = -CUDART_INF_F;
-      lo[k] = 0.f;
-      rf[k] = -CUDART_INF_F;
-      jj[k] = 0;
-      cv[k] = 0.f;
-      av[k] = 0.f;
-    }
+    const int idx = l + G * k;
+    const bool v = idx < d;
+    float c, a;
+    int j;
+    sv.edge(base + (v ? idx : dl), j, c, a);
+    const float m = MU_SMEM ? cx.mu_s[j] : cx.mu(j);
+    rf[k] = v ? -__fmaf_rn(a, m, c) : -CUDART_INF_F;
     rmax = fmaxf(rmax, rf[k]);
-  }
-  rmax = warp_max(rmax);
-  float x[K];
-  if (rmax <= 0.f) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) x[k] = 0.f;
-  } else {
-    float s0 = 0.f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      al[k] = edge_alpha<W>(cx, edge_w<W>(av[k]));
-      s0 += rf[k] > 0.f ? __fmul_rn(al[k], rf[k]) : 0.f;
-    }
-    s0 = warp_sum(s0);
-    if (s0 <= 1.f) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) x[k] = rf[k] > 0.f ? __fmul_rn(al[k], rf[k]) : 0.f;
+    if (W) {
+      const float w = edge_w<W>(a);
+      s0 += rf[k] > 0.f ? __fmul_rn(edge_alpha<W>(cx, w), rf[k]) : 0.f;
+      m2 = fmaxf(m2, __fsub_rn(rf[k], __fmul_rn(cx.gamma, w)));
     } else {
-      // shifted scores d_e = r_e - rmax; threshold t in [LB, 0)
-      float dd[K];
-      float lb = -CUDART_INF_F;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        dd[k] = (lane + 32 * k < d) ? __fadd_rn(__fsub_rn(hi[k], rmax), lo[k]) : -CUDART_INF_F;
-        lb = fmaxf(lb, __fsub_rn(dd[k], W ? __fmul_rn(cx.gamma, edge_w<W>(av[k])) : cx.gamma));
-      }
-      lb = warp_max(lb);
-      float theta = lb, t = lb, nprev = -1.f;
-      for (int it = 0; it <= d; ++it) {
-        float sr = 0.f, sa = 0.f, n = 0.f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          if (dd[k] > theta) {
-            sr += W ? __fmul_rn(al[k], dd[k]) : dd[k];
-            sa += W ? al[k] : 0.f;
-            n += 1.f;
-          }
-        }
-        sr = warp_sum(sr);
-        n = warp_sum(n);
-        if (W) sa = warp_sum(sa);
-        if (n == nprev) break;
-        t = W ? __fdiv_rn(sr - 1.f, sa) : __fdiv_rn(sr - cx.gamma, n);
-        nprev = n;
-        theta = fmaxf(theta, t);
-      }
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        x[k] = dd[k] > t ? __fmul_rn(al[k], __fsub_rn(dd[k], t)) : 0.f;
+      s0 += fmaxf(rf[k], 0.f);
     }
   }
+#pragma unroll
+  for (int o = G / 2; o; o >>= 1) {
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    if (W) m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+  }
+  if (!W) s0 = __fmul_rn(s0, cx.inv_gamma);
+  const int mode = rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2);
+  const float lb = (W ? fminf(__fsub_rn(m2, rmax), 0.f) : -cx.gamma) - ldexpf(fabsf(rmax), -20);
+  int lc = 0, kc = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    if (x[k] > 0.f) account(cx, jj[k], cv[k], av[k], edge_w<W>(av[k]), x[k]);
-    if (cx.x_out != nullptr && lane + 32 * k < d) cx.x_out[e_glob + lane + 32 * k] = x[k];
+    if (__fsub_rn(rf[k], rmax) > lb) {
+      ++lc;
+      kc = k;
+    }
   }
+  if (mode != 2) lc = 0;
+  const int cnt = group_isum<G>(lc);
+  if (mode == 2 && cnt == 1 && lc == 1) {
+    // the only candidate is the only active edge: x = 1 exactly
+    float c, a;
+    int j;
+    sv.edge(base + l + G * kc, j, c, a);
+    acc.account(cx, j, c, a, edge_w<W>(a), 1.f);
+  }
+  const unsigned lead =
+      __ballot_sync(0xffffffffu, l == 0 && gvalid && (mode == 1 || (mode == 2 && cnt > 1)));
+  unsigned need = 0u;
+#pragma unroll
+  for (int q = 0; q < 32 / G; ++q) need |= ((lead >> (G * q)) & 1u) << q;
+  return need;
 }
 
 // ------------------------- multi-pass projection (any degree, any group) ----
@@ -353,9 +371,11 @@ struct WarpGroup {
   __device__ __forceinline__ float sum(float v) const { return warp_sum(v); }
   __device__ __forceinline__ float max(float v) const { return warp_max(v); }
 };
-template <bool BF16, bool W, class View, class G>
-__device__ void project_multipass(const View& v, int64_t base, int64_t d, int64_t e_glob,
-                                  const G& g, Ctx& cx) {
+template <bool BF16, bool W, class View>
+__device__ __forceinline__ void project_multipass(const View& v, int64_t base, int64_t d,
+                                                  int64_t e_glob, int lane, const Ctx& cx,
+                                                  Sums& acc) {
+  const WarpGroup g{lane};
   auto load = [&](int64_t k, int& j, float& c, float& a, float& hi, float& lo) {
     v.edge(base + k, j, c, a);
     score(c, a, cx.mu(j), hi, lo);
@@ -422,24 +442,26 @@ __device__ void project_multipass(const View& v, int64_t base, int64_t d, int64_
       const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
       x = dk > t ? __fmul_rn(al, __fsub_rn(dk, t)) : 0.f;
     }
-    if (x > 0.f) account(cx, j, c, a, w, x);
+    if (x > 0.f) acc.account(cx, j, c, a, w, x);
     if (cx.x_out != nullptr) cx.x_out[e_glob + k] = x;
   }
 }
 
 // ----------------------------------------------------------- the pass ----
-template <bool BF16, bool W>
+// MU_SMEM: every destination's mu is cached in shared memory (J <= the cache).
+// WRITE_X: the primal x is written for every edge (dualip_get_primal); every
+// source then takes the general path.
+template <bool BF16, bool W, bool MU_SMEM, bool WRITE_X>
 __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p) {
   using L = Layout<BF16>;
   extern __shared__ __align__(128) unsigned char smem[];
   float* mu_s = reinterpret_cast<float*>(smem + L::kMu);
-  float* y_s = reinterpret_cast<float*>(smem + L::kY);
-  float* ye_s = reinterpret_cast<float*>(smem + L::kYe);
+  unsigned long long* y_s = reinterpret_cast<unsigned long long*>(smem + L::kY);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBars);
   uint64_t* empty = full + kStages;
   StageInfo* info = reinterpret_cast<StageInfo*>(smem + L::kInfo);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + L::kMisc);
-  double* dred = reinterpret_cast<double*>(smem + L::kMisc + 16);  // 2 doubles per warp
+  long long* dred = reinterpret_cast<long long*>(smem + L::kMisc + 16);  // 2 per warp
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -455,24 +477,23 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     fence_mbar_init();
   }
   for (int j = tid; j < p.h_mu; j += blockDim.x) mu_s[j] = p.mu_r[j];
-  for (int j = tid; j < p.h_y; j += blockDim.x) {
-    y_s[j] = 0.f;
-    ye_s[j] = 0.f;
-  }
+  for (int j = tid; j < p.h_y; j += blockDim.x) y_s[j] = 0ull;
   __syncthreads();
 
   Ctx cx;
+  Sums acc;
   cx.mu_s = mu_s;
   cx.mu_g = p.mu_r;
   cx.h_mu = p.h_mu;
   cx.y_s = y_s;
-  cx.ye_s = ye_s;
   cx.h_y = p.h_y;
   cx.y = p.y;
-  cx.ye = p.yerr;
+  cx.sy = p.sy;
+  cx.sc = p.sc;
+  cx.sw = p.sw;
   cx.gamma = p.gamma_dev ? *p.gamma_dev : p.gamma;
   cx.inv_gamma = __frcp_rn(cx.gamma);
-  cx.x_out = p.x_out;
+  cx.x_out = WRITE_X ? p.x_out : nullptr;
 
   if (warp == 0) {
     // ------------------------------------------------------ producer ----
@@ -560,6 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
   } else {
     // ------------------------------------------------------ consumers ----
     const int cw = warp - 1;
+    int rot = 0;  // batches seen in earlier tiles, mod kConsumerWarps
     int64_t it = 0;
     for (int64_t t = t_begin; t < t_end; ++t, ++it) {
       const int s = (int)(it % kStages);
@@ -572,21 +594,61 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         // stage straight from global memory; no cross-warp barrier is used
         if (cw == (int)(t % kConsumerWarps)) {
           GlobalView<BF16> gv{p.dst, p.c, p.a, p.ca};
-          project_multipass<BF16, W>(gv, si.e0, si.e1 - si.e0, si.e0, WarpGroup{lane}, cx);
+          project_multipass<BF16, W>(gv, si.e0, si.e1 - si.e0, si.e0, lane, cx, acc);
         }
       } else {
         const StageView<BF16> sv = stage_view<BF16>(smem, s);
-        for (int64_t src = si.s0 + cw; src < si.s1; src += kConsumerWarps) {
-          const int li = (int)(src - si.o0);
-          const int64_t eb = sv.off[li], ee = sv.off[li + 1];
-          const int d = (int)(ee - eb);
-          const int base = (int)(eb - si.a0);
-          if (d <= 0) continue;
-          if (d <= 32) project_regs<1, BF16, W>(sv, base, d, eb, lane, cx);
-          else if (d <= 64) project_regs<2, BF16, W>(sv, base, d, eb, lane, cx);
-          else if (d <= 96) project_regs<3, BF16, W>(sv, base, d, eb, lane, cx);
-          else if (d <= kRegMaxDeg) project_regs<4, BF16, W>(sv, base, d, eb, lane, cx);
-          else project_multipass<BF16, W>(sv, (int64_t)base, (int64_t)d, eb, WarpGroup{lane}, cx);
+        const int nsrc = (int)(si.s1 - si.s0);
+        const int li0 = (int)(si.s0 - si.o0);
+        // sources are taken in batches of four: four 8-lane groups when every
+        // degree is <= 64, else pairs of 16-lane groups (<= 128), else one
+        // warp per source (<= 256); what the lean path leaves (unsaturated
+        // sources, near-ties, larger degrees, the primal output) goes through
+        // the multi-pass path.  Batches are dealt round robin across tiles
+        // (rot), so a tile whose batch count is not a multiple of the warp
+        // count loads different warps.
+        const int nb = (nsrc + 3) >> 2;
+        const int first = (cw - rot + kConsumerWarps) % kConsumerWarps;
+        rot = (rot + nb) % kConsumerWarps;
+        for (int bi = first; bi < nb; bi += kConsumerWarps) {
+          const int li = li0 + 4 * bi;
+          const int n4 = nsrc - 4 * bi < 4 ? nsrc - 4 * bi : 4;
+          int dg[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            dg[q] = q < n4 ? (int)(sv.off[li + q + 1] - sv.off[li + q]) : 0;
+          const int dm = max(max(dg[0], dg[1]), max(dg[2], dg[3]));
+          if (dm <= 0) continue;
+          unsigned need = 0u;
+          if (WRITE_X) {
+            need = (1u << n4) - 1u;
+          } else if (dm <= 64) {
+            need = project_lean<8, 8, BF16, W, MU_SMEM>(sv, li, n4, si.a0, lane, cx, acc);
+          } else {
+            for (int h = 0; h < n4; h += 2) {
+              const int np = n4 - h < 2 ? n4 - h : 2;
+              const int d2 = np == 2 ? max(dg[h], dg[h + 1]) : dg[h];
+              if (d2 <= 0) continue;
+              if (d2 <= 128) {
+                need |= project_lean<16, 8, BF16, W, MU_SMEM>(sv, li + h, np, si.a0, lane, cx,
+                                                              acc) << h;
+                continue;
+              }
+              for (int q = h; q < h + np; ++q) {
+                if (dg[q] <= 0) continue;
+                if (dg[q] <= 256)
+                  need |= project_lean<32, 8, BF16, W, MU_SMEM>(sv, li + q, 1, si.a0, lane, cx,
+                                                                acc) << q;
+                else need |= 1u << q;
+              }
+            }
+          }
+          while (need) {
+            const int q = __ffs(need) - 1;
+            need &= need - 1u;
+            const int64_t eb = sv.off[li + q];
+            project_multipass<BF16, W>(sv, eb - si.a0, (int64_t)dg[q], eb, lane, cx, acc);
+          }
         }
       }
       __syncwarp();
@@ -597,12 +659,11 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
 
   // flush the shared-memory accumulators of the hot destinations
   for (int j = tid; j < p.h_y; j += blockDim.x) {
-    const float v = y_s[j], e = ye_s[j];
-    if (v != 0.f) comp_atomic_add(p.y + j, p.yerr + j, v);
-    if (e != 0.f) atomicAdd(p.yerr + j, e);
+    const unsigned long long v = y_s[j];
+    if (v != 0ull) atomicAdd(p.y + j, v);
   }
-  // per-CTA objective partials, FP64 from here on
-  double v0 = cx.cx.value(), v1 = cx.wxx.value();
+  // per-CTA objective partials: exact integer sums, converted once
+  long long v0 = acc.cx, v1 = acc.wxx;
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     v0 += __shfl_xor_sync(0xffffffffu, v0, o);
@@ -614,13 +675,13 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
   }
   __syncthreads();
   if (tid == 0) {
-    double s0 = 0.0, s1 = 0.0;
+    long long s0 = 0, s1 = 0;
     for (int w = 0; w < kThreads / 32; ++w) {
       s0 += dred[2 * w];
       s1 += dred[2 * w + 1];
     }
-    p.part[2 * blockIdx.x] = s0;
-    p.part[2 * blockIdx.x + 1] = s1;
+    p.part[2 * blockIdx.x] = (double)s0 * p.inv_sc;
+    p.part[2 * blockIdx.x + 1] = (double)s1 * p.inv_sw;
   }
 }
 
@@ -641,9 +702,8 @@ __global__ void epilogue_kernel(EpiParams q) {
   double s_mug = 0.0, s_inf = 0.0;
   for (int64_t jr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; jr < q.J;
        jr += (int64_t)gridDim.x * blockDim.x) {
-    const double ax = (double)q.y[jr] + (double)q.yerr[jr];
-    q.y[jr] = 0.f;
-    q.yerr[jr] = 0.f;
+    const double ax = (double)(long long)q.y[jr] * q.inv_sy;
+    q.y[jr] = 0ull;
     const double gj = ax - (double)q.b_r[jr];
     const int jo = q.orig_of ? q.orig_of[jr] : (int)jr;
     s_mug += (double)q.mu_r[jr] * gj;
@@ -676,16 +736,30 @@ __global__ void epilogue_kernel(EpiParams q) {
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // fixed-order FP64 combination of every partial (strided per thread, then a
+  // fixed shuffle tree and a fixed warp order)
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = threadIdx.x; k < q.npart; k += blockDim.x) {
+    v[0] += q.part[2 * k];
+    v[1] += q.part[2 * k + 1];
+  }
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+    v[2] += q.epi_part[2 * k];
+    v[3] += q.epi_part[2 * k + 1];
+  }
+  for (int o = 16; o; o >>= 1)
+    for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  __shared__ double fin[4][32];
+  if (lane == 0)
+    for (int i = 0; i < 4; ++i) fin[i][w] = v[i];
+  __syncthreads();
   if (threadIdx.x == 0) {
-    // fixed-order FP64 combination of every partial
     double cxs = 0.0, wxx = 0.0, mug = 0.0, inf = 0.0;
-    for (int k = 0; k < q.npart; ++k) {
-      cxs += q.part[2 * k];
-      wxx += q.part[2 * k + 1];
-    }
-    for (unsigned k = 0; k < gridDim.x; ++k) {
-      mug += q.epi_part[2 * k];
-      inf += q.epi_part[2 * k + 1];
+    for (int k = 0; k < nw; ++k) {
+      cxs += fin[0][k];
+      wxx += fin[1][k];
+      mug += fin[2][k];
+      inf += fin[3][k];
     }
     const double gamma = q.gamma_dev ? (double)*q.gamma_dev : q.gamma;
     const double reg = 0.5 * gamma * wxx;
@@ -743,6 +817,15 @@ __global__ void check_finite_kernel(const float* __restrict__ v, int64_t n, Devi
   }
 }
 
+__global__ void absmax_kernel(const float* __restrict__ v, int64_t n, unsigned* out) {
+  unsigned m = 0u;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(fabsf(v[e])));
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 int grid_for(int64_t n, int threads, int cap) {
   int64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -756,23 +839,24 @@ size_t pass_smem_bytes(int storage) {
   return storage == DUALIP_EDGE_BF16 ? Layout<true>::kTotal : Layout<false>::kTotal;
 }
 
-cudaError_t configure_pass_kernels() {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(dualgrad_pass_kernel<false, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Layout<false>::kTotal)))
-    return e;
-  if ((e = cudaFuncSetAttribute(dualgrad_pass_kernel<false, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Layout<false>::kTotal)))
-    return e;
-  if ((e = cudaFuncSetAttribute(dualgrad_pass_kernel<true, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Layout<true>::kTotal)))
-    return e;
-  return cudaFuncSetAttribute(dualgrad_pass_kernel<true, true>,
+template <bool BF16, bool W, bool MU, bool WX>
+static cudaError_t set_smem() {
+  return cudaFuncSetAttribute(dualgrad_pass_kernel<BF16, W, MU, WX>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Layout<true>::kTotal);
+                              (int)Layout<BF16>::kTotal);
+}
+
+cudaError_t configure_pass_kernels() {
+  const cudaError_t es[] = {
+      set_smem<false, false, false, false>(), set_smem<false, false, true, false>(),
+      set_smem<false, true, false, false>(),  set_smem<false, true, true, false>(),
+      set_smem<true, false, false, false>(),  set_smem<true, false, true, false>(),
+      set_smem<true, true, false, false>(),   set_smem<true, true, true, false>(),
+      set_smem<false, false, false, true>(),  set_smem<false, true, false, true>(),
+      set_smem<true, false, false, true>(),   set_smem<true, true, false, true>()};
+  for (cudaError_t e : es)
+    if (e != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 cudaError_t launch_prep(const Problem& P, const float* lambda, const float* D, cudaStream_t s) {
@@ -800,19 +884,45 @@ cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, f
   p.gamma_dev = gamma_dev;
   p.gamma = gamma;
   p.y = P.y;
-  p.yerr = P.yerr;
+  p.sy = ldexpf(1.f, P.exp_y);
+  p.sc = ldexpf(1.f, P.exp_c);
+  p.sw = ldexpf(1.f, P.exp_w);
+  p.inv_sc = ldexp(1.0, -P.exp_c);
+  p.inv_sw = ldexp(1.0, -P.exp_w);
   p.part = P.part;
   p.x_out = x_out;
   p.status = P.status;
   const bool bf16 = P.storage == DUALIP_EDGE_BF16;
+  const bool mu_all = P.J <= P.h_mu;
   const size_t smem = pass_smem_bytes(P.storage);
-  if (bf16) {
-    if (P.weighted) dualgrad_pass_kernel<true, true><<<P.grid, kThreads, smem, s>>>(p);
-    else dualgrad_pass_kernel<true, false><<<P.grid, kThreads, smem, s>>>(p);
+  const dim3 grid(P.grid), block(kThreads);
+#define DUALIP_LAUNCH(B, W, M, X) dualgrad_pass_kernel<B, W, M, X><<<grid, block, smem, s>>>(p)
+  if (x_out) {
+    if (bf16) {
+      if (P.weighted) DUALIP_LAUNCH(true, true, false, true);
+      else DUALIP_LAUNCH(true, false, false, true);
+    } else {
+      if (P.weighted) DUALIP_LAUNCH(false, true, false, true);
+      else DUALIP_LAUNCH(false, false, false, true);
+    }
+  } else if (bf16) {
+    if (P.weighted) {
+      if (mu_all) DUALIP_LAUNCH(true, true, true, false);
+      else DUALIP_LAUNCH(true, true, false, false);
+    } else {
+      if (mu_all) DUALIP_LAUNCH(true, false, true, false);
+      else DUALIP_LAUNCH(true, false, false, false);
+    }
   } else {
-    if (P.weighted) dualgrad_pass_kernel<false, true><<<P.grid, kThreads, smem, s>>>(p);
-    else dualgrad_pass_kernel<false, false><<<P.grid, kThreads, smem, s>>>(p);
+    if (P.weighted) {
+      if (mu_all) DUALIP_LAUNCH(false, true, true, false);
+      else DUALIP_LAUNCH(false, true, false, false);
+    } else {
+      if (mu_all) DUALIP_LAUNCH(false, false, true, false);
+      else DUALIP_LAUNCH(false, false, false, false);
+    }
   }
+#undef DUALIP_LAUNCH
   return cudaGetLastError();
 }
 
@@ -825,7 +935,7 @@ cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const
   q.mu_r = P.mu_r;
   q.D = D;
   q.y = P.y;
-  q.yerr = P.yerr;
+  q.inv_sy = ldexp(1.0, -P.exp_y);
   q.grad = grad;
   q.part = P.part;
   q.npart = P.grid;
@@ -853,6 +963,11 @@ cudaError_t launch_renumber(const int32_t* dst_in, int32_t* dst_out, const int32
 cudaError_t launch_pack_bf16(const float* c, const float* a, uint32_t* ca, int64_t E,
                              cudaStream_t s) {
   pack_bf16_kernel<<<grid_for(E, 256, 8192), 256, 0, s>>>(c, a, ca, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const float* v, int64_t n, unsigned* out, cudaStream_t s) {
+  absmax_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(v, n, out);
   return cudaGetLastError();
 }
 

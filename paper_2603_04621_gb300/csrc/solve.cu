@@ -116,12 +116,29 @@ __global__ void solve_norms_kernel(int32_t J, SolveState* st, Vecs v, double* pa
     last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
   double sdy = 0.0, sdg = 0.0;
-  for (unsigned i = 0; i < gridDim.x; ++i) {
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
     sdy += part[2 * i];
     sdg += part[2 * i + 1];
+  }
+  for (int o = 16; o; o >>= 1) {
+    sdy += __shfl_xor_sync(0xffffffffu, sdy, o);
+    sdg += __shfl_xor_sync(0xffffffffu, sdg, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    red[0][w] = sdy;
+    red[1][w] = sdg;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  sdy = 0.0;
+  sdg = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+    sdy += red[0][i];
+    sdg += red[1][i];
   }
   const double gk = gamma_at(*st, k);
   const double eta_max = st->max_step * gk / st->gamma0;

@@ -125,7 +125,7 @@ def test_many_tiny_sources_and_all_hot(dl):
 
 
 def test_large_lambda_and_empty_rows(dl):
-    inst = synth.matching(3000, 400, 13, ("poisson", 20, 0, 60), "zipf")
+    inst = synth.matching(3000, 20_000, 13, ("poisson", 20, 0, 60), "zipf")
     assert np.bincount(inst.dst, minlength=inst.J).min() == 0  # some rows are empty
     P, Po, grad, ev = check_eval(dl, inst, np.full(inst.J, 1e6), 1e-3)
     assert ev["primal_obj"] == 0.0 and ev["reg"] == 0.0
