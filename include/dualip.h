@@ -207,6 +207,32 @@ void dualip_solve_opts_default(dualip_solve_opts* opts);
 dualip_status dualip_solve(dualip_problem* p, const dualip_solve_opts* opts, float* lambda_inout,
                            dualip_solve_result* result, double* trace, void* stream);
 
+/*
+ * Dual evaluation that allocates nothing (the paper has no counterpart; this
+ * is for callers that cannot allocate device memory: a framework whose
+ * caching allocator or pre-planned arena owns the device, a request path that
+ * cannot take cudaMalloc's implicit synchronisation, a device that is nearly
+ * full).  It needs no handle: it reads the caller's device arrays directly,
+ * laid out as in dualip_problem_desc (FP32 c and a), and computes the same
+ * grad and scalars as dualip_dual_grad.
+ *   num_sources I >= 0; num_dests J, 1 <= J <= 1048576 (larger J: DUALIP_EINVAL)
+ *   src_offsets [I+1], dst [E], c [E], a [E], b [J], lambda [J]: device, read only
+ *   primal_scaling 0 / 1 as in dualip_problem_desc; gamma > 0
+ *   grad [J] device, written; out_dev [5] device doubles in dualip_eval order
+ * Scratch lives in one fixed __device__ array of about 8 MiB that every GPU
+ * loading the library holds until exit.  The first call on a device looks up
+ * that array's address and should come before any stream capture.  Every call
+ * shares the array (it is cleared at the start of each call), so calls whose
+ * work overlaps on the GPU race: serialise them.  Nothing is synchronised;
+ * an edge whose destination is outside [0, J) is skipped and turns every
+ * scalar in out_dev into NaN.  The offsets are trusted as given.
+ */
+dualip_status dualip_dual_grad_noalloc(int64_t num_sources, int32_t num_dests,
+                                       const int64_t* src_offsets, const int32_t* dst,
+                                       const float* c, const float* a, const float* b,
+                                       int32_t primal_scaling, const float* lambda, double gamma,
+                                       float* grad, double* out_dev, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* dualip_last_error(void);
 

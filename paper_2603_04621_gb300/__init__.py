@@ -28,7 +28,7 @@ EXPORTS = [
     "dualip_create", "dualip_destroy", "dualip_dual_grad", "dualip_dual_grad_async",
     "dualip_dual_grad_host", "dualip_get_primal", "dualip_check_device_status",
     "dualip_get_info", "dualip_solve_opts_default", "dualip_solve", "dualip_last_error",
-    "dualip_profile_enable", "dualip_profile_collect",
+    "dualip_profile_enable", "dualip_profile_collect", "dualip_dual_grad_noalloc",
 ]
 
 
@@ -108,6 +108,9 @@ def lib() -> ctypes.CDLL:
         pd = ctypes.POINTER(dbl)
         L.dualip_profile_collect.argtypes = [vp, pd, pd, pd, ctypes.POINTER(i32)]
         L.dualip_profile_collect.restype = st
+        L.dualip_dual_grad_noalloc.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, vp, dbl, vp,
+                                               vp, vp]
+        L.dualip_dual_grad_noalloc.restype = st
         L.dualip_last_error.argtypes = []
         L.dualip_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -195,6 +198,15 @@ def dualip_profile_collect(h: int) -> dict:
     _check(lib().dualip_profile_collect(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                         ctypes.byref(n)))
     return dict(ms_prologue=a.value, ms_pass=b.value, ms_epilogue=c.value, count=n.value)
+
+
+def dualip_dual_grad_noalloc(I: int, J: int, off_ptr: int, dst_ptr: int, c_ptr: int, a_ptr: int,
+                             b_ptr: int, primal_scaling: int, lam_ptr: int, gamma: float,
+                             grad_ptr: int, out_ptr: int, stream: int) -> None:
+    """The allocation-free evaluation (all pointers are device pointers)."""
+    _check(lib().dualip_dual_grad_noalloc(I, J, off_ptr, dst_ptr, c_ptr, a_ptr, b_ptr,
+                                          int(primal_scaling), lam_ptr, gamma, grad_ptr,
+                                          out_ptr, stream))
 
 
 def dualip_solve_opts_default() -> SolveOpts:
