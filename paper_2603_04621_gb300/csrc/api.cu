@@ -215,8 +215,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
       (e = dev_alloc(P, &P.grad_stage, J)) || (e = dev_alloc(P, &P.status, 1)))
     return bail(cuda_fail(e, "allocating problem memory"));
   if (P.storage == DUALIP_EDGE_F32) {
-    if ((e = dev_alloc(P, &P.c, e_pad)) || (e = dev_alloc(P, &P.a, e_pad)))
-      return bail(cuda_fail(e, "allocating edge memory"));
+    if ((e = dev_alloc(P, &P.ca2, e_pad))) return bail(cuda_fail(e, "allocating edge memory"));
   } else {
     if ((e = dev_alloc(P, &P.ca, e_pad))) return bail(cuda_fail(e, "allocating edge memory"));
   }
@@ -227,8 +226,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   if ((e = cudaMemsetAsync(P.dst, 0, e_pad * 4, s)) || (e = cudaMemsetAsync(P.y, 0, J * 8, s)) ||
       (e = cudaMemsetAsync(P.status, 0, sizeof(DeviceStatus), s)))
     return bail(cuda_fail(e, "clearing problem memory"));
-  if (P.c && ((e = cudaMemsetAsync(P.c, 0, e_pad * 4, s)) ||
-              (e = cudaMemsetAsync(P.a, 0, e_pad * 4, s))))
+  if (P.ca2 && (e = cudaMemsetAsync(P.ca2, 0, e_pad * 8, s)))
     return bail(cuda_fail(e, "clearing edge memory"));
   if (P.ca && (e = cudaMemsetAsync(P.ca, 0, e_pad * 4, s)))
     return bail(cuda_fail(e, "clearing edge memory"));
@@ -306,13 +304,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   if (E > 0) {
     float *c_tmp = nullptr, *a_tmp = nullptr;
     const float *c_src = d->c, *a_src = d->a;
-    if (P.storage == DUALIP_EDGE_F32) {
-      if ((e = cudaMemcpyAsync(P.c, d->c, 4 * (size_t)E, h2d, s)) ||
-          (e = cudaMemcpyAsync(P.a, d->a, 4 * (size_t)E, h2d, s)))
-        return bail(cuda_fail(e, "uploading c and a"));
-      c_src = P.c;
-      a_src = P.a;
-    } else if (!d->inputs_on_device) {
+    if (!d->inputs_on_device) {
       if ((e = cudaMalloc(&c_tmp, 4 * (size_t)E)) || (e = cudaMalloc(&a_tmp, 4 * (size_t)E)) ||
           (e = cudaMemcpyAsync(c_tmp, d->c, 4 * (size_t)E, h2d, s)) ||
           (e = cudaMemcpyAsync(a_tmp, d->a, 4 * (size_t)E, h2d, s))) {
@@ -331,7 +323,8 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
         (e = launch_absmax(a_src, E, counts_max + 1, s)) ||
         (e = cudaMemcpyAsync(absmax, counts_max, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost,
                              s)) ||
-        (P.storage == DUALIP_EDGE_BF16 && (e = launch_pack_bf16(c_src, a_src, P.ca, E, s)))) {
+        (P.storage == DUALIP_EDGE_BF16 && (e = launch_pack_bf16(c_src, a_src, P.ca, E, s))) ||
+        (P.storage == DUALIP_EDGE_F32 && (e = launch_pack_f32(c_src, a_src, P.ca2, E, s)))) {
       cudaStreamSynchronize(s);
       cudaFree(c_tmp);
       cudaFree(a_tmp);
@@ -344,24 +337,15 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   e = cudaStreamSynchronize(s);
   cudaFree(counts_max);
   if (e) return bail(cuda_fail(e, "building the problem"));
-  // Fixed-point scales 2^exp: every sum they carry stays below 2^61.
-  //   A x:      |(A x)_j| <= max in-degree * max |a|      (x <= 1)
-  //   c^T x:    |sum c x| <= I * max |c|                  (sum_j x_ij <= 1)
-  //   sum w x^2 <= I * max w                              (sum_j x_ij^2 <= 1)
+  // Fixed-point scale 2^exp_y of A x: |(A x)_j| <= max in-degree * max |a|
+  // (x <= 1), kept below 2^61 so no sum can overflow.
   {
-    float mc, ma;
-    std::memcpy(&mc, &absmax[0], 4);
+    float ma;
     std::memcpy(&ma, &absmax[1], 4);
     const unsigned maxcnt = cnt.empty() ? 0u : *std::max_element(cnt.begin(), cnt.end());
-    const double mw = P.weighted ? std::max(1.0, (double)ma * ma) : 1.0;
-    auto pick = [](double bound) {
-      int ex = 0;
-      std::frexp(std::max(bound, 1e-30), &ex);  // bound < 2^ex
-      return std::max(-100, std::min(100, 61 - ex));
-    };
-    P.exp_y = pick((double)maxcnt * ma);
-    P.exp_c = pick((double)std::max<int64_t>(I, 1) * mc);
-    P.exp_w = pick((double)std::max<int64_t>(I, 1) * mw);
+    int ex = 0;
+    std::frexp(std::max((double)maxcnt * ma, 1e-30), &ex);  // bound < 2^ex
+    P.exp_y = std::max(-100, std::min(100, 61 - ex));
   }
   DeviceStatus st{};
   if ((e = cudaMemcpy(&st, P.status, sizeof(st), cudaMemcpyDeviceToHost)))

@@ -17,17 +17,24 @@ namespace dualip {
 #define DUALIP_TILE_EDGES 3072
 #endif
 #ifndef DUALIP_STAGES
-#define DUALIP_STAGES 3
+#define DUALIP_STAGES 4
 #endif
 #ifndef DUALIP_CONSUMER_WARPS
 #define DUALIP_CONSUMER_WARPS 16
 #endif
+#ifndef DUALIP_L2_PREFETCH_TILES
+#define DUALIP_L2_PREFETCH_TILES 0
+#endif
 #ifndef DUALIP_PRIV_DESTS
-#define DUALIP_PRIV_DESTS 4096
+#define DUALIP_PRIV_DESTS 2048
 #endif
 constexpr int kTileEdges = DUALIP_TILE_EDGES;       // edge capacity of a stage
-constexpr int kTileSources = 512;                    // source capacity of a stage
+#ifndef DUALIP_TILE_SOURCES
+#define DUALIP_TILE_SOURCES 256
+#endif
+constexpr int kTileSources = DUALIP_TILE_SOURCES;   // source capacity of a stage
 constexpr int kStages = DUALIP_STAGES;               // depth of the staging ring
+constexpr int kL2PrefetchTiles = DUALIP_L2_PREFETCH_TILES;  // L2 prefetch distance (tiles)
 constexpr int kConsumerWarps = DUALIP_CONSUMER_WARPS;  // warps that project sources
 constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
 constexpr int kMaxCachedDests = 10240; // hot destinations whose mu lives in smem
@@ -52,8 +59,7 @@ struct PassParams {
   // edges
   const int64_t* off;     // [I+1 (+ padding)]
   const int32_t* dst;     // [E_pad] renumbered destinations
-  const float* c;         // [E_pad] (f32 storage)
-  const float* a;         // [E_pad] (f32 storage)
+  const float2* ca2;      // [E_pad] (c, a) pairs (f32 storage)
   const uint32_t* ca;     // [E_pad] packed bf16 (c | a << 16) (bf16 storage)
   const int64_t* tiles;   // [ntiles+1] first source of each tile
   const int64_t* tile_e;  // [ntiles+1] first edge of each tile (= off[tiles[t]])
@@ -68,8 +74,7 @@ struct PassParams {
   float gamma;
   // outputs / scratch
   unsigned long long* y;  // [J] A x in fixed point (two's complement, scale 2^exp_y)
-  float sy, sc, sw;       // 2^exp_y, 2^exp_c, 2^exp_w
-  double inv_sc, inv_sw;  // 2^-exp_c, 2^-exp_w
+  int ey;                 // fixed-point exponent of A x (scale 2^ey)
   double* part;           // [gridDim.x * 2] per-CTA (sum c x, sum w x^2)
   float* x_out;           // [E] optional primal output (edge order)
   DeviceStatus* status;
@@ -106,8 +111,7 @@ struct Problem {
   // device buffers (owned)
   int64_t* off = nullptr;
   int32_t* dst = nullptr;
-  float* c = nullptr;
-  float* a = nullptr;
+  float2* ca2 = nullptr;  // (c, a) pairs, FP32 storage
   uint32_t* ca = nullptr;
   int64_t* tiles = nullptr;
   int64_t* tile_e = nullptr;
@@ -116,7 +120,7 @@ struct Problem {
   int32_t* new_of = nullptr;
   float* mu_r = nullptr;
   unsigned long long* y = nullptr;  // fixed-point accumulator of A x
-  int exp_y = 0, exp_c = 0, exp_w = 0;  // fixed-point scales (powers of two)
+  int exp_y = 0;                    // fixed-point scale of A x (power of two)
   double* part = nullptr;
   int epi_blocks = 0;
   double* epi_part = nullptr;
@@ -145,6 +149,8 @@ cudaError_t launch_renumber(const int32_t* dst_in, int32_t* dst_out, const int32
                             int64_t E, int32_t J, DeviceStatus* st, cudaStream_t s);
 cudaError_t launch_histogram(const int32_t* dst, int64_t E, int32_t J, unsigned* counts,
                              DeviceStatus* st, cudaStream_t s);
+cudaError_t launch_pack_f32(const float* c, const float* a, float2* ca2, int64_t E,
+                            cudaStream_t s);
 cudaError_t launch_pack_bf16(const float* c, const float* a, uint32_t* ca, int64_t E,
                              cudaStream_t s);
 cudaError_t launch_check_finite(const float* v, int64_t n, DeviceStatus* st, cudaStream_t s);

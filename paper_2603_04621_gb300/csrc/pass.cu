@@ -75,6 +75,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -130,9 +133,9 @@ __device__ __forceinline__ void score(float c, float a, float m, float& hi, floa
 }
 
 // Fixed-point accumulation: v * 2^S is exact in FP32 (a power-of-two scale)
-// and is rounded once to an integer; integer adds are exact and independent
-// of their order, so A x and the objective partials are reproducible bit for
-// bit.  The scales are chosen at create so that no sum can exceed 2^61.
+// and is rounded once to a 64-bit integer; integer adds are exact and
+// independent of their order, so A x is reproducible bit for bit.  The scale
+// is chosen at create so that no sum can exceed 2^61.
 __device__ __forceinline__ long long to_fixed(float v, float scale) {
   return __float2ll_rn(__fmul_rn(v, scale));
 }
@@ -162,12 +165,13 @@ struct Layout {
   static_assert(kTotal <= 227 * 1024, "shared memory budget");
 };
 
+// Stage layout: offsets | dst (4 B per slot) | c, a (8 B per slot: FP32 pairs,
+// or 4 B: packed bf16 pair c | a << 16).
 template <bool BF16>
 struct StageView {
   const int64_t* off;
   const int32_t* dst;
-  const float* c;
-  const float* a;
+  const float2* ca2;
   const uint32_t* ca;
   __device__ __forceinline__ void edge(int k, int& j, float& cv, float& av) const {
     j = dst[k];
@@ -176,8 +180,9 @@ struct StageView {
       cv = __uint_as_float(u << 16);
       av = __uint_as_float(u & 0xffff0000u);
     } else {
-      cv = c[k];
-      av = a[k];
+      const float2 v = ca2[k];
+      cv = v.x;
+      av = v.y;
     }
   }
 };
@@ -189,8 +194,7 @@ __device__ __forceinline__ StageView<BF16> stage_view(unsigned char* smem, int s
   StageView<BF16> v;
   v.off = reinterpret_cast<const int64_t*>(base);
   v.dst = reinterpret_cast<const int32_t*>(base + L::kOffBytes);
-  v.c = reinterpret_cast<const float*>(base + L::kOffBytes + L::kEdgeArr);
-  v.a = BF16 ? nullptr : reinterpret_cast<const float*>(base + L::kOffBytes + 2 * L::kEdgeArr);
+  v.ca2 = reinterpret_cast<const float2*>(base + L::kOffBytes + L::kEdgeArr);
   v.ca = reinterpret_cast<const uint32_t*>(base + L::kOffBytes + L::kEdgeArr);
   return v;
 }
@@ -199,8 +203,7 @@ __device__ __forceinline__ StageView<BF16> stage_view(unsigned char* smem, int s
 template <bool BF16>
 struct GlobalView {
   const int32_t* dst;
-  const float* c;
-  const float* a;
+  const float2* ca2;
   const uint32_t* ca;
   __device__ __forceinline__ void edge(int64_t k, int& j, float& cv, float& av) const {
     j = __ldg(dst + k);
@@ -209,8 +212,9 @@ struct GlobalView {
       cv = __uint_as_float(u << 16);
       av = __uint_as_float(u & 0xffff0000u);
     } else {
-      cv = __ldg(c + k);
-      av = __ldg(a + k);
+      const float2 v = __ldg(ca2 + k);
+      cv = v.x;
+      av = v.y;
     }
   }
 };
@@ -225,15 +229,26 @@ struct Ctx {
   int h_y;
   unsigned long long* y;
   float gamma, inv_gamma;
-  float sy, sc, sw;
+  float sy;  // 2^ey: fixed-point scale of A x
   float* x_out;
 
   __device__ __forceinline__ float mu(int j) const { return j < h_mu ? mu_s[j] : __ldg(mu_g + j); }
+  // y_j += v in fixed point.  A shared bin is a little-endian (low, high)
+  // pair of 32-bit words: the low word takes a returning 32-bit atomic add,
+  // its carry goes into the high word, so the 64-bit total stays exact
+  // without 64-bit shared-memory atomics.  Global bins use 64-bit reductions.
   __device__ __forceinline__ void scatter(int j, float v) const {
-    const unsigned long long q = (unsigned long long)to_fixed(v, sy);
-    if (q == 0ull) return;
-    if (j < h_y) atomicAdd(y_s + j, q);
-    else atomicAdd(y + j, q);
+    const long long q = to_fixed(v, sy);
+    if (q == 0) return;
+    if (j < h_y) {
+      unsigned* w = reinterpret_cast<unsigned*>(y_s + j);
+      const unsigned lo = (unsigned)q;
+      const unsigned old = atomicAdd(w, lo);
+      const unsigned hi = (unsigned)(q >> 32) + (old + lo < old ? 1u : 0u);
+      if (hi) atomicAdd(w + 1, hi);
+    } else {
+      atomicAdd(y + j, (unsigned long long)q);
+    }
   }
 };
 
@@ -246,18 +261,25 @@ __device__ __forceinline__ float edge_alpha(const Ctx& cx, float w) {
   return W ? __frcp_rn(__fmul_rn(cx.gamma, w)) : cx.inv_gamma;
 }
 
-// Per-lane objective partials sum c x and sum w x^2, in fixed point.
+// Per-lane objective partials sum c x and sum w x^2: FP32 running sums with
+// an exact TwoSum compensation each (FMA-pipe work only); the per-lane order
+// is fixed, so the partials are reproducible.
+struct Acc {
+  float s = 0.f, e = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = __fadd_rn(s, v);
+    e = __fadd_rn(e, two_sum_err(s, v, t));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
 struct Sums {
-  long long cx = 0, wxx = 0;
+  Acc cx, wxx;
   __device__ __forceinline__ void account(const Ctx& c, int j, float cv, float a, float w,
                                           float x) {
     c.scatter(j, __fmul_rn(a, x));
-    cx += to_fixed(__fmul_rn(cv, x), c.sc);
-    wxx += to_fixed(__fmul_rn(w, __fmul_rn(x, x)), c.sw);
-  }
-  __device__ __forceinline__ void merge(const Sums& o) {
-    cx += o.cx;
-    wxx += o.wxx;
+    cx.add(__fmul_rn(cv, x));
+    wxx.add(__fmul_rn(w, __fmul_rn(x, x)));
   }
 };
 
@@ -287,78 +309,164 @@ __device__ __forceinline__ int group_isum(int v) {
   return v;
 }
 
-// The hot path: 32/G sources per warp, G lanes per source, K edges per lane
-// (degree <= G K).  Plain FP32 scores (FMA), one fused group reduction (max,
-// saturation sum, weighted bound), a per-lane count of the candidates near
-// the top, and x = 1 for a saturated source with a single candidate.
-// Returns (warp-uniform) bit q set for every source li + q of the batch that
-// is unsaturated or has near-ties at the top; those take the general path.
-template <int G, int K, bool BF16, bool W, bool MU_SMEM>
-__device__ __forceinline__ unsigned project_lean(const StageView<BF16>& sv, int li, int nsrc,
-                                                 int64_t a0, int lane, const Ctx& cx,
-                                                 Sums& acc) {
-  const int g = lane / G, l = lane % G;
-  const bool gvalid = g < nsrc;
-  const int lis = gvalid ? li + g : li;
-  const int64_t eb = sv.off[lis];
-  const int d = gvalid ? (int)(sv.off[lis + 1] - eb) : 0;
-  const int base = (int)(eb - a0);
-  float rf[K];
-  float rmax = -CUDART_INF_F, s0 = 0.f, m2 = -CUDART_INF_F;
-  // branch-free: out-of-range slots re-read the group's last edge (or the
-  // first staged slot of an empty group, still inside the stage) and are
-  // masked with -inf
-  const int dl = d > 0 ? d - 1 : 0;
+// Four consecutive staged edges from a 16-byte-aligned stage index e.
+template <bool BF16>
+__device__ __forceinline__ void load4(const StageView<BF16>& sv, int e, int (&j)[4],
+                                      float (&c)[4], float (&a)[4]) {
+  const int4 jv = *reinterpret_cast<const int4*>(sv.dst + e);
+  j[0] = jv.x;
+  j[1] = jv.y;
+  j[2] = jv.z;
+  j[3] = jv.w;
+  if (BF16) {
+    const uint4 u = *reinterpret_cast<const uint4*>(sv.ca + e);
+    const unsigned uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int idx = l + G * k;
-    const bool v = idx < d;
-    float c, a;
-    int j;
-    sv.edge(base + (v ? idx : dl), j, c, a);
-    const float m = MU_SMEM ? cx.mu_s[j] : cx.mu(j);
-    rf[k] = v ? -__fmaf_rn(a, m, c) : -CUDART_INF_F;
-    rmax = fmaxf(rmax, rf[k]);
-    if (W) {
-      const float w = edge_w<W>(a);
-      s0 += rf[k] > 0.f ? __fmul_rn(edge_alpha<W>(cx, w), rf[k]) : 0.f;
-      m2 = fmaxf(m2, __fsub_rn(rf[k], __fmul_rn(cx.gamma, w)));
-    } else {
-      s0 += fmaxf(rf[k], 0.f);
+    for (int i = 0; i < 4; ++i) {
+      c[i] = __uint_as_float(uu[i] << 16);
+      a[i] = __uint_as_float(uu[i] & 0xffff0000u);
+    }
+  } else {
+    const float4 p0 = *reinterpret_cast<const float4*>(sv.ca2 + e);
+    const float4 p1 = *reinterpret_cast<const float4*>(sv.ca2 + e + 2);
+    c[0] = p0.x;
+    a[0] = p0.y;
+    c[1] = p0.z;
+    a[1] = p0.w;
+    c[2] = p1.x;
+    a[2] = p1.y;
+    c[3] = p1.z;
+    a[3] = p1.w;
+  }
+}
+
+// The hot path: 32/G sources per warp, G lanes per source.  A source's edges
+// are covered by a window aligned down to a multiple of 4 stage slots; each
+// lane reads S runs of 4 consecutive edges with 128-bit shared loads (window
+// 4 G S slots; the caller guarantees (base mod 4) + degree fits).  Plain FP32
+// scores (FMA); the group reduction keeps the two largest scores (and, with
+// primal scaling, the saturation sum and the weighted bound).  A saturated
+// source whose second score is below the candidate bound has a single
+// candidate, which takes x = 1 exactly.  Each lane passes its group's source
+// as (stage slot of the first edge, degree; 0 = no source).  Returns, per
+// group, whether the source is unsaturated or has near-ties at the top: those
+// take the general path.
+template <int G, int S, bool BF16, bool W, bool MU_SMEM>
+__device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base, int d,
+                                             int lane, const Ctx& cx, Sums& acc) {
+  constexpr int K = 4 * S;
+  const int g = lane / G, l = lane % G;
+  const bool gvalid = d > 0;
+  const int ws = base & ~3;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (G * g));
+  float rf[K];
+  float m1 = -CUDART_INF_F, m2 = -CUDART_INF_F, s0 = 0.f, mb = -CUDART_INF_F;
+  int kb = 0;
+#pragma unroll
+  for (int st = 0; st < S; ++st) {
+    const int e = ws + 4 * (l + G * st);
+    int jv[4];
+    float cv[4], av[4];
+    load4<BF16>(sv, e, jv, cv, av);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = 4 * st + i;
+      const bool v = (unsigned)(e + i - base) < (unsigned)d;
+      const int j = v ? jv[i] : 0;
+      const float m = MU_SMEM ? cx.mu_s[j] : cx.mu(j);
+      const float r = v ? -__fmaf_rn(av[i], m, cv[i]) : -CUDART_INF_F;
+      rf[k] = r;
+      if (W) {
+        const float w = edge_w<W>(av[i]);
+        s0 += r > 0.f ? __fmul_rn(edge_alpha<W>(cx, w), r) : 0.f;
+        mb = fmaxf(mb, __fsub_rn(r, __fmul_rn(cx.gamma, w)));
+      } else {
+        m2 = fmaxf(m2, fminf(m1, r));
+        kb = r > m1 ? k : kb;
+      }
+      m1 = fmaxf(m1, r);
     }
   }
+  const float lm1 = m1;  // this lane's own maximum
 #pragma unroll
   for (int o = G / 2; o; o >>= 1) {
-    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-    if (W) m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-  }
-  if (!W) s0 = __fmul_rn(s0, cx.inv_gamma);
-  const int mode = rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2);
-  const float lb = (W ? fminf(__fsub_rn(m2, rmax), 0.f) : -cx.gamma) - ldexpf(fabsf(rmax), -20);
-  int lc = 0, kc = 0;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (__fsub_rn(rf[k], rmax) > lb) {
-      ++lc;
-      kc = k;
+    const float p1 = __shfl_xor_sync(0xffffffffu, m1, o);
+    if (W) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    } else {
+      const float p2 = __shfl_xor_sync(0xffffffffu, m2, o);
+      m2 = fmaxf(fmaxf(m2, p2), fminf(m1, p1));
     }
+    m1 = fmaxf(m1, p1);
   }
-  if (mode != 2) lc = 0;
-  const int cnt = group_isum<G>(lc);
-  if (mode == 2 && cnt == 1 && lc == 1) {
+  const float rmax = m1;
+  int mode;
+  float lb;
+  bool lone = false;
+  if (W) {
+    mode = rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2);
+    lb = fminf(__fsub_rn(mb, rmax), 0.f) - ldexpf(fabsf(rmax), -20);
+    int lc = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (__fsub_rn(rf[k], rmax) > lb) {
+        ++lc;
+        kb = k;
+      }
+    }
+    if (mode != 2) lc = 0;
+    const int cnt = group_isum<G>(lc);
+    lone = mode == 2 && cnt == 1;
+    if (lc != 1) kb = -1;  // the owner is the lane holding the candidate
+  } else {
+    // rmax > gamma alone makes sum r_+ / gamma > 1: saturated.  Otherwise
+    // (rare) the saturation sum decides.
+    mode = rmax <= 0.f ? 0 : 2;
+    if (__any_sync(0xffffffffu, gvalid && rmax > 0.f && rmax <= cx.gamma)) {
+      float t0 = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) t0 += fmaxf(rf[k], 0.f);
+#pragma unroll
+      for (int o = G / 2; o; o >>= 1) t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+      if (rmax > 0.f && __fmul_rn(t0, cx.inv_gamma) <= 1.f) mode = 1;
+    }
+    lb = -cx.gamma - ldexpf(fabsf(rmax), -20);
+    lone = mode == 2 && __fsub_rn(m2, rmax) <= lb;
+    if (lm1 != rmax) kb = -1;  // the owner holds the group maximum
+  }
+  if (lone && kb >= 0) {
     // the only candidate is the only active edge: x = 1 exactly
     float c, a;
     int j;
-    sv.edge(base + l + G * kc, j, c, a);
+    sv.edge(ws + 4 * (l + G * (kb >> 2)) + (kb & 3), j, c, a);
     acc.account(cx, j, c, a, edge_w<W>(a), 1.f);
   }
-  const unsigned lead =
-      __ballot_sync(0xffffffffu, l == 0 && gvalid && (mode == 1 || (mode == 2 && cnt > 1)));
-  unsigned need = 0u;
+  return gvalid && (mode == 1 || (mode == 2 && !lone));
+}
+
+// Projects the batch sources selected by `mask` (bit q = source q of the
+// batch), 32/G at a time: group g takes the g-th remaining set bit.  bq / dq
+// are held by lane q: the stage slot of source q's first edge and its degree.
+// Returns the mask of sources that need the general path.
+template <int G, int S, bool BF16, bool W, bool MU_SMEM>
+__device__ __forceinline__ unsigned lean_over(const StageView<BF16>& sv, unsigned mask, int bq,
+                                              int dq, int lane, const Ctx& cx, Sums& acc) {
+  unsigned needm = 0u;
+  const int g = lane / G;
+  while (mask) {
+    unsigned m = mask;
+    for (int r = 0; r < g; ++r) m &= m - 1u;
+    const int q = m ? __ffs(m) - 1 : -1;
+    const int qs = q < 0 ? 0 : q;
+    const int b = __shfl_sync(0xffffffffu, bq, qs);
+    const int dd = __shfl_sync(0xffffffffu, dq, qs);
+    const bool nd = project_lean<G, S, BF16, W, MU_SMEM>(sv, b, q >= 0 ? dd : 0, lane, cx, acc);
+    needm |= __reduce_or_sync(0xffffffffu, ((lane % G) == 0 && nd && q >= 0) ? (1u << q) : 0u);
 #pragma unroll
-  for (int q = 0; q < 32 / G; ++q) need |= ((lead >> (G * q)) & 1u) << q;
-  return need;
+    for (int r = 0; r < 32 / G; ++r) mask &= mask - 1u;
+  }
+  return needm;
 }
 
 // ------------------------- multi-pass projection (any degree, any group) ----
@@ -461,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
   uint64_t* empty = full + kStages;
   StageInfo* info = reinterpret_cast<StageInfo*>(smem + L::kInfo);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + L::kMisc);
-  long long* dred = reinterpret_cast<long long*>(smem + L::kMisc + 16);  // 2 per warp
+  double* dred = reinterpret_cast<double*>(smem + L::kMisc + 16);  // 2 per warp
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -488,9 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
   cx.y_s = y_s;
   cx.h_y = p.h_y;
   cx.y = p.y;
-  cx.sy = p.sy;
-  cx.sc = p.sc;
-  cx.sw = p.sw;
+  cx.sy = ldexpf(1.f, p.ey);
   cx.gamma = p.gamma_dev ? *p.gamma_dev : p.gamma;
   cx.inv_gamma = __frcp_rn(cx.gamma);
   cx.x_out = WRITE_X ? p.x_out : nullptr;
@@ -500,6 +606,26 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     // The warp fetches 32 tile descriptors per load; lane 0 waits and issues.
     int64_t it = 0;
     bool stop = false;
+    // L2 prefetch frontier: edges up to kL2PrefetchTiles tiles ahead of the
+    // tile being staged are requested into L2 (no shared memory involved),
+    // which keeps more of HBM's latency covered than the ring alone
+    const int64_t e_end = (p.tile_e[t_end] + 3) & ~int64_t(3);
+    int64_t pf = p.tile_e[t_begin] & ~int64_t(3);
+    auto prefetch_to = [&](int64_t target) {
+      target = target < e_end ? ((target + 3) & ~int64_t(3)) : e_end;
+      while (pf < target) {
+        const int64_t n = target - pf < (int64_t)kTileEdges ? target - pf : (int64_t)kTileEdges;
+        bulk_prefetch_l2(p.dst + pf, (uint32_t)n * 4u);
+        if (BF16) {
+          bulk_prefetch_l2(p.ca + pf, (uint32_t)n * 4u);
+        } else {
+          bulk_prefetch_l2(p.ca2 + pf, (uint32_t)n * 8u);
+        }
+        pf += n;
+      }
+    };
+    if (kL2PrefetchTiles > 0 && lane == 0 && t_begin < t_end)
+      prefetch_to(p.tile_e[t_begin] + (int64_t)kL2PrefetchTiles * kTileEdges);
     for (int64_t t0 = t_begin; t0 < t_end && !stop; t0 += 32) {
       const int64_t tl = t0 + lane < t_end ? t0 + lane : t_end;
       const int64_t my_s = p.tiles[tl], my_e = p.tile_e[tl];
@@ -543,15 +669,14 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
               const uint32_t bytes = no * 8u + ne * (BF16 ? 8u : 12u);
               mbar_arrive_expect_tx(&full[s], bytes);
               unsigned char* base = smem + (size_t)s * L::kStageBytes;
+              if (kL2PrefetchTiles > 0) prefetch_to(e0 + (int64_t)(kL2PrefetchTiles + 1) * kTileEdges);
               bulk_g2s(base, p.off + si.o0, no * 8u, &full[s]);
               if (ne) {
                 bulk_g2s(base + L::kOffBytes, p.dst + si.a0, ne * 4u, &full[s]);
                 if (BF16) {
                   bulk_g2s(base + L::kOffBytes + L::kEdgeArr, p.ca + si.a0, ne * 4u, &full[s]);
                 } else {
-                  bulk_g2s(base + L::kOffBytes + L::kEdgeArr, p.c + si.a0, ne * 4u, &full[s]);
-                  bulk_g2s(base + L::kOffBytes + 2 * L::kEdgeArr, p.a + si.a0, ne * 4u,
-                           &full[s]);
+                  bulk_g2s(base + L::kOffBytes + L::kEdgeArr, p.ca2 + si.a0, ne * 8u, &full[s]);
                 }
               }
             }
@@ -593,61 +718,52 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         // one warp (chosen by tile index) projects a source larger than a
         // stage straight from global memory; no cross-warp barrier is used
         if (cw == (int)(t % kConsumerWarps)) {
-          GlobalView<BF16> gv{p.dst, p.c, p.a, p.ca};
+          GlobalView<BF16> gv{p.dst, p.ca2, p.ca};
           project_multipass<BF16, W>(gv, si.e0, si.e1 - si.e0, si.e0, lane, cx, acc);
         }
       } else {
         const StageView<BF16> sv = stage_view<BF16>(smem, s);
         const int nsrc = (int)(si.s1 - si.s0);
         const int li0 = (int)(si.s0 - si.o0);
-        // sources are taken in batches of four: four 8-lane groups when every
-        // degree is <= 64, else pairs of 16-lane groups (<= 128), else one
-        // warp per source (<= 256); what the lean path leaves (unsaturated
-        // sources, near-ties, larger degrees, the primal output) goes through
-        // the multi-pass path.  Batches are dealt round robin across tiles
-        // (rot), so a tile whose batch count is not a multiple of the warp
-        // count loads different warps.
-        const int nb = (nsrc + 3) >> 2;
+        // Sources are taken in batches of eight.  The span of a source (stage
+        // slot of its first edge mod 4, plus its degree) picks the group
+        // width: 4 lanes (span <= 64, eight sources per warp), 8 (<= 128),
+        // 16 (<= 256), 32 (<= 512), else the multi-pass path.  Whatever the
+        // lean path leaves (unsaturated sources, near-ties, the primal output)
+        // goes through the multi-pass path.  Batches are dealt round robin
+        // across tiles (rot), so a tile whose batch count is not a multiple of
+        // the warp count loads different warps.
+        const int nb = (nsrc + 7) >> 3;
         const int first = (cw - rot + kConsumerWarps) % kConsumerWarps;
         rot = (rot + nb) % kConsumerWarps;
         for (int bi = first; bi < nb; bi += kConsumerWarps) {
-          const int li = li0 + 4 * bi;
-          const int n4 = nsrc - 4 * bi < 4 ? nsrc - 4 * bi : 4;
-          int dg[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            dg[q] = q < n4 ? (int)(sv.off[li + q + 1] - sv.off[li + q]) : 0;
-          const int dm = max(max(dg[0], dg[1]), max(dg[2], dg[3]));
-          if (dm <= 0) continue;
-          unsigned need = 0u;
+          const int li = li0 + 8 * bi;
+          const int n8 = nsrc - 8 * bi < 8 ? nsrc - 8 * bi : 8;
+          const int64_t oq = sv.off[li + (lane <= n8 ? lane : n8)];
+          const int64_t on = __shfl_down_sync(0xffffffffu, oq, 1);
+          const int dq = lane < n8 ? (int)(on - oq) : 0;
+          const int bq = (int)(oq - si.a0);
+          const int spq = dq > 0 ? (bq & 3) + dq : 0;
+          unsigned needm;
           if (WRITE_X) {
-            need = (1u << n4) - 1u;
-          } else if (dm <= 64) {
-            need = project_lean<8, 8, BF16, W, MU_SMEM>(sv, li, n4, si.a0, lane, cx, acc);
+            needm = __ballot_sync(0xffffffffu, dq > 0);
           } else {
-            for (int h = 0; h < n4; h += 2) {
-              const int np = n4 - h < 2 ? n4 - h : 2;
-              const int d2 = np == 2 ? max(dg[h], dg[h + 1]) : dg[h];
-              if (d2 <= 0) continue;
-              if (d2 <= 128) {
-                need |= project_lean<16, 8, BF16, W, MU_SMEM>(sv, li + h, np, si.a0, lane, cx,
-                                                              acc) << h;
-                continue;
-              }
-              for (int q = h; q < h + np; ++q) {
-                if (dg[q] <= 0) continue;
-                if (dg[q] <= 256)
-                  need |= project_lean<32, 8, BF16, W, MU_SMEM>(sv, li + q, 1, si.a0, lane, cx,
-                                                                acc) << q;
-                else need |= 1u << q;
-              }
-            }
+            const unsigned m64 = __ballot_sync(0xffffffffu, dq > 0 && spq <= 64);
+            const unsigned m128 = __ballot_sync(0xffffffffu, spq > 64 && spq <= 128);
+            const unsigned m256 = __ballot_sync(0xffffffffu, spq > 128 && spq <= 256);
+            const unsigned m512 = __ballot_sync(0xffffffffu, spq > 256 && spq <= 512);
+            needm = __ballot_sync(0xffffffffu, spq > 512);
+            if (m64) needm |= lean_over<4, 4, BF16, W, MU_SMEM>(sv, m64, bq, dq, lane, cx, acc);
+            if (m128) needm |= lean_over<8, 4, BF16, W, MU_SMEM>(sv, m128, bq, dq, lane, cx, acc);
+            if (m256) needm |= lean_over<16, 4, BF16, W, MU_SMEM>(sv, m256, bq, dq, lane, cx, acc);
+            if (m512) needm |= lean_over<32, 4, BF16, W, MU_SMEM>(sv, m512, bq, dq, lane, cx, acc);
           }
-          while (need) {
-            const int q = __ffs(need) - 1;
-            need &= need - 1u;
-            const int64_t eb = sv.off[li + q];
-            project_multipass<BF16, W>(sv, eb - si.a0, (int64_t)dg[q], eb, lane, cx, acc);
+          while (needm) {
+            const int q = __ffs(needm) - 1;
+            needm &= needm - 1u;
+            const int b = __shfl_sync(0xffffffffu, bq, q);
+            const int dd = __shfl_sync(0xffffffffu, dq, q);
+            project_multipass<BF16, W>(sv, (int64_t)b, (int64_t)dd, si.a0 + b, lane, cx, acc);
           }
         }
       }
@@ -662,8 +778,8 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     const unsigned long long v = y_s[j];
     if (v != 0ull) atomicAdd(p.y + j, v);
   }
-  // per-CTA objective partials: exact integer sums, converted once
-  long long v0 = acc.cx, v1 = acc.wxx;
+  // per-CTA objective partials, FP64 from here on (fixed order)
+  double v0 = acc.cx.value(), v1 = acc.wxx.value();
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     v0 += __shfl_xor_sync(0xffffffffu, v0, o);
@@ -675,13 +791,13 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
   }
   __syncthreads();
   if (tid == 0) {
-    long long s0 = 0, s1 = 0;
+    double s0 = 0.0, s1 = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) {
       s0 += dred[2 * w];
       s1 += dred[2 * w + 1];
     }
-    p.part[2 * blockIdx.x] = (double)s0 * p.inv_sc;
-    p.part[2 * blockIdx.x + 1] = (double)s1 * p.inv_sw;
+    p.part[2 * blockIdx.x] = s0;
+    p.part[2 * blockIdx.x + 1] = s1;
   }
 }
 
@@ -800,6 +916,13 @@ __global__ void renumber_kernel(const int32_t* __restrict__ in, int32_t* __restr
   }
 }
 
+__global__ void pack_f32_kernel(const float* __restrict__ c, const float* __restrict__ a,
+                                float2* __restrict__ ca2, int64_t E) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x)
+    ca2[e] = make_float2(c[e], a[e]);
+}
+
 __global__ void pack_bf16_kernel(const float* __restrict__ c, const float* __restrict__ a,
                                  uint32_t* __restrict__ ca, int64_t E) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
@@ -870,8 +993,7 @@ cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, f
   PassParams p;
   p.off = P.off;
   p.dst = P.dst;
-  p.c = P.c;
-  p.a = P.a;
+  p.ca2 = P.ca2;
   p.ca = P.ca;
   p.tiles = P.tiles;
   p.tile_e = P.tile_e;
@@ -884,11 +1006,7 @@ cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, f
   p.gamma_dev = gamma_dev;
   p.gamma = gamma;
   p.y = P.y;
-  p.sy = ldexpf(1.f, P.exp_y);
-  p.sc = ldexpf(1.f, P.exp_c);
-  p.sw = ldexpf(1.f, P.exp_w);
-  p.inv_sc = ldexp(1.0, -P.exp_c);
-  p.inv_sw = ldexp(1.0, -P.exp_w);
+  p.ey = P.exp_y;
   p.part = P.part;
   p.x_out = x_out;
   p.status = P.status;
@@ -957,6 +1075,12 @@ cudaError_t launch_histogram(const int32_t* dst, int64_t E, int32_t J, unsigned*
 cudaError_t launch_renumber(const int32_t* dst_in, int32_t* dst_out, const int32_t* new_of,
                             int64_t E, int32_t J, DeviceStatus* st, cudaStream_t s) {
   renumber_kernel<<<grid_for(E, 256, 8192), 256, 0, s>>>(dst_in, dst_out, new_of, E, J, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_f32(const float* c, const float* a, float2* ca2, int64_t E,
+                            cudaStream_t s) {
+  pack_f32_kernel<<<grid_for(E, 256, 8192), 256, 0, s>>>(c, a, ca2, E);
   return cudaGetLastError();
 }
 

@@ -195,12 +195,12 @@ __global__ void solve_final_kernel(int32_t J, Vecs v, const int32_t* __restrict_
 }
 
 // D_j = (sum_{e -> j} a_e^2 / w_e)^(-1/2), 1 for a zero row (Section 5.1)
-__global__ void row_norm_kernel(const int32_t* __restrict__ dst, const float* __restrict__ a,
+__global__ void row_norm_kernel(const int32_t* __restrict__ dst, const float2* __restrict__ ca2,
                                 const uint32_t* __restrict__ ca, int64_t E, int weighted,
                                 double* __restrict__ acc) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const float av = a ? a[e] : __uint_as_float(ca[e] & 0xffff0000u);
+    const float av = ca2 ? ca2[e].y : __uint_as_float(ca[e] & 0xffff0000u);
     double v = (double)av * (double)av;
     if (weighted) v = av != 0.f ? 1.0 : 0.0;
     if (v != 0.0) atomicAdd(acc + dst[e], v);
@@ -282,7 +282,7 @@ static cudaError_t ensure_row_scale(Problem& P, SolveCtx& C, int row_normalize, 
     e = cudaMemsetAsync(acc, 0, sizeof(double) * P.J, s);
     if (!e && P.E > 0) {
       const int64_t g = std::min<int64_t>((P.E + 255) / 256, 8192);
-      row_norm_kernel<<<(int)g, 256, 0, s>>>(P.dst, P.a, P.ca, P.E, P.weighted, acc);
+      row_norm_kernel<<<(int)g, 256, 0, s>>>(P.dst, P.ca2, P.ca, P.E, P.weighted, acc);
       e = cudaGetLastError();
     }
     if (!e) {
