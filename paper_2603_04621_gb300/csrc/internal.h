@@ -36,11 +36,16 @@ constexpr int kTileSources = DUALIP_TILE_SOURCES;   // source capacity of a stag
 constexpr int kStages = DUALIP_STAGES;               // depth of the staging ring
 constexpr int kL2PrefetchTiles = DUALIP_L2_PREFETCH_TILES;  // L2 prefetch distance (tiles)
 constexpr int kConsumerWarps = DUALIP_CONSUMER_WARPS;  // warps that project sources
+#ifndef DUALIP_WAIT_HINT_NS
+#define DUALIP_WAIT_HINT_NS 0
+#endif
+constexpr unsigned kWaitHintNs = DUALIP_WAIT_HINT_NS;  // mbarrier suspend hint (0: none)
 constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
 constexpr int kMaxCachedDests = 10240; // hot destinations whose mu lives in smem
 constexpr int kMaxPrivDests = DUALIP_PRIV_DESTS;  // hot destinations accumulated in smem
 constexpr int kRegMaxDeg = 128;        // degrees held in registers (4 per lane)
 constexpr int kStageEdgeSlots = kTileEdges + 8;      // + 16-byte alignment slack
+constexpr int kDstPad = 512;                         // widest group window (32 lanes x 16)
 constexpr int kStageOffSlots = kTileSources + 4;
 
 // device error word bits

@@ -41,6 +41,55 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// explicit shared-space accesses on 32-bit shared addresses
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int lds_s32(uint32_t a) {
+  int v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int64_t lds_s64(uint32_t a) {
+  int64_t v;
+  asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float2 lds_f32x2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int4 lds_s32x4(uint32_t a) {
+  int4 v;
+  asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float4 lds_f32x4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t atoms_add_u32(uint32_t a, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v));
+  return old;
+}
+__device__ __forceinline__ void reds_add_u32(uint32_t a, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                : "memory");
@@ -56,15 +105,27 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// try_wait, optionally with a suspend-time hint (ns): a warp whose phase has
+// not completed may be suspended instead of spinning.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
+  if (kWaitHintNs > 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"((uint32_t)kWaitHintNs)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  }
   return ok != 0;
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
@@ -154,33 +215,38 @@ template <bool BF16>
 struct Layout {
   static constexpr size_t kOffBytes = sizeof(int64_t) * kStageOffSlots;
   static constexpr size_t kEdgeArr = sizeof(uint32_t) * kStageEdgeSlots;
-  static constexpr size_t kStageBytes = kOffBytes + kEdgeArr * (BF16 ? 2 : 3);
+  // dst carries kDstPad extra slots: a group's aligned window (at most 512
+  // slots) never leaves it, and every slot holds a valid destination id
+  // (zeroed at start, then earlier tiles' ids), so window slots outside the
+  // source need no index masking
+  static constexpr size_t kDstArr = sizeof(uint32_t) * (kStageEdgeSlots + kDstPad);
+  static constexpr size_t kStageBytes = kOffBytes + kDstArr + kEdgeArr * (BF16 ? 1 : 2);
   static constexpr size_t kMu = kStages * kStageBytes;
   static constexpr size_t kY = kMu + sizeof(float) * kMaxCachedDests;
   static constexpr size_t kBars = kY + sizeof(unsigned long long) * kMaxPrivDests;
   static constexpr size_t kInfo = kBars + sizeof(uint64_t) * 2 * kStages;
   static constexpr size_t kMisc = kInfo + sizeof(StageInfo) * kStages;
   static constexpr size_t kTotal = kMisc + 512;
-  static_assert(kOffBytes % 16 == 0 && kEdgeArr % 16 == 0, "16-byte staging");
+  static_assert(kOffBytes % 16 == 0 && kEdgeArr % 16 == 0 && kDstArr % 16 == 0,
+                "16-byte staging");
   static_assert(kTotal <= 227 * 1024, "shared memory budget");
 };
 
-// Stage layout: offsets | dst (4 B per slot) | c, a (8 B per slot: FP32 pairs,
-// or 4 B: packed bf16 pair c | a << 16).
+// Stage layout: offsets | dst (4 B per slot, padded) | c, a (8 B per slot:
+// FP32 pairs, or 4 B: packed bf16 pair c | a << 16).  Addresses are 32-bit
+// shared-space addresses, read with ld.shared.
 template <bool BF16>
 struct StageView {
-  const int64_t* off;
-  const int32_t* dst;
-  const float2* ca2;
-  const uint32_t* ca;
+  uint32_t off_a, dst_a, ca_a;
+  __device__ __forceinline__ int64_t off(int k) const { return lds_s64(off_a + 8u * k); }
   __device__ __forceinline__ void edge(int k, int& j, float& cv, float& av) const {
-    j = dst[k];
+    j = lds_s32(dst_a + 4u * k);
     if (BF16) {
-      const uint32_t u = ca[k];
+      const uint32_t u = lds_u32(ca_a + 4u * k);
       cv = __uint_as_float(u << 16);
       av = __uint_as_float(u & 0xffff0000u);
     } else {
-      const float2 v = ca2[k];
+      const float2 v = lds_f32x2(ca_a + 8u * k);
       cv = v.x;
       av = v.y;
     }
@@ -190,12 +256,11 @@ struct StageView {
 template <bool BF16>
 __device__ __forceinline__ StageView<BF16> stage_view(unsigned char* smem, int s) {
   using L = Layout<BF16>;
-  unsigned char* base = smem + (size_t)s * L::kStageBytes;
+  const uint32_t base = smem_u32(smem) + (uint32_t)((size_t)s * L::kStageBytes);
   StageView<BF16> v;
-  v.off = reinterpret_cast<const int64_t*>(base);
-  v.dst = reinterpret_cast<const int32_t*>(base + L::kOffBytes);
-  v.ca2 = reinterpret_cast<const float2*>(base + L::kOffBytes + L::kEdgeArr);
-  v.ca = reinterpret_cast<const uint32_t*>(base + L::kOffBytes + L::kEdgeArr);
+  v.off_a = base;
+  v.dst_a = base + (uint32_t)L::kOffBytes;
+  v.ca_a = base + (uint32_t)(L::kOffBytes + L::kDstArr);
   return v;
 }
 
@@ -220,19 +285,23 @@ struct GlobalView {
 };
 
 // ------------------------------------------------------ per-thread state ----
-// Read-only context of a pass (passed by value to out-of-line paths).
+// Read-only context of a pass.  Shared arrays are addressed by 32-bit
+// shared-space addresses.
 struct Ctx {
-  const float* mu_s;
+  uint32_t mu_a;  // shared mu cache (h_mu floats)
   const float* mu_g;
   int h_mu;
-  unsigned long long* y_s;
+  uint32_t y_a;   // shared fixed-point bins (h_y x 8 bytes)
   int h_y;
   unsigned long long* y;
   float gamma, inv_gamma;
   float sy;  // 2^ey: fixed-point scale of A x
   float* x_out;
 
-  __device__ __forceinline__ float mu(int j) const { return j < h_mu ? mu_s[j] : __ldg(mu_g + j); }
+  __device__ __forceinline__ float mu_smem(int j) const { return lds_f32(mu_a + 4u * j); }
+  __device__ __forceinline__ float mu(int j) const {
+    return j < h_mu ? mu_smem(j) : __ldg(mu_g + j);
+  }
   // y_j += v in fixed point.  A shared bin is a little-endian (low, high)
   // pair of 32-bit words: the low word takes a returning 32-bit atomic add,
   // its carry goes into the high word, so the 64-bit total stays exact
@@ -241,11 +310,11 @@ struct Ctx {
     const long long q = to_fixed(v, sy);
     if (q == 0) return;
     if (j < h_y) {
-      unsigned* w = reinterpret_cast<unsigned*>(y_s + j);
+      const uint32_t w = y_a + 8u * j;
       const unsigned lo = (unsigned)q;
-      const unsigned old = atomicAdd(w, lo);
+      const unsigned old = atoms_add_u32(w, lo);
       const unsigned hi = (unsigned)(q >> 32) + (old + lo < old ? 1u : 0u);
-      if (hi) atomicAdd(w + 1, hi);
+      if (hi) reds_add_u32(w + 4u, hi);
     } else {
       atomicAdd(y + j, (unsigned long long)q);
     }
@@ -275,6 +344,7 @@ struct Acc {
 };
 struct Sums {
   Acc cx, wxx;
+  int units = 0;  // lone unweighted candidates: each adds exactly 1 to sum w x^2
   __device__ __forceinline__ void account(const Ctx& c, int j, float cv, float a, float w,
                                           float x) {
     c.scatter(j, __fmul_rn(a, x));
@@ -313,22 +383,22 @@ __device__ __forceinline__ int group_isum(int v) {
 template <bool BF16>
 __device__ __forceinline__ void load4(const StageView<BF16>& sv, int e, int (&j)[4],
                                       float (&c)[4], float (&a)[4]) {
-  const int4 jv = *reinterpret_cast<const int4*>(sv.dst + e);
+  const int4 jv = lds_s32x4(sv.dst_a + 4u * e);
   j[0] = jv.x;
   j[1] = jv.y;
   j[2] = jv.z;
   j[3] = jv.w;
   if (BF16) {
-    const uint4 u = *reinterpret_cast<const uint4*>(sv.ca + e);
-    const unsigned uu[4] = {u.x, u.y, u.z, u.w};
+    const int4 u = lds_s32x4(sv.ca_a + 4u * e);
+    const unsigned uu[4] = {(unsigned)u.x, (unsigned)u.y, (unsigned)u.z, (unsigned)u.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       c[i] = __uint_as_float(uu[i] << 16);
       a[i] = __uint_as_float(uu[i] & 0xffff0000u);
     }
   } else {
-    const float4 p0 = *reinterpret_cast<const float4*>(sv.ca2 + e);
-    const float4 p1 = *reinterpret_cast<const float4*>(sv.ca2 + e + 2);
+    const float4 p0 = lds_f32x4(sv.ca_a + 8u * e);
+    const float4 p1 = lds_f32x4(sv.ca_a + 8u * e + 16u);
     c[0] = p0.x;
     a[0] = p0.y;
     c[1] = p0.z;
@@ -355,10 +425,9 @@ template <int G, int S, bool BF16, bool W, bool MU_SMEM>
 __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base, int d,
                                              int lane, const Ctx& cx, Sums& acc) {
   constexpr int K = 4 * S;
-  const int g = lane / G, l = lane % G;
+  const int l = lane % G;
   const bool gvalid = d > 0;
   const int ws = base & ~3;
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (G * g));
   float rf[K];
   float m1 = -CUDART_INF_F, m2 = -CUDART_INF_F, s0 = 0.f, mb = -CUDART_INF_F;
   int kb = 0;
@@ -372,8 +441,8 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
     for (int i = 0; i < 4; ++i) {
       const int k = 4 * st + i;
       const bool v = (unsigned)(e + i - base) < (unsigned)d;
-      const int j = v ? jv[i] : 0;
-      const float m = MU_SMEM ? cx.mu_s[j] : cx.mu(j);
+      const int j = jv[i];  // a valid id even outside the source (see Layout)
+      const float m = MU_SMEM ? cx.mu_smem(j) : cx.mu(j);
       const float r = v ? -__fmaf_rn(av[i], m, cv[i]) : -CUDART_INF_F;
       rf[k] = r;
       if (W) {
@@ -440,7 +509,13 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
     float c, a;
     int j;
     sv.edge(ws + 4 * (l + G * (kb >> 2)) + (kb & 3), j, c, a);
-    acc.account(cx, j, c, a, edge_w<W>(a), 1.f);
+    if (W) {
+      acc.account(cx, j, c, a, edge_w<W>(a), 1.f);
+    } else {
+      cx.scatter(j, a);
+      acc.cx.add(c);
+      ++acc.units;
+    }
   }
   return gvalid && (mode == 1 || (mode == 2 && !lone));
 }
@@ -455,9 +530,14 @@ __device__ __forceinline__ unsigned lean_over(const StageView<BF16>& sv, unsigne
   unsigned needm = 0u;
   const int g = lane / G;
   while (mask) {
-    unsigned m = mask;
-    for (int r = 0; r < g; ++r) m &= m - 1u;
-    const int q = m ? __ffs(m) - 1 : -1;
+    int q;
+    if ((mask & (mask + 1u)) == 0u) {  // 0...01...1: group g takes source g
+      q = (mask >> g) & 1u ? g : -1;
+    } else {
+      unsigned m = mask;
+      for (int r = 0; r < g; ++r) m &= m - 1u;
+      q = m ? __ffs(m) - 1 : -1;
+    }
     const int qs = q < 0 ? 0 : q;
     const int b = __shfl_sync(0xffffffffu, bq, qs);
     const int dd = __shfl_sync(0xffffffffu, dq, qs);
@@ -570,6 +650,8 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
   StageInfo* info = reinterpret_cast<StageInfo*>(smem + L::kInfo);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + L::kMisc);
   double* dred = reinterpret_cast<double*>(smem + L::kMisc + 16);  // 2 per warp
+  // per-stage batch claim counters (reset by the producer when it refills)
+  unsigned* claim = reinterpret_cast<unsigned*>(smem + L::kMisc + 320);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -580,20 +662,25 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kConsumerWarps);
+      claim[s] = 0u;
     }
     *abort = 0;
     fence_mbar_init();
   }
   for (int j = tid; j < p.h_mu; j += blockDim.x) mu_s[j] = p.mu_r[j];
   for (int j = tid; j < p.h_y; j += blockDim.x) y_s[j] = 0ull;
+  for (int s = 0; s < kStages; ++s) {
+    uint32_t* d = reinterpret_cast<uint32_t*>(smem + (size_t)s * L::kStageBytes + L::kOffBytes);
+    for (int k = tid; k < (int)(L::kDstArr / 4); k += blockDim.x) d[k] = 0u;
+  }
   __syncthreads();
 
   Ctx cx;
   Sums acc;
-  cx.mu_s = mu_s;
+  cx.mu_a = smem_u32(mu_s);
   cx.mu_g = p.mu_r;
   cx.h_mu = p.h_mu;
-  cx.y_s = y_s;
+  cx.y_a = smem_u32(y_s);
   cx.h_y = p.h_y;
   cx.y = p.y;
   cx.sy = ldexpf(1.f, p.ey);
@@ -645,6 +732,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
           if (round > 0 && !wait_phase(&empty[s], (round - 1) & 1u, abort, p.status, 1)) {
             stop = true;
           } else {
+            claim[s] = 0u;  // every consumer has left this stage's last tile
             StageInfo si;
             si.s0 = s0;
             si.s1 = s1;
@@ -674,9 +762,9 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
               if (ne) {
                 bulk_g2s(base + L::kOffBytes, p.dst + si.a0, ne * 4u, &full[s]);
                 if (BF16) {
-                  bulk_g2s(base + L::kOffBytes + L::kEdgeArr, p.ca + si.a0, ne * 4u, &full[s]);
+                  bulk_g2s(base + L::kOffBytes + L::kDstArr, p.ca + si.a0, ne * 4u, &full[s]);
                 } else {
-                  bulk_g2s(base + L::kOffBytes + L::kEdgeArr, p.ca2 + si.a0, ne * 8u, &full[s]);
+                  bulk_g2s(base + L::kOffBytes + L::kDstArr, p.ca2 + si.a0, ne * 8u, &full[s]);
                 }
               }
             }
@@ -705,8 +793,12 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     __syncwarp();
   } else {
     // ------------------------------------------------------ consumers ----
-    const int cw = warp - 1;
-    int rot = 0;  // batches seen in earlier tiles, mod kConsumerWarps
+    // Every consumer warp visits every tile and claims work from it through
+    // the stage's counter (one batch of eight sources per claim), so a warp
+    // that is done early takes the next batch, of this tile or the next.  A
+    // warp leaves a tile (arrives on its empty barrier) once the counter runs
+    // past the tile's batches; the producer resets the counter only after
+    // every warp has left, so no claim can reach a refilled stage.
     int64_t it = 0;
     for (int64_t t = t_begin; t < t_end; ++t, ++it) {
       const int s = (int)(it % kStages);
@@ -714,10 +806,14 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       const bool ok = wait_phase(&full[s], round & 1u, abort, p.status, 2);
       if (!__all_sync(0xffffffffu, ok)) break;
       const StageInfo si = info[s];
+      const uint32_t claim_a = smem_u32(claim + s);
       if (si.big) {
-        // one warp (chosen by tile index) projects a source larger than a
-        // stage straight from global memory; no cross-warp barrier is used
-        if (cw == (int)(t % kConsumerWarps)) {
+        // the warp that claims it projects a source larger than a stage
+        // straight from global memory
+        unsigned b = 0u;
+        if (lane == 0) b = atoms_add_u32(claim_a, 1u);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b == 0u) {
           GlobalView<BF16> gv{p.dst, p.ca2, p.ca};
           project_multipass<BF16, W>(gv, si.e0, si.e1 - si.e0, si.e0, lane, cx, acc);
         }
@@ -730,16 +826,16 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         // width: 4 lanes (span <= 64, eight sources per warp), 8 (<= 128),
         // 16 (<= 256), 32 (<= 512), else the multi-pass path.  Whatever the
         // lean path leaves (unsaturated sources, near-ties, the primal output)
-        // goes through the multi-pass path.  Batches are dealt round robin
-        // across tiles (rot), so a tile whose batch count is not a multiple of
-        // the warp count loads different warps.
-        const int nb = (nsrc + 7) >> 3;
-        const int first = (cw - rot + kConsumerWarps) % kConsumerWarps;
-        rot = (rot + nb) % kConsumerWarps;
-        for (int bi = first; bi < nb; bi += kConsumerWarps) {
-          const int li = li0 + 8 * bi;
-          const int n8 = nsrc - 8 * bi < 8 ? nsrc - 8 * bi : 8;
-          const int64_t oq = sv.off[li + (lane <= n8 ? lane : n8)];
+        // goes through the multi-pass path.
+        const unsigned nb = (unsigned)((nsrc + 7) >> 3);
+        for (;;) {
+          unsigned bi = 0u;
+          if (lane == 0) bi = atoms_add_u32(claim_a, 1u);
+          bi = __shfl_sync(0xffffffffu, bi, 0);
+          if (bi >= nb) break;
+          const int li = li0 + 8 * (int)bi;
+          const int n8 = nsrc - 8 * (int)bi < 8 ? nsrc - 8 * (int)bi : 8;
+          const int64_t oq = sv.off(li + (lane <= n8 ? lane : n8));
           const int64_t on = __shfl_down_sync(0xffffffffu, oq, 1);
           const int dq = lane < n8 ? (int)(on - oq) : 0;
           const int bq = (int)(oq - si.a0);
@@ -779,7 +875,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     if (v != 0ull) atomicAdd(p.y + j, v);
   }
   // per-CTA objective partials, FP64 from here on (fixed order)
-  double v0 = acc.cx.value(), v1 = acc.wxx.value();
+  double v0 = acc.cx.value(), v1 = acc.wxx.value() + (double)acc.units;
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     v0 += __shfl_xor_sync(0xffffffffu, v0, o);
