@@ -36,6 +36,10 @@ constexpr int kTileSources = DUALIP_TILE_SOURCES;   // source capacity of a stag
 constexpr int kStages = DUALIP_STAGES;               // depth of the staging ring
 constexpr int kL2PrefetchTiles = DUALIP_L2_PREFETCH_TILES;  // L2 prefetch distance (tiles)
 constexpr int kConsumerWarps = DUALIP_CONSUMER_WARPS;  // warps that project sources
+#ifndef DUALIP_SMEM_RED64
+#define DUALIP_SMEM_RED64 0
+#endif
+constexpr bool kSmemRed64 = DUALIP_SMEM_RED64 != 0;  // shared bins: one 64-bit reduction
 #ifndef DUALIP_WAIT_HINT_NS
 #define DUALIP_WAIT_HINT_NS 0
 #endif

@@ -89,6 +89,9 @@ __device__ __forceinline__ uint32_t atoms_add_u32(uint32_t a, uint32_t v) {
 __device__ __forceinline__ void reds_add_u32(uint32_t a, uint32_t v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
 }
+__device__ __forceinline__ void reds_add_u64(uint32_t a, unsigned long long v) {
+  asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a), "l"(v));
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
@@ -308,13 +311,16 @@ struct Ctx {
   // without 64-bit shared-memory atomics.  Global bins use 64-bit reductions.
   __device__ __forceinline__ void scatter(int j, float v) const {
     const long long q = to_fixed(v, sy);
-    if (q == 0) return;
     if (j < h_y) {
       const uint32_t w = y_a + 8u * j;
-      const unsigned lo = (unsigned)q;
-      const unsigned old = atoms_add_u32(w, lo);
-      const unsigned hi = (unsigned)(q >> 32) + (old + lo < old ? 1u : 0u);
-      if (hi) reds_add_u32(w + 4u, hi);
+      if (kSmemRed64) {
+        reds_add_u64(w, (unsigned long long)q);
+      } else {
+        const unsigned lo = (unsigned)q;
+        const unsigned old = atoms_add_u32(w, lo);
+        const unsigned hi = (unsigned)(q >> 32) + (old + lo < old ? 1u : 0u);
+        if (hi) reds_add_u32(w + 4u, hi);
+      }
     } else {
       atomicAdd(y + j, (unsigned long long)q);
     }
@@ -475,7 +481,7 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
   bool lone = false;
   if (W) {
     mode = rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2);
-    lb = fminf(__fsub_rn(mb, rmax), 0.f) - ldexpf(fabsf(rmax), -20);
+    lb = fminf(__fsub_rn(mb, rmax), 0.f) - __fmul_rn(fabsf(rmax), 0x1p-20f);
     int lc = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -500,7 +506,7 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
       for (int o = G / 2; o; o >>= 1) t0 += __shfl_xor_sync(0xffffffffu, t0, o);
       if (rmax > 0.f && __fmul_rn(t0, cx.inv_gamma) <= 1.f) mode = 1;
     }
-    lb = -cx.gamma - ldexpf(fabsf(rmax), -20);
+    lb = -cx.gamma - __fmul_rn(fabsf(rmax), 0x1p-20f);
     lone = mode == 2 && __fsub_rn(m2, rmax) <= lb;
     if (lm1 != rmax) kb = -1;  // the owner holds the group maximum
   }
