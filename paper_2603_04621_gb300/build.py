@@ -46,7 +46,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        # DUALIP_NVCC_EXTRA: extra nvcc flags (e.g. -DDUALIP_FUSE=0) for tuning builds
+        extra = os.environ.get("DUALIP_NVCC_EXTRA", "").split()
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -209,8 +209,8 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
       (e = dev_alloc(P, &P.b_r, J)) || (e = dev_alloc(P, &P.orig_of, J)) ||
       (e = dev_alloc(P, &P.new_of, J)) || (e = dev_alloc(P, &P.mu_r, J)) ||
       (e = dev_alloc(P, &P.y, J)) ||
-      (e = dev_alloc(P, &P.part, 2 * (size_t)P.grid)) ||
-      (e = dev_alloc(P, &P.epi_part, 2 * (size_t)P.epi_blocks)) ||
+      (e = dev_alloc(P, &P.part, (size_t)P.grid)) ||
+      (e = dev_alloc(P, &P.epi_part, (size_t)P.epi_blocks)) ||
       (e = dev_alloc(P, &P.eval_dev, 8)) || (e = dev_alloc(P, &P.lam_stage, J)) ||
       (e = dev_alloc(P, &P.grad_stage, J)) || (e = dev_alloc(P, &P.status, 1)))
     return bail(cuda_fail(e, "allocating problem memory"));

@@ -63,6 +63,25 @@ struct DeviceStatus {
   int pad;
 };
 
+// Kernel parameters of the J-length epilogue.
+struct EpiParams {
+  int32_t J;
+  const int32_t* orig_of;  // renumbered -> caller's destination id
+  const float* b_r;        // [J] budgets, renumbered
+  const float* mu_r;       // [J] renumbered dual point of the pass
+  const float* D;          // [J] optional row scale in caller numbering (solver)
+  unsigned long long* y;   // [J] fixed-point A x, reset to 0 after reading
+  float sy;                // 2^-exp_y (exact in FP32: |exp_y| <= 100)
+  float* grad;             // [J] caller numbering: D (A x - b) (D = 1 if null)
+  const float4* part;      // per-CTA partials of the pass (pairs, see PassParams)
+  int npart;
+  float4* epi_part;        // [gridDim.x] per-block (lambda^T g, ||g_+||^2) as FP32 pairs
+  const float* gamma_dev;
+  double gamma;
+  double* eval_out;        // [5] dualip_eval order
+  DeviceStatus* status;
+};
+
 // Kernel parameters of one pass (one dual evaluation).
 struct PassParams {
   // edges
@@ -84,27 +103,9 @@ struct PassParams {
   // outputs / scratch
   unsigned long long* y;  // [J] A x in fixed point (two's complement, scale 2^exp_y)
   int ey;                 // fixed-point exponent of A x (scale 2^ey)
-  double* part;           // [gridDim.x * 2] per-CTA (sum c x, sum w x^2)
+  float4* part;           // [gridDim.x] per-CTA (sum c x, sum w x^2), each an FP32
+                          // pair hi + lo (double-float)
   float* x_out;           // [E] optional primal output (edge order)
-  DeviceStatus* status;
-};
-
-// Kernel parameters of the J-length epilogue.
-struct EpiParams {
-  int32_t J;
-  const int32_t* orig_of;  // renumbered -> caller's destination id
-  const float* b_r;        // [J] budgets, renumbered
-  const float* mu_r;       // [J] renumbered dual point used by the pass
-  const float* D;          // [J] optional row scale in caller numbering (solver)
-  unsigned long long* y;   // [J] fixed-point A x, reset to 0 after reading
-  double inv_sy;           // 2^-exp_y
-  float* grad;             // [J] caller numbering: D (A x - b) (D = 1 if null)
-  const double* part;      // per-CTA partials of the pass
-  int npart;
-  double* epi_part;        // [gridDim.x * 4] per-block partials of the epilogue
-  const float* gamma_dev;
-  double gamma;
-  double* eval_out;        // [5] dualip_eval order
   DeviceStatus* status;
 };
 
@@ -130,9 +131,9 @@ struct Problem {
   float* mu_r = nullptr;
   unsigned long long* y = nullptr;  // fixed-point accumulator of A x
   int exp_y = 0;                    // fixed-point scale of A x (power of two)
-  double* part = nullptr;
+  float4* part = nullptr;
   int epi_blocks = 0;
-  double* epi_part = nullptr;
+  float4* epi_part = nullptr;
   double* eval_dev = nullptr;
   float* lam_stage = nullptr;   // [J] staging for host-buffer calls
   float* grad_stage = nullptr;  // [J]

@@ -233,6 +233,7 @@ struct Layout {
   static_assert(kOffBytes % 16 == 0 && kEdgeArr % 16 == 0 && kDstArr % 16 == 0,
                 "16-byte staging");
   static_assert(kTotal <= 227 * 1024, "shared memory budget");
+  static_assert(kMisc % 16 == 0, "float4 reduction slots at kMisc + 16");
 };
 
 // Stage layout: offsets | dst (4 B per slot, padded) | c, a (8 B per slot:
@@ -346,7 +347,6 @@ struct Acc {
     e = __fadd_rn(e, two_sum_err(s, v, t));
     s = t;
   }
-  __device__ __forceinline__ double value() const { return (double)s + (double)e; }
 };
 struct Sums {
   Acc cx, wxx;
@@ -358,6 +358,30 @@ struct Sums {
     wxx.add(__fmul_rn(w, __fmul_rn(x, x)));
   }
 };
+
+// Double-float (hi + lo) arithmetic for the reductions.  FP64 issues at a
+// small fraction of the FP32 rate on this part, so the J-length rows and the
+// block/warp trees stay in FP32 pairs and only the final scalars are FP64.
+__device__ __forceinline__ void pair_add(float& h, float& l, float v) {
+  const float t = __fadd_rn(h, v);
+  l = __fadd_rn(l, two_sum_err(h, v, t));
+  h = t;
+}
+__device__ __forceinline__ void pair_addp(float& h, float& l, float h2, float l2) {
+  const float t = __fadd_rn(h, h2);
+  l = __fadd_rn(__fadd_rn(l, l2), two_sum_err(h, h2, t));
+  h = t;
+}
+// xor-shuffle tree over the warp (fixed order: every lane ends with the sum)
+__device__ __forceinline__ void warp_pair_sum(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    pair_addp(h, l, h2, l2);
+  }
+}
+__device__ __forceinline__ double pair_value(float h, float l) { return (double)h + (double)l; }
 
 // ------------------------------------- group projection, registers ----
 // G lanes own one source (32/G sources per warp), each lane holds up to K of
@@ -641,6 +665,71 @@ __device__ __forceinline__ void project_multipass(const View& v, int64_t base, i
   }
 }
 
+// J-length epilogue rows: (A x)_j from the fixed-point accumulator (which is
+// reset to zero for the next evaluation), grad = D (A x - b) in the caller's
+// numbering, and the partials lambda^T (A x - b) and ||(A x - b)_+||^2 as FP32
+// pairs.  The accumulator converts exactly to a pair (its high part is an
+// integer-valued float, the remainder fits 40 bits) and the scale is a power of
+// two, so g = A x - b is formed with one rounding in its low word.
+struct EpiAcc {
+  float mh = 0.f, ml = 0.f;  // lambda^T g
+  float nh = 0.f, nl = 0.f;  // ||g_+||^2
+};
+__device__ __forceinline__ void epi_rows(const EpiParams& q, int64_t j0, int64_t stride,
+                                         EpiAcc& r) {
+  // eight rows per round, every load issued before any use
+  constexpr int U = 8;
+  for (int64_t r0 = j0; r0 < q.J; r0 += U * stride) {
+    long long yv[U];
+    float bv[U], mv[U], dv[U];
+    int jo[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t jr = r0 + u * stride;
+      const int64_t jc = jr < q.J ? jr : 0;
+      yv[u] = (long long)__ldcg(q.y + jc);
+      bv[u] = q.b_r[jc];
+      mv[u] = q.mu_r[jc];
+      jo[u] = q.orig_of ? q.orig_of[jc] : (int)jc;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) dv[u] = q.D ? q.D[jo[u]] : 1.f;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t jr = r0 + u * stride;
+      if (jr >= q.J) continue;
+      q.y[jr] = 0ull;
+      const float fh = __ll2float_rn(yv[u]);
+      const float fl = __ll2float_rn(yv[u] - __float2ll_rn(fh));
+      const float ah = __fmul_rn(fh, q.sy), al = __fmul_rn(fl, q.sy);
+      const float t = __fsub_rn(ah, bv[u]);
+      const float e = __fadd_rn(two_sum_err(ah, -bv[u], t), al);
+      const float g = __fadd_rn(t, e);
+      const float gl = two_sum_err(t, e, g);
+      const float m = mv[u];
+      const float pm = __fmul_rn(m, g);
+      pair_add(r.mh, r.ml, pm);
+      r.ml = __fadd_rn(r.ml, __fmaf_rn(m, gl, __fmaf_rn(m, g, -pm)));
+      if (g > 0.f) {
+        const float sq = __fmul_rn(g, g);
+        pair_add(r.nh, r.nl, sq);
+        r.nl = __fadd_rn(r.nl, __fmaf_rn(2.f * g, gl, __fmaf_rn(g, g, -sq)));
+      }
+      q.grad[jo[u]] = q.D ? __fmaf_rn(dv[u], g, __fmul_rn(dv[u], gl)) : __fadd_rn(g, gl);
+    }
+  }
+}
+__device__ __forceinline__ void epi_write(const EpiParams& q, double cxs, double wxx, double mug,
+                                          double inf) {
+  const double gamma = q.gamma_dev ? (double)*q.gamma_dev : q.gamma;
+  const double reg = 0.5 * gamma * wxx;
+  q.eval_out[0] = cxs + reg + mug;
+  q.eval_out[1] = cxs;
+  q.eval_out[2] = reg;
+  q.eval_out[3] = sqrt(inf);
+  q.eval_out[4] = mug;
+}
+
 // ----------------------------------------------------------- the pass ----
 // MU_SMEM: every destination's mu is cached in shared memory (J <= the cache).
 // WRITE_X: the primal x is written for every edge (dualip_get_primal); every
@@ -655,7 +744,8 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
   uint64_t* empty = full + kStages;
   StageInfo* info = reinterpret_cast<StageInfo*>(smem + L::kInfo);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + L::kMisc);
-  double* dred = reinterpret_cast<double*>(smem + L::kMisc + 16);  // 2 per warp
+  // [kMisc+16, kMisc+320): per-warp reduction slots (float4)
+  float* dred = reinterpret_cast<float*>(smem + L::kMisc + 16);
   // per-stage batch claim counters (reset by the producer when it refills)
   unsigned* claim = reinterpret_cast<unsigned*>(smem + L::kMisc + 320);
 
@@ -880,26 +970,23 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     const unsigned long long v = y_s[j];
     if (v != 0ull) atomicAdd(p.y + j, v);
   }
-  // per-CTA objective partials, FP64 from here on (fixed order)
-  double v0 = acc.cx.value(), v1 = acc.wxx.value() + (double)acc.units;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-  }
-  if (lane == 0) {
-    dred[2 * warp] = v0;
-    dred[2 * warp + 1] = v1;
-  }
+  // per-CTA objective partials: FP32 pairs through fixed shuffle and warp
+  // orders (reproducible); the units are exact small integers
+  float ch = acc.cx.s, cl = acc.cx.e, wh = acc.wxx.s, wl = acc.wxx.e;
+  pair_add(wh, wl, (float)acc.units);
+  warp_pair_sum(ch, cl);
+  warp_pair_sum(wh, wl);
+  float4* wred = reinterpret_cast<float4*>(dred);  // one per warp
+  if (lane == 0) wred[warp] = make_float4(ch, cl, wh, wl);
   __syncthreads();
   if (tid == 0) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      s0 += dred[2 * w];
-      s1 += dred[2 * w + 1];
+    float4 t = wred[0];
+    for (int w = 1; w < kThreads / 32; ++w) {
+      const float4 u = wred[w];
+      pair_addp(t.x, t.y, u.x, u.y);
+      pair_addp(t.z, t.w, u.z, u.w);
     }
-    p.part[2 * blockIdx.x] = s0;
-    p.part[2 * blockIdx.x + 1] = s1;
+    p.part[blockIdx.x] = t;
   }
 }
 
@@ -916,37 +1003,23 @@ __global__ void prep_mu_kernel(int32_t J, const float* __restrict__ lambda,
 }
 
 __global__ void epilogue_kernel(EpiParams q) {
-  __shared__ double red[3][32];
-  double s_mug = 0.0, s_inf = 0.0;
-  for (int64_t jr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; jr < q.J;
-       jr += (int64_t)gridDim.x * blockDim.x) {
-    const double ax = (double)(long long)q.y[jr] * q.inv_sy;
-    q.y[jr] = 0ull;
-    const double gj = ax - (double)q.b_r[jr];
-    const int jo = q.orig_of ? q.orig_of[jr] : (int)jr;
-    s_mug += (double)q.mu_r[jr] * gj;
-    if (gj > 0.0) s_inf += gj * gj;
-    q.grad[jo] = (float)(q.D ? (double)q.D[jo] * gj : gj);
-  }
-  for (int o = 16; o; o >>= 1) {
-    s_mug += __shfl_xor_sync(0xffffffffu, s_mug, o);
-    s_inf += __shfl_xor_sync(0xffffffffu, s_inf, o);
-  }
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (lane == 0) {
-    red[0][w] = s_mug;
-    red[1][w] = s_inf;
-  }
-  __syncthreads();
+  __shared__ float4 red[32];
+  __shared__ float4 fin[2][32];
   __shared__ bool last;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  EpiAcc r;
+  epi_rows(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, r);
+  warp_pair_sum(r.mh, r.ml);
+  warp_pair_sum(r.nh, r.nl);
+  if (lane == 0) red[w] = make_float4(r.mh, r.ml, r.nh, r.nl);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int k = 0; k < nw; ++k) {
-      a += red[0][k];
-      b += red[1][k];
+    float4 t = red[0];
+    for (int k = 1; k < nw; ++k) {
+      pair_addp(t.x, t.y, red[k].x, red[k].y);
+      pair_addp(t.z, t.w, red[k].z, red[k].w);
     }
-    q.epi_part[2 * blockIdx.x] = a;
-    q.epi_part[2 * blockIdx.x + 1] = b;
+    q.epi_part[blockIdx.x] = t;
     __threadfence();
     const unsigned prev = atomicAdd(&q.status->ticket, 1u);
     last = prev == gridDim.x - 1;
@@ -954,38 +1027,35 @@ __global__ void epilogue_kernel(EpiParams q) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // fixed-order FP64 combination of every partial (strided per thread, then a
+  // fixed-order combination of every partial (strided per thread, then a
   // fixed shuffle tree and a fixed warp order)
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int k = threadIdx.x; k < q.npart; k += blockDim.x) {
-    v[0] += q.part[2 * k];
-    v[1] += q.part[2 * k + 1];
+    const float4 u = __ldcg(q.part + k);
+    pair_addp(v[0], v[1], u.x, u.y);
+    pair_addp(v[2], v[3], u.z, u.w);
   }
   for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
-    v[2] += q.epi_part[2 * k];
-    v[3] += q.epi_part[2 * k + 1];
+    const float4 u = __ldcg(q.epi_part + k);
+    pair_addp(v[4], v[5], u.x, u.y);
+    pair_addp(v[6], v[7], u.z, u.w);
   }
-  for (int o = 16; o; o >>= 1)
-    for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-  __shared__ double fin[4][32];
-  if (lane == 0)
-    for (int i = 0; i < 4; ++i) fin[i][w] = v[i];
+  for (int i = 0; i < 8; i += 2) warp_pair_sum(v[i], v[i + 1]);
+  if (lane == 0) {
+    fin[0][w] = make_float4(v[0], v[1], v[2], v[3]);
+    fin[1][w] = make_float4(v[4], v[5], v[6], v[7]);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double cxs = 0.0, wxx = 0.0, mug = 0.0, inf = 0.0;
+    float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = 0; k < nw; ++k) {
-      cxs += fin[0][k];
-      wxx += fin[1][k];
-      mug += fin[2][k];
-      inf += fin[3][k];
+      pair_addp(t[0], t[1], fin[0][k].x, fin[0][k].y);
+      pair_addp(t[2], t[3], fin[0][k].z, fin[0][k].w);
+      pair_addp(t[4], t[5], fin[1][k].x, fin[1][k].y);
+      pair_addp(t[6], t[7], fin[1][k].z, fin[1][k].w);
     }
-    const double gamma = q.gamma_dev ? (double)*q.gamma_dev : q.gamma;
-    const double reg = 0.5 * gamma * wxx;
-    q.eval_out[0] = cxs + reg + mug;
-    q.eval_out[1] = cxs;
-    q.eval_out[2] = reg;
-    q.eval_out[3] = sqrt(inf);
-    q.eval_out[4] = mug;
+    epi_write(q, pair_value(t[0], t[1]), pair_value(t[2], t[3]), pair_value(t[4], t[5]),
+              pair_value(t[6], t[7]));
     q.status->ticket = 0u;
   }
 }
@@ -1090,8 +1160,8 @@ cudaError_t launch_prep(const Problem& P, const float* lambda, const float* D, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, float* x_out,
-                        cudaStream_t s) {
+static PassParams pass_params(const Problem& P, const float* gamma_dev, float gamma,
+                              float* x_out) {
   PassParams p;
   p.off = P.off;
   p.dst = P.dst;
@@ -1112,6 +1182,19 @@ cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, f
   p.part = P.part;
   p.x_out = x_out;
   p.status = P.status;
+  return p;
+}
+
+static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_out,
+                                 cudaStream_t s);
+
+cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, float* x_out,
+                        cudaStream_t s) {
+  return dispatch_pass(P, pass_params(P, gamma_dev, gamma, x_out), x_out != nullptr, s);
+}
+
+static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_out,
+                                 cudaStream_t s) {
   const bool bf16 = P.storage == DUALIP_EDGE_BF16;
   const bool mu_all = P.J <= P.h_mu;
   const size_t smem = pass_smem_bytes(P.storage);
@@ -1155,7 +1238,7 @@ cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const
   q.mu_r = P.mu_r;
   q.D = D;
   q.y = P.y;
-  q.inv_sy = ldexp(1.0, -P.exp_y);
+  q.sy = ldexpf(1.0f, -P.exp_y);
   q.grad = grad;
   q.part = P.part;
   q.npart = P.grid;
