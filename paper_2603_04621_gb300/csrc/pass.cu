@@ -10,23 +10,31 @@
 //
 // Kernel design (GB300-first, not the paper's bucketed padded slabs):
 //  * one persistent CTA per SM walks a contiguous range of "tiles" (runs of
-//    whole sources holding <= kTileEdges edges); warp 0 streams each tile's
-//    offsets and edge arrays into a kStages-deep shared-memory ring with
-//    cp.async.bulk + mbarrier transaction counts, 16 consumer warps project;
-//  * a consumer warp owns one source at a time; degrees <= 128 live in
-//    registers (up to 4 edges per lane), larger ones are re-read from the
-//    staged tile, and a source too large for a tile is projected by one warp
-//    straight from global memory;
-//  * scores are formed as an unevaluated FP32 pair (hi + lo = -(c + a mu) to
-//    about 2^-48 relative) and, when the sum constraint binds, shifted by the
-//    block maximum (exact by Sterbenz's lemma near the top), so the threshold
-//    and x keep FP32 accuracy even when gamma is small and r/gamma is large;
-//  * the threshold follows Michelot's finite iteration started from the set
-//    {d_e > max_e(d_e - gamma w_e)}, which contains the active set;
-//  * y = A x uses FP32 atomics with an exact TwoSum error term accumulated in a
-//    second array; hot destinations (ids renumbered by in-degree) accumulate
-//    in shared memory first; objective partials use per-lane FP32 TwoSum
-//    accumulators and FP64 only for the final per-CTA reduction.
+//    whole sources holding <= kTileEdges edges and <= kTileSources sources);
+//    warp 0 streams each tile's offsets, destinations and (c, a) into a
+//    kStages-deep shared-memory ring with cp.async.bulk + mbarrier
+//    transaction counts; 16 consumer warps project;
+//  * consumer warps claim batches of eight sources of a staged tile through a
+//    per-stage shared counter; the span of a source picks how many lanes
+//    share it (4, 8, 16 or 32, up to 16 edges per lane in registers);
+//  * the common case at small gamma is a saturated source with a single
+//    candidate (its second score is more than gamma below the first): it gets
+//    x = 1 exactly.  Everything else (unsaturated sources, near-ties, spans
+//    over 512, the primal output) is projected by a whole warp in several
+//    passes over the staged tile, with scores as an unevaluated FP32 pair
+//    (hi + lo = -(c + a mu) to about 2^-48 relative) shifted by the block
+//    maximum (exact by Sterbenz's lemma near the top), so the threshold and x
+//    keep FP32 accuracy relative to gamma; Michelot's finite iteration starts
+//    from {d_e > max_e(d_e - gamma w_e)}, which contains the active set.  A
+//    source larger than a tile is projected by one warp from global memory;
+//  * y = A x accumulates in 64-bit two's-complement fixed point (scale
+//    2^exp_y chosen at create so that no sum can overflow): every add is
+//    exact, so A x does not depend on the order of the adds.  Hot
+//    destinations (ids renumbered by in-degree) accumulate in shared memory
+//    and are flushed once per CTA; the rest go to global atomics;
+//  * objective partials are per-lane FP32 TwoSum accumulators and FP32
+//    double-float pairs through the warp and CTA trees; batches go to warps
+//    dynamically, so their last bits may differ from run to run.
 #include <cuda_bf16.h>
 #include <math_constants.h>
 
@@ -970,8 +978,8 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     const unsigned long long v = y_s[j];
     if (v != 0ull) atomicAdd(p.y + j, v);
   }
-  // per-CTA objective partials: FP32 pairs through fixed shuffle and warp
-  // orders (reproducible); the units are exact small integers
+  // per-CTA objective partials: FP32 pairs through the shuffle and warp
+  // trees; the units are exact small integers
   float ch = acc.cx.s, cl = acc.cx.e, wh = acc.wxx.s, wl = acc.wxx.e;
   pair_add(wh, wl, (float)acc.units);
   warp_pair_sum(ch, cl);
