@@ -43,8 +43,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2"])
-    ap.add_argument("--scale", type=float, default=1.0, help="fraction of c2's sources (debug)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: 1M x 10k, ~50M edges (default); c3: 25M x 1M, ~2.0B edges")
+    ap.add_argument("--storage", default=None, choices=["f32", "bf16"],
+                    help="edge storage (default f32 for c2, bf16 for c3)")
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the sources")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -58,27 +61,37 @@ def dist_env():
     return ws, rank, local
 
 
-def workload(scale=1.0):
+def workload(name="c2", scale=1.0):
     import synth
 
-    inst = synth.config("c2", scale=scale)
-    return inst
+    return synth.config(name, scale=scale)
 
 
 def lam_for(inst):
     return np.random.default_rng(LAM_SEED).uniform(0.0, 1.0, inst.J).astype(np.float32)
 
 
-def config_dict(inst, scale):
+WORKLOADS = {
+    "c2": ("c2: matching LP, 1M sources x 10k destinations, Poisson(50) degrees in [1,500], "
+           "Zipf(1.1) destinations, c=-LogNormal(0,1), a~U(0.5,1.5), b=0.2*sum(a), int32 dst"),
+    "c3": ("c3: matching LP, 25M sources x 1M destinations, Poisson(80) degrees in [1,2000], "
+           "Zipf(1.1) destinations, c=-LogNormal(0,1), a~U(0.5,1.5), b=0.2*sum(a), int64 offsets"),
+}
+
+
+def edge_bytes(storage):
+    return 8 if storage == "bf16" else 12
+
+
+def config_dict(inst, name, scale, storage):
+    eb = edge_bytes(storage)
     return {
-        "workload": ("c2: matching LP, 1M sources x 10k destinations, Poisson(50) degrees in "
-                     "[1,500], Zipf(1.1) destinations, c=-LogNormal(0,1), a~U(0.5,1.5), "
-                     "b=0.2*sum(a)" if scale == 1.0 else f"c2 at {scale:g} of the sources"),
-        "I": inst.I, "J": inst.J, "E": inst.E, "gamma": GAMMA,
+        "workload": WORKLOADS[name] if scale == 1.0 else f"{name} at {scale:g} of the sources",
+        "storage": storage, "I": inst.I, "J": inst.J, "E": inst.E, "gamma": GAMMA,
         "lambda": f"U(0,1) seed {LAM_SEED}",
-        "edge_bytes": 12 * inst.E,
-        "l2": "inputs larger than L2 (edges 12 B/edge > 129 MB); no flush",
-        "parallelism": "replicas" ,
+        "edge_bytes": eb * inst.E,
+        "l2": f"inputs larger than L2 (edges {eb} B/edge > 129 MB); no flush",
+        "parallelism": "replicas",
     }
 
 
@@ -102,16 +115,19 @@ def kernel_code_hash():
     return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
 
 
-def pass_traffic(inst):
+def pass_traffic(inst, name, storage):
+    if name != "c2" or storage != "f32":
+        return None  # no capture of this configuration
     if kernel_code_hash() != PASS_TRAFFIC["pass_cu_code_sha256"]:
         return None
     return PASS_TRAFFIC["bytes"] * inst.E / PASS_TRAFFIC["edges"]
 
 
-def algorithmic_bytes(inst):
-    # what one pass must move: 12 B/edge (dst, c, a), 8 B per source offset,
-    # and per destination: mu read, the A x accumulator written and read
-    return 12 * inst.E + 8 * (inst.I + 1) + 12 * inst.J
+def algorithmic_bytes(inst, storage="f32"):
+    # what one pass must move: 12 B/edge (dst, c, a; 8 B with (c, a) in BF16),
+    # 8 B per source offset, and per destination: mu read, the A x
+    # accumulator written and read
+    return edge_bytes(storage) * inst.E + 8 * (inst.I + 1) + 12 * inst.J
 
 
 class ClockSampler:
@@ -198,7 +214,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    inst = workload(args.scale)
+    inst = workload(args.workload, args.scale)
     import oracle
 
     n = max(1, min(inst.I, int(inst.I * 0.02)))
@@ -216,22 +232,25 @@ def run_reference(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "impl": "reference", "config": config_dict(inst, args.scale),
+           "data": "synthetic", "impl": "reference",
+           "config": config_dict(inst, args.workload, args.scale, args.storage),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"each step: first {n} sources of c2 ({sub.E} edges)"},
+                            "sample": f"each step: first {n} sources of {args.workload} "
+                                      f"({sub.E} edges)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
 
 
-def time_to_gap(d, torch):
-    """dualip_solve to the 1e-4 relative gap on c2 with the paper's greedy-load budgets
-    (the sum-fraction budgets of c2 never bind, so lambda* = 0 there)."""
+def time_to_gap(d, torch, base, name, storage):
+    """dualip_solve to the 1e-4 relative gap on the workload's graph and values with
+    the paper's greedy-load budgets (the sum-fraction budgets never bind, so
+    lambda* = 0 there)."""
     import synth
 
-    inst = synth.greedy_budgets(synth.config("c2"))
-    P = d.Problem.from_instance(inst)
+    inst = synth.greedy_budgets(base)
+    P = d.Problem.from_instance(inst, storage=storage)
     P.solve(max_iters=20)  # warm: graph capture, row scale
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -239,7 +258,8 @@ def time_to_gap(d, torch):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     P.close()
-    return {"workload": "c2 graph and values with greedy-load budgets (App. B rule)",
+    return {"workload": f"{name} graph and values with greedy-load budgets (App. B rule)",
+            "storage": storage,
             "seconds": dt, "iters": res["iters"], "converged": res["converged"],
             "gap_rel": res["gap_rel"], "infeas_rel": res["infeas_rel"],
             "dual_obj": res["dual_obj"]}
@@ -262,8 +282,8 @@ def run_ours(args):
         dist.barrier()
     import paper_2603_04621_gb300 as d
 
-    inst = workload(args.scale)
-    P = d.Problem.from_instance(inst)
+    inst = workload(args.workload, args.scale)
+    P = d.Problem.from_instance(inst, storage=args.storage)
     lam_h = lam_for(inst)
     lam = torch.from_numpy(lam_h).cuda()
     grad = torch.empty(inst.J, dtype=torch.float32, device="cuda")
@@ -320,7 +340,8 @@ def run_ours(args):
             e2e_s = float(t.item())
     ttg = None
     if not args.no_solve and rank == 0 and args.scale == 1.0:
-        ttg = time_to_gap(d, torch)
+        P.close()
+        ttg = time_to_gap(d, torch, inst, args.workload, args.storage)
     if rank != 0:
         if ws > 1:
             dist.barrier()
@@ -329,7 +350,7 @@ def run_ours(args):
     E = inst.E
     value = E * args.steps * ws / (ms / 1e3)
     pass_ms = prof["ms_pass"] / max(prof["count"], 1)
-    alg = algorithmic_bytes(inst)
+    alg = algorithmic_bytes(inst, args.storage)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -344,9 +365,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(inst, args.scale),
+        "config": config_dict(inst, args.workload, args.scale, args.storage),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": pass_traffic(inst),
+                     "frac": achieved / peak, "traffic": pass_traffic(inst, args.workload, args.storage),
                      "kernel": "dualgrad_pass_kernel",
                      "kernel_ms": pass_ms, "algorithmic_bytes": alg, "peak_source": peak_note},
         "kernel_ms": {"prologue": prof["ms_prologue"] / max(prof["count"], 1), "pass": pass_ms,
@@ -369,6 +390,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.storage is None:
+        args.storage = "bf16" if args.workload == "c3" else "f32"
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -103,8 +103,10 @@ class Instance:
         deg = self.off[idx + 1] - self.off[idx]
         off = np.zeros(idx.shape[0] + 1, dtype=np.int64)
         np.cumsum(deg, out=off[1:])
-        sel = np.concatenate([np.arange(self.off[i], self.off[i + 1]) for i in idx]) if idx.size else \
-            np.zeros(0, dtype=np.int64)
+        # edge ids of the chosen sources, in order: each source's first edge
+        # repeated over its degree, plus the running position inside it
+        E = int(off[-1])
+        sel = np.repeat(self.off[idx] - off[:-1], deg) + np.arange(E, dtype=np.int64)
         return Instance(off, self.dst[sel], self.c[sel], self.a[sel], self.b.copy(), self.J,
                         name=self.name + "[subset]")
 
