@@ -233,6 +233,72 @@ dualip_status dualip_dual_grad_noalloc(int64_t num_sources, int32_t num_dests,
                                        int32_t primal_scaling, const float* lambda, double gamma,
                                        float* grad, double* out_dev, void* stream);
 
+/* ------------------------------------------------------------ batches ----
+ * The batched form: several independent matching LPs evaluated, and solved,
+ * by one launch of the pass per iteration (the paper batches the per-source
+ * projections of one problem, Section 6; here whole problems are batched).
+ * A batch is built from problem handles made by dualip_create, which keep
+ * their own data; the batch only references them: destroy it before them,
+ * and do not use a problem on its own while a batch call on it may run.
+ * Every problem must use the same storage and primal_scaling.
+ *
+ * Joint vectors ("joint [sum J]") hold the problems' destination vectors back
+ * to back in batch order, each in the caller's numbering: problem k's entries
+ * start at J_0 + ... + J_{k-1}.
+ */
+typedef struct dualip_batch dualip_batch;
+
+/* n >= 1 problems (host array of handles).  Tiles use the default shape
+ * (3072 edges, 256 sources) until dualip_batch_autotune picks another. */
+dualip_status dualip_batch_create(int32_t n, dualip_problem* const* problems,
+                                  dualip_batch** out);
+void dualip_batch_destroy(dualip_batch* b);
+
+/*
+ * One evaluation of every problem, each at its own gamma, equal to what
+ * dualip_dual_grad gives for it alone (the gradient bit for bit; the scalars
+ * up to the order of their partial sums).
+ *   lambda [sum J] device joint, read; gammas [n] host; grad [sum J] device joint, written
+ *   out [n] host (may be NULL): the scalars of each problem
+ * Synchronises the stream.
+ */
+dualip_status dualip_batch_dual_grad(dualip_batch* b, const float* lambda, const double* gammas,
+                                     float* grad, dualip_eval* out, void* stream);
+/* Same, stream-ordered, scalars to out_dev ([5 n] device doubles, may be NULL). */
+dualip_status dualip_batch_dual_grad_async(dualip_batch* b, const float* lambda,
+                                           const double* gammas, float* grad, double* out_dev,
+                                           void* stream);
+
+/*
+ * The ascent of dualip_solve for every problem at once, each with its own
+ * gamma schedule, step, momentum and stopping test; a problem that has met
+ * its tolerances (or its max_iters) stops being evaluated.
+ *   opts: n_opts = 1 (shared) or n; check_every, row_normalize and use_graph
+ *         are taken from opts[0]
+ *   lambda_inout [sum J] device joint; results [n] host (may be NULL)
+ * Returns DUALIP_ENOTCONVERGED if some problem ran out of iterations.
+ */
+dualip_status dualip_batch_solve(dualip_batch* b, const dualip_solve_opts* opts, int32_t n_opts,
+                                 float* lambda_inout, dualip_solve_result* results, void* stream);
+
+/* Tile shape autotuner: candidate (edges, sources) shapes are pruned by the
+ * degree (segment length) histogram of the batch, each survivor is timed
+ * over a few passes, and the fastest is kept. */
+typedef struct {
+  int32_t n_candidates;
+  int32_t chosen;              /* index of the shape kept */
+  int32_t tile_edges[8];
+  int32_t tile_sources[8];
+  double ms[8];                /* mean pass time of each candidate */
+  int64_t degree_hist[32];     /* sources with degree in [2^k, 2^(k+1)) (k = 0: 0 or 1) */
+} dualip_autotune_result;
+dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* result, void* stream);
+/* Explicit tile shape: 1 <= edges <= 3072, 1 <= sources <= 256. */
+dualip_status dualip_batch_set_tile_shape(dualip_batch* b, int32_t edges, int32_t sources);
+dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* total_J,
+                                    int64_t* total_E, int64_t* ntiles, int32_t* tile_edges,
+                                    int32_t* tile_sources);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* dualip_last_error(void);
 

@@ -29,6 +29,9 @@ EXPORTS = [
     "dualip_dual_grad_host", "dualip_get_primal", "dualip_check_device_status",
     "dualip_get_info", "dualip_solve_opts_default", "dualip_solve", "dualip_last_error",
     "dualip_profile_enable", "dualip_profile_collect", "dualip_dual_grad_noalloc",
+    "dualip_batch_create", "dualip_batch_destroy", "dualip_batch_dual_grad",
+    "dualip_batch_dual_grad_async", "dualip_batch_solve", "dualip_batch_autotune",
+    "dualip_batch_set_tile_shape", "dualip_batch_get_info",
 ]
 
 
@@ -36,6 +39,18 @@ class DualipError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"dualip {STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
+
+
+class AutotuneResult(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int32), ("chosen", ctypes.c_int32),
+                ("tile_edges", ctypes.c_int32 * 8), ("tile_sources", ctypes.c_int32 * 8),
+                ("ms", ctypes.c_double * 8), ("degree_hist", ctypes.c_int64 * 32)]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return dict(n_candidates=n, chosen=self.chosen, tile_edges=list(self.tile_edges[:n]),
+                    tile_sources=list(self.tile_sources[:n]), ms=list(self.ms[:n]),
+                    degree_hist=list(self.degree_hist))
 
 
 class ProblemDesc(ctypes.Structure):
@@ -111,6 +126,26 @@ def lib() -> ctypes.CDLL:
         L.dualip_dual_grad_noalloc.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, vp, dbl, vp,
                                                vp, vp]
         L.dualip_dual_grad_noalloc.restype = st
+        L.dualip_batch_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.dualip_batch_create.restype = st
+        L.dualip_batch_destroy.argtypes = [vp]
+        L.dualip_batch_destroy.restype = None
+        L.dualip_batch_dual_grad.argtypes = [vp, vp, ctypes.POINTER(dbl), vp,
+                                             ctypes.POINTER(Eval), vp]
+        L.dualip_batch_dual_grad.restype = st
+        L.dualip_batch_dual_grad_async.argtypes = [vp, vp, ctypes.POINTER(dbl), vp, vp, vp]
+        L.dualip_batch_dual_grad_async.restype = st
+        L.dualip_batch_solve.argtypes = [vp, ctypes.POINTER(SolveOpts), i32, vp,
+                                         ctypes.POINTER(SolveResult), vp]
+        L.dualip_batch_solve.restype = st
+        L.dualip_batch_autotune.argtypes = [vp, ctypes.POINTER(AutotuneResult), vp]
+        L.dualip_batch_autotune.restype = st
+        L.dualip_batch_set_tile_shape.argtypes = [vp, i32, i32]
+        L.dualip_batch_set_tile_shape.restype = st
+        L.dualip_batch_get_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                            ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                            ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.dualip_batch_get_info.restype = st
         L.dualip_last_error.argtypes = []
         L.dualip_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -222,6 +257,61 @@ def dualip_solve(h: int, opts: SolveOpts, lam_ptr: int, trace_ptr: int, stream: 
     return r
 
 
+def dualip_batch_create(handles) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    out = ctypes.c_void_p()
+    _check(lib().dualip_batch_create(len(handles), arr, ctypes.byref(out)))
+    return out.value
+
+
+def dualip_batch_destroy(b: int) -> None:
+    lib().dualip_batch_destroy(b)
+
+
+def _doubles(xs):
+    return (ctypes.c_double * len(xs))(*[float(x) for x in xs])
+
+
+def dualip_batch_dual_grad(b: int, lam_ptr: int, gammas, grad_ptr: int, stream: int):
+    out = (Eval * len(gammas))()
+    _check(lib().dualip_batch_dual_grad(b, lam_ptr, _doubles(gammas), grad_ptr, out, stream))
+    return [e.as_dict() for e in out]
+
+
+def dualip_batch_dual_grad_async(b: int, lam_ptr: int, gammas, grad_ptr: int, out_dev_ptr: int,
+                                 stream: int) -> None:
+    _check(lib().dualip_batch_dual_grad_async(b, lam_ptr, _doubles(gammas), grad_ptr,
+                                              out_dev_ptr, stream))
+
+
+def dualip_batch_solve(b: int, opts, lam_ptr: int, n: int, stream: int):
+    opts = list(opts) if isinstance(opts, (list, tuple)) else [opts]
+    oa = (SolveOpts * len(opts))(*opts)
+    res = (SolveResult * n)()
+    _check(lib().dualip_batch_solve(b, oa, len(opts), lam_ptr, res, stream),
+           ok=(DUALIP_OK, DUALIP_ENOTCONVERGED))
+    return list(res)
+
+
+def dualip_batch_autotune(b: int, stream: int) -> dict:
+    r = AutotuneResult()
+    _check(lib().dualip_batch_autotune(b, ctypes.byref(r), stream))
+    return r.as_dict()
+
+
+def dualip_batch_set_tile_shape(b: int, edges: int, sources: int) -> None:
+    _check(lib().dualip_batch_set_tile_shape(b, edges, sources))
+
+
+def dualip_batch_get_info(b: int) -> dict:
+    n, te, ts = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    J, E, T = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().dualip_batch_get_info(b, ctypes.byref(n), ctypes.byref(J), ctypes.byref(E),
+                                       ctypes.byref(T), ctypes.byref(te), ctypes.byref(ts)))
+    return dict(n=n.value, J=J.value, E=E.value, ntiles=T.value, tile_edges=te.value,
+                tile_sources=ts.value)
+
+
 # ------------------------------------------------- convenience (marshalling) ----
 class Problem:
     """Owns one dualip handle built from host (numpy) or device (torch) arrays.
@@ -316,3 +406,72 @@ class Problem:
         if trace:
             return lam, res, tr[: r.iters].cpu().numpy()
         return lam, res
+
+
+class Batch:
+    """A dualip batch over Problem objects (which must outlive it).  Joint
+    vectors hold the problems' destination vectors back to back."""
+
+    def __init__(self, problems):
+        import torch
+
+        self.problems = list(problems)
+        self.h = dualip_batch_create([p.h for p in self.problems])
+        self.Js = [p.J for p in self.problems]
+        self.joff = np.concatenate([[0], np.cumsum(self.Js)]).astype(np.int64)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @property
+    def n(self) -> int:
+        return len(self.problems)
+
+    def close(self):
+        if getattr(self, "h", 0):
+            dualip_batch_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def split(self, v):
+        return [v[self.joff[k]:self.joff[k + 1]] for k in range(self.n)]
+
+    def dual_grad(self, lam, gammas, stream=None):
+        """lam: joint torch vector; returns (joint grad tensor, list of scalar dicts)."""
+        import torch
+
+        assert lam.is_cuda and lam.dtype == torch.float32 and lam.numel() == int(self.joff[-1])
+        grad = torch.empty_like(lam)
+        ev = dualip_batch_dual_grad(self.h, _ptr(lam.contiguous()), gammas, _ptr(grad),
+                                    _stream(stream))
+        return grad, ev
+
+    def solve(self, lam0=None, opts=None, stream=None, **kw):
+        """Per-problem ascent; opts: a list of per-problem dicts or one dict (kw)."""
+        import torch
+
+        def mk(d):
+            o = dualip_solve_opts_default()
+            for k, v in d.items():
+                setattr(o, "restart_on_gamma_change" if k == "restart" else k, v)
+            return o
+
+        ol = [mk(d) for d in opts] if opts is not None else [mk(kw)]
+        lam = (torch.zeros(int(self.joff[-1]), dtype=torch.float32, device=self.device)
+               if lam0 is None else lam0.clone())
+        res = dualip_batch_solve(self.h, ol, _ptr(lam), self.n, _stream(stream))
+        out = [dict(iters=r.iters, converged=bool(r.converged), gap_rel=r.gap_rel,
+                    infeas_rel=r.infeas_rel, gamma=r.gamma, **r.last.as_dict()) for r in res]
+        return lam, out
+
+    def autotune(self, stream=None) -> dict:
+        return dualip_batch_autotune(self.h, _stream(stream))
+
+    def set_tile_shape(self, edges: int, sources: int) -> None:
+        dualip_batch_set_tile_shape(self.h, edges, sources)
+
+    def info(self) -> dict:
+        return dualip_batch_get_info(self.h)

@@ -55,11 +55,13 @@ void free_all(Problem& P) {
   P.eval_host = nullptr;
 }
 
+}  // namespace
+
 // Greedy tiling: consecutive whole sources while the edge count stays within
-// kTileEdges and the source count within kTileSources; a source larger than
-// a tile forms a tile of its own (projected from global memory).
+// max_edges and the source count within max_sources; a source larger than
+// max_edges forms a tile of its own (projected from global memory).
 void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
-                 std::vector<int64_t>& tile_e) {
+                 std::vector<int64_t>& tile_e, int64_t max_edges, int64_t max_sources) {
   const int64_t I = (int64_t)off.size() - 1;
   tiles.clear();
   tile_e.clear();
@@ -68,11 +70,11 @@ void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
     tiles.push_back(s);
     tile_e.push_back(off[s]);
     int64_t e = 0, n = 0;
-    if (off[s + 1] - off[s] > kTileEdges) {
+    if (off[s + 1] - off[s] > max_edges) {
       ++s;
       continue;
     }
-    while (s < I && n < kTileSources && e + (off[s + 1] - off[s]) <= kTileEdges) {
+    while (s < I && n < max_sources && e + (off[s + 1] - off[s]) <= max_edges) {
       e += off[s + 1] - off[s];
       ++n;
       ++s;
@@ -83,6 +85,8 @@ void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+namespace {
 
 dualip_status read_status(Problem& P, cudaStream_t s) {
   DeviceStatus h{};
@@ -351,6 +355,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   if ((e = cudaMemcpy(&st, P.status, sizeof(st), cudaMemcpyDeviceToHost)))
     return bail(cuda_fail(e, "reading the device status"));
   if (st.err) return bail(fail(DUALIP_EINVAL, "dst out of [0, J) or non-finite c / a"));
+  P.off_host = std::move(off);
   *out = h;
   return DUALIP_OK;
 }

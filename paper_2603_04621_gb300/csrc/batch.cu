@@ -1,0 +1,969 @@
+// Batched form: several matching LPs evaluated, and solved, together.
+//
+// Each problem keeps the arrays dualip_create made for it (packed edges,
+// renumbering, fixed-point scale) and occupies a slot of a device table.  One
+// launch of the pass walks a joint list of tiles of all active slots; the
+// J-length work walks a joint list of row chunks.  The ascent (Section 5 and
+// Appendix B of the paper, as in the single-problem solver) runs per slot:
+// every slot has its own gamma schedule, step, momentum and stopping test, and
+// a slot that has converged leaves the lists, so its edges are no longer
+// streamed.  Every per-problem result equals the problem's own evaluation:
+// A x is exact in fixed point, so the gradient does not depend on the other
+// problems, and the scalars differ from a lone evaluation only in the order
+// of their FP32/FP64 partial sums.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace dualip {
+namespace {
+
+constexpr int kChunkRows = 2048;  // rows of a J-length chunk
+
+// ------------------------------------------------ double-float helpers ----
+__device__ __forceinline__ float b_two_sum_err(float u, float v, float s) {
+  const float vv = __fsub_rn(s, u);
+  return __fadd_rn(__fsub_rn(u, __fsub_rn(s, vv)), __fsub_rn(v, vv));
+}
+__device__ __forceinline__ void b_pair_add(float& h, float& l, float v) {
+  const float t = __fadd_rn(h, v);
+  l = __fadd_rn(l, b_two_sum_err(h, v, t));
+  h = t;
+}
+__device__ __forceinline__ void b_pair_addp(float& h, float& l, float h2, float l2) {
+  const float t = __fadd_rn(h, h2);
+  l = __fadd_rn(__fadd_rn(l, l2), b_two_sum_err(h, h2, t));
+  h = t;
+}
+__device__ __forceinline__ void b_warp_pair_sum(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    b_pair_addp(h, l, h2, l2);
+  }
+}
+// Block sum of two pairs (blockDim.x = 256), result in thread 0.
+__device__ __forceinline__ float4 block_pair_sum2(float4 v) {
+  __shared__ float4 red[8];
+  b_warp_pair_sum(v.x, v.y);
+  b_warp_pair_sum(v.z, v.w);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      b_pair_addp(t.x, t.y, red[k].x, red[k].y);
+      b_pair_addp(t.z, t.w, red[k].z, red[k].w);
+    }
+  return t;
+}
+
+__host__ __device__ inline double slot_gamma(const SlotSolve& s, int32_t k) {
+  double g = s.gamma0;
+  if (s.halve_every > 0) g = ldexp(s.gamma0, -(k / s.halve_every));
+  return g > s.gamma_final ? g : s.gamma_final;
+}
+__device__ inline bool slot_restart(const SlotSolve& s, int32_t k) {
+  return s.restart && k > 0 && slot_gamma(s, k) != slot_gamma(s, k - 1);
+}
+
+// ------------------------------------------------- J-length kernels ----
+// Rows of chunk c are rows [r0, r1) of the chunk's slot in renumbered order.
+// API mode: mu_r[jr] = lambda[joff + orig_of[jr]].  Solver mode: the ascent's
+// point y (renumbered) times the row scale, with the momentum restart at a
+// gamma change; the first chunk of a slot publishes the slot's gamma.
+__global__ void bprep_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __restrict__ sd,
+                             const float* __restrict__ lam, int solver, SlotSolve* ss,
+                             float* gamma_f, double* gamma_d) {
+  const RowChunk ch = rc[blockIdx.x];
+  const SlotDesc& d = sd[ch.slot];
+  if (!solver) {
+    for (int jr = ch.r0 + threadIdx.x; jr < ch.r1; jr += blockDim.x)
+      d.mu_r[jr] = lam[d.joff + d.orig_of[jr]];
+    return;
+  }
+  const SlotSolve& st = ss[ch.slot];
+  const bool rs = slot_restart(st, st.k);
+  for (int jr = ch.r0 + threadIdx.x; jr < ch.r1; jr += blockDim.x) {
+    float yj = d.yv[jr];
+    if (rs) {
+      yj = d.lam[jr];
+      d.yv[jr] = yj;
+    }
+    d.mu_r[jr] = __fmul_rn(d.D[jr], yj);
+  }
+  if (ch.r0 == 0 && threadIdx.x == 0) {
+    const double g = slot_gamma(st, st.k);
+    gamma_f[ch.slot] = (float)g;
+    gamma_d[ch.slot] = (double)(float)g;  // the pass projects with the FP32 value
+  }
+}
+
+// grad = D (A x - b) (solver: renumbered G; API: caller's order at joff),
+// the fixed-point accumulator reset, and per-chunk FP32-pair partials
+// (mu^T g, ||g_+||^2).  The last block combines, per active slot and in chunk
+// order, the chunk partials with the pass's per-slot sums into the five
+// scalars of dualip_eval.
+__global__ void bepi_kernel(const RowChunk* __restrict__ rc, int nchunks,
+                            const SlotDesc* __restrict__ sd, float* __restrict__ grad, int solver,
+                            float4* __restrict__ cpart, const int32_t* __restrict__ act, int nact,
+                            const int2* __restrict__ crange, double* slot_part,
+                            const double* __restrict__ gamma_d, double* eval, unsigned* ticket) {
+  const RowChunk ch = rc[blockIdx.x];
+  const SlotDesc& d = sd[ch.slot];
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int jr = ch.r0 + threadIdx.x; jr < ch.r1; jr += blockDim.x) {
+    const long long yq = (long long)__ldcg(d.y + jr);
+    d.y[jr] = 0ull;
+    const float fh = __ll2float_rn(yq);
+    const float fl = __ll2float_rn(yq - __float2ll_rn(fh));
+    const float ah = __fmul_rn(fh, d.inv_sy), al = __fmul_rn(fl, d.inv_sy);
+    const float b = d.b_r[jr];
+    const float t = __fsub_rn(ah, b);
+    const float e = __fadd_rn(b_two_sum_err(ah, -b, t), al);
+    const float g = __fadd_rn(t, e);
+    const float gl = b_two_sum_err(t, e, g);
+    const float m = d.mu_r[jr];
+    const float pm = __fmul_rn(m, g);
+    b_pair_add(v.x, v.y, pm);
+    v.y = __fadd_rn(v.y, __fmaf_rn(m, gl, __fmaf_rn(m, g, -pm)));
+    if (g > 0.f) {
+      const float sq = __fmul_rn(g, g);
+      b_pair_add(v.z, v.w, sq);
+      v.w = __fadd_rn(v.w, __fmaf_rn(2.f * g, gl, __fmaf_rn(g, g, -sq)));
+    }
+    if (solver) {
+      const float dj = d.D[jr];
+      d.G[jr] = __fmaf_rn(dj, g, __fmul_rn(dj, gl));
+    } else {
+      grad[d.joff + d.orig_of[jr]] = __fadd_rn(g, gl);
+    }
+  }
+  const float4 t = block_pair_sum2(v);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    cpart[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == (unsigned)nchunks - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int a = threadIdx.x; a < nact; a += blockDim.x) {
+    const int s = act[a];
+    const int2 cr = crange[s];
+    float mh = 0.f, ml = 0.f, nh = 0.f, nl = 0.f;
+    for (int c = cr.x; c < cr.y; ++c) {
+      const float4 u = __ldcg(cpart + c);
+      b_pair_addp(mh, ml, u.x, u.y);
+      b_pair_addp(nh, nl, u.z, u.w);
+    }
+    const double cx = __ldcg(slot_part + 2 * s), wxx = __ldcg(slot_part + 2 * s + 1);
+    slot_part[2 * s] = 0.0;
+    slot_part[2 * s + 1] = 0.0;
+    const double mug = (double)mh + (double)ml, inf = (double)nh + (double)nl;
+    const double reg = 0.5 * gamma_d[s] * wxx;
+    double* o = eval + 5 * (size_t)s;
+    o[0] = cx + reg + mug;
+    o[1] = cx;
+    o[2] = reg;
+    o[3] = sqrt(inf);
+    o[4] = mug;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// ||y_k - y_{k-1}||^2 and ||G_k - G_{k-1}||^2 per chunk; the last block turns
+// them, per active slot, into the step (secant estimate capped by
+// max_step gamma / gamma0), the momentum weight and the stopping quantities,
+// and advances the slot's iteration counter.
+__global__ void bnorms_kernel(const RowChunk* __restrict__ rc, int nchunks,
+                              const SlotDesc* __restrict__ sd, SlotSolve* ss,
+                              float4* __restrict__ cpart, const int32_t* __restrict__ act,
+                              int nact, const int2* __restrict__ crange,
+                              const double* __restrict__ eval, unsigned* ticket) {
+  const RowChunk ch = rc[blockIdx.x];
+  const SlotDesc& d = sd[ch.slot];
+  const SlotSolve& st = ss[ch.slot];
+  const bool have_prev = st.k > 0 && !slot_restart(st, st.k);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (have_prev) {
+    for (int j = ch.r0 + threadIdx.x; j < ch.r1; j += blockDim.x) {
+      const float u = __fsub_rn(d.yv[j], d.yp[j]);
+      const float w = __fsub_rn(d.G[j], d.Gp[j]);
+      const float uu = __fmul_rn(u, u), ww = __fmul_rn(w, w);
+      b_pair_add(v.x, v.y, uu);
+      v.y = __fadd_rn(v.y, __fmaf_rn(u, u, -uu));
+      b_pair_add(v.z, v.w, ww);
+      v.w = __fadd_rn(v.w, __fmaf_rn(w, w, -ww));
+    }
+  }
+  const float4 t = block_pair_sum2(v);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    cpart[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == (unsigned)nchunks - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int a = threadIdx.x; a < nact; a += blockDim.x) {
+    const int s = act[a];
+    const int2 cr = crange[s];
+    float yh = 0.f, yl = 0.f, gh = 0.f, gl = 0.f;
+    for (int c = cr.x; c < cr.y; ++c) {
+      const float4 u = __ldcg(cpart + c);
+      b_pair_addp(yh, yl, u.x, u.y);
+      b_pair_addp(gh, gl, u.z, u.w);
+    }
+    SlotSolve& S = ss[s];
+    const int32_t k = S.k;
+    const bool hp = k > 0 && !slot_restart(S, k);
+    const double sdy = (double)yh + (double)yl, sdg = (double)gh + (double)gl;
+    const double gk = slot_gamma(S, k);
+    const double eta_max = S.max_step * gk / S.gamma0;
+    double eta;
+    if (hp) eta = sdg > 0.0 ? fmin(eta_max, sqrt(sdy) / sqrt(sdg)) : eta_max;
+    else eta = fmin(S.init_step, eta_max);
+    const double tk = slot_restart(S, k) ? 1.0 : S.t;
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+    S.eta = eta;
+    S.beta = (tk - 1.0) / tn;
+    S.t = tn;
+    S.sdy = sdy;
+    S.sdg = sdg;
+    const double* o = eval + 5 * (size_t)s;
+    const double g = o[0], p = o[1] + o[2];
+    S.gap_rel = fabs(o[4]) / fmax(1.0, fmax(fabs(p), fabs(g)));
+    S.infeas_rel = o[3] / fmax(1.0, S.bnorm);
+    S.last_gamma = gk;
+    S.k = k + 1;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// lambda_{k+1} = max(0, y_k + eta G_k), y_{k+1} = max(0, lambda_{k+1} +
+// beta (lambda_{k+1} - lambda_k)), per slot with its own eta and beta.  Runs
+// after bnorms, which has already advanced k; eta and beta are those of the
+// evaluated point.
+__global__ void bstep_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __restrict__ sd,
+                             const SlotSolve* __restrict__ ss) {
+  const RowChunk ch = rc[blockIdx.x];
+  const SlotDesc& d = sd[ch.slot];
+  const float eta = (float)ss[ch.slot].eta, beta = (float)ss[ch.slot].beta;
+  for (int j = ch.r0 + threadIdx.x; j < ch.r1; j += blockDim.x) {
+    const float yk = d.yv[j], g = d.G[j], lk = d.lam[j];
+    float ln = __fmaf_rn(eta, g, yk);
+    ln = ln > 0.f ? ln : 0.f;
+    float yn = __fmaf_rn(beta, __fsub_rn(ln, lk), ln);
+    yn = yn > 0.f ? yn : 0.f;
+    d.yp[j] = yk;
+    d.Gp[j] = g;
+    d.lam[j] = ln;
+    d.yv[j] = yn;
+  }
+}
+
+// lambda' = max(0, lambda_caller / D) in renumbered order, y = y_prev = lambda'.
+__global__ void binit_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __restrict__ sd,
+                             const float* __restrict__ lam_in) {
+  const RowChunk ch = rc[blockIdx.x];
+  const SlotDesc& d = sd[ch.slot];
+  for (int j = ch.r0 + threadIdx.x; j < ch.r1; j += blockDim.x) {
+    const float l = lam_in[d.joff + d.orig_of[j]] / d.D[j];
+    const float c = l > 0.f ? l : 0.f;
+    d.lam[j] = c;
+    d.yv[j] = c;
+    d.yp[j] = c;
+    d.G[j] = 0.f;
+    d.Gp[j] = 0.f;
+  }
+}
+
+// lambda_caller = D y_prev (the point of the last evaluation), caller's order.
+__global__ void bfinal_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __restrict__ sd,
+                              float* __restrict__ lam_out) {
+  const RowChunk ch = rc[blockIdx.x];
+  const SlotDesc& d = sd[ch.slot];
+  for (int j = ch.r0 + threadIdx.x; j < ch.r1; j += blockDim.x)
+    lam_out[d.joff + d.orig_of[j]] = __fmul_rn(d.D[j], d.yp[j]);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side ----
+namespace {
+
+struct Batch {
+  int n = 0;
+  int storage = DUALIP_EDGE_F32, weighted = 0;
+  int num_sms = 0;
+  std::vector<Problem*> prob;     // per slot
+  std::vector<SlotDesc> desc;     // host copy of the slot table
+  std::vector<char> active;       // slots in the joint lists
+  int64_t tile_edges = kTileEdges, tile_sources = kTileSources;
+  // per-slot tile lists for the current tile shape (host), and their joint
+  // concatenation for the active slots (device)
+  std::vector<std::vector<JointTile>> tiles;
+  std::vector<JointTile> jt_host;
+  std::vector<RowChunk> rc_host;
+  std::vector<int32_t> act_host;
+  std::vector<int2> crange_host;
+  int64_t ntiles = 0;
+  int nchunks = 0;
+  bool lists_ok = false;
+  // device
+  SlotDesc* d_slots = nullptr;
+  float* d_gamma_f = nullptr;
+  double* d_gamma_d = nullptr;
+  double* d_slot_part = nullptr;
+  double* d_eval = nullptr;
+  SlotSolve* d_ss = nullptr;
+  int32_t* d_act = nullptr;
+  int2* d_crange = nullptr;
+  unsigned* d_tickets = nullptr;
+  DeviceStatus* d_status = nullptr;
+  JointTile* d_jt = nullptr;
+  size_t jt_cap = 0;
+  RowChunk* d_rc = nullptr;
+  float4* d_cpart = nullptr;
+  size_t rc_cap = 0;
+  // pinned staging
+  double* h_gamma = nullptr;  // n doubles then n floats
+  double* h_eval = nullptr;   // 5 n
+  SlotSolve* h_ss = nullptr;  // n
+  // solver vectors (6 per slot, renumbered order), allocated by the solver
+  std::vector<float*> vecs;
+  int row_normalize = -1;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;        // stream ordering
+  cudaEvent_t ev_stage = nullptr;  // the gamma staging copies have been read
+  cudaEvent_t ev_use = nullptr;    // the last queued use of the joint lists
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  int grid = 0;
+};
+
+template <class T>
+cudaError_t grow(T** p, size_t& cap, size_t need) {
+  if (need <= cap && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  cap = 0;
+  const size_t n = std::max<size_t>(need, 1) * 5 / 4 + 16;
+  cudaError_t e = cudaMalloc(p, sizeof(T) * n);
+  if (e == cudaSuccess) cap = n;
+  return e;
+}
+
+void batch_free(Batch& B) {
+  if (B.stream) cudaStreamSynchronize(B.stream);
+  if (B.graph) cudaGraphExecDestroy(B.graph);
+  void* bufs[] = {B.d_slots, B.d_gamma_f, B.d_gamma_d, B.d_slot_part, B.d_eval, B.d_ss, B.d_act,
+                  B.d_crange, B.d_tickets, B.d_status, B.d_jt, B.d_rc, B.d_cpart};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  for (float* p : B.vecs)
+    if (p) cudaFree(p);
+  if (B.h_gamma) cudaFreeHost(B.h_gamma);
+  if (B.h_eval) cudaFreeHost(B.h_eval);
+  if (B.h_ss) cudaFreeHost(B.h_ss);
+  if (B.ev) cudaEventDestroy(B.ev);
+  if (B.ev_stage) cudaEventDestroy(B.ev_stage);
+  if (B.ev_use) cudaEventDestroy(B.ev_use);
+  if (B.stream) cudaStreamDestroy(B.stream);
+}
+
+void slot_tiles(const Problem& P, int slot, int64_t max_e, int64_t max_s,
+                std::vector<JointTile>& out) {
+  std::vector<int64_t> t, te;
+  build_tiles(P.off_host, t, te, max_e, max_s);
+  out.clear();
+  out.reserve(t.size());
+  for (size_t k = 0; k + 1 < t.size(); ++k)
+    out.push_back(JointTile{t[k], t[k + 1], te[k], te[k + 1], slot, 0});
+}
+
+cudaError_t build_slot_tiles(Batch& B) {
+  B.tiles.assign(B.n, {});
+  for (int s = 0; s < B.n; ++s) slot_tiles(*B.prob[s], s, B.tile_edges, B.tile_sources, B.tiles[s]);
+  B.lists_ok = false;
+  return cudaSuccess;
+}
+
+// Joint tile and row-chunk lists of the active slots, uploaded on B.stream.
+cudaError_t rebuild_lists(Batch& B) {
+  if (B.lists_ok) return cudaSuccess;
+  B.jt_host.clear();
+  B.rc_host.clear();
+  B.act_host.clear();
+  B.crange_host.assign(B.n, int2{0, 0});
+  for (int s = 0; s < B.n; ++s) {
+    if (!B.active[s]) continue;
+    B.act_host.push_back(s);
+    B.jt_host.insert(B.jt_host.end(), B.tiles[s].begin(), B.tiles[s].end());
+    const int c0 = (int)B.rc_host.size();
+    for (int32_t r = 0; r < B.prob[s]->J; r += kChunkRows)
+      B.rc_host.push_back(RowChunk{s, r, std::min<int32_t>(B.prob[s]->J, r + kChunkRows), 0});
+    B.crange_host[s] = int2{c0, (int)B.rc_host.size()};
+  }
+  B.ntiles = (int64_t)B.jt_host.size();
+  B.nchunks = (int)B.rc_host.size();
+  cudaError_t e;
+  // the lists may still be read by queued work, here or on a caller's stream
+  cudaStreamSynchronize(B.stream);
+  cudaEventSynchronize(B.ev_use);
+  if ((e = grow(&B.d_jt, B.jt_cap, B.jt_host.size()))) return e;
+  size_t rc_cap = B.rc_cap;
+  if ((e = grow(&B.d_rc, B.rc_cap, B.rc_host.size()))) return e;
+  if (B.rc_cap != rc_cap || !B.d_cpart) {
+    if (B.d_cpart) cudaFree(B.d_cpart);
+    if ((e = cudaMalloc(&B.d_cpart, sizeof(float4) * B.rc_cap))) return e;
+  }
+  if ((!B.jt_host.empty() &&
+       (e = cudaMemcpyAsync(B.d_jt, B.jt_host.data(), sizeof(JointTile) * B.jt_host.size(),
+                            cudaMemcpyHostToDevice, B.stream))) ||
+      (!B.rc_host.empty() &&
+       (e = cudaMemcpyAsync(B.d_rc, B.rc_host.data(), sizeof(RowChunk) * B.rc_host.size(),
+                            cudaMemcpyHostToDevice, B.stream))) ||
+      (!B.act_host.empty() &&
+       (e = cudaMemcpyAsync(B.d_act, B.act_host.data(), sizeof(int32_t) * B.act_host.size(),
+                            cudaMemcpyHostToDevice, B.stream))) ||
+      (e = cudaMemcpyAsync(B.d_crange, B.crange_host.data(), sizeof(int2) * B.n,
+                           cudaMemcpyHostToDevice, B.stream)) ||
+      (e = cudaStreamSynchronize(B.stream)))
+    return e;
+  B.grid = (int)std::max<int64_t>(1, std::min<int64_t>(B.num_sms, B.ntiles));
+  if (B.graph) cudaGraphExecDestroy(B.graph);
+  B.graph = nullptr;
+  B.lists_ok = true;
+  return cudaSuccess;
+}
+
+cudaError_t upload_slots(Batch& B) {
+  return cudaMemcpyAsync(B.d_slots, B.desc.data(), sizeof(SlotDesc) * B.n, cudaMemcpyHostToDevice,
+                         B.stream);
+}
+
+// One evaluation of every active slot on stream s.  solver: the ascent's
+// point and vectors; otherwise lam / grad are joint caller vectors.
+cudaError_t enqueue_batch_eval(Batch& B, const float* lam, float* grad, int solver,
+                               cudaStream_t s) {
+  if (B.nchunks == 0) return cudaSuccess;
+  cudaError_t e;
+  bprep_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.d_slots, lam, solver, B.d_ss, B.d_gamma_f,
+                                         B.d_gamma_d);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = launch_pass_batch(B.storage, B.weighted, B.d_jt, B.ntiles, B.d_slots, B.d_gamma_f,
+                             B.d_slot_part, B.d_status, B.grid, s)))
+    return e;
+  bepi_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.nchunks, B.d_slots, grad, solver, B.d_cpart,
+                                        B.d_act, (int)B.act_host.size(), B.d_crange,
+                                        B.d_slot_part, B.d_gamma_d, B.d_eval, B.d_tickets);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_batch_iteration(Batch& B, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = enqueue_batch_eval(B, nullptr, nullptr, 1, s))) return e;
+  if (B.nchunks == 0) return cudaSuccess;
+  bnorms_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.nchunks, B.d_slots, B.d_ss, B.d_cpart,
+                                          B.d_act, (int)B.act_host.size(), B.d_crange, B.d_eval,
+                                          B.d_tickets + 1);
+  if ((e = cudaGetLastError())) return e;
+  bstep_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.d_slots, B.d_ss);
+  return cudaGetLastError();
+}
+
+cudaError_t run_batch_chunk(Batch& B, int n, bool use_graph) {
+  cudaError_t e;
+  if (!use_graph) {
+    for (int i = 0; i < n; ++i)
+      if ((e = enqueue_batch_iteration(B, B.stream))) return e;
+    return cudaSuccess;
+  }
+  if (!B.graph || B.graph_len != n) {
+    if (B.graph) cudaGraphExecDestroy(B.graph);
+    B.graph = nullptr;
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal))) return e;
+    for (int i = 0; i < n && !e; ++i) e = enqueue_batch_iteration(B, B.stream);
+    const cudaError_t e2 = cudaStreamEndCapture(B.stream, &g);
+    if (e || e2) {
+      if (g) cudaGraphDestroy(g);
+      return e ? e : e2;
+    }
+    e = cudaGraphInstantiate(&B.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e) return e;
+    B.graph_len = n;
+  }
+  return cudaGraphLaunch(B.graph, B.stream);
+}
+
+dualip_status batch_status(Batch& B) {
+  DeviceStatus h{};
+  cudaError_t e = cudaMemcpyAsync(&h, B.d_status, sizeof(h), cudaMemcpyDeviceToHost, B.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the batch status");
+  if (h.err & kErrTimeout) return fail(DUALIP_ETIMEOUT, "a device wait timed out in a batched pass");
+  if (h.err) return fail(DUALIP_EINVAL, "a batched pass met an invalid tile");
+  return DUALIP_OK;
+}
+
+}  // namespace
+}  // namespace dualip
+
+struct dualip_batch {
+  dualip::Batch b;
+};
+
+using namespace dualip;
+
+namespace {
+
+bool gamma_ok(double g) { return std::isfinite(g) && g >= 1e-30 && g <= 1e30; }
+
+// joint lists of every slot (API calls evaluate all problems)
+dualip_status ensure_all_active(Batch& B) {
+  bool all = true;
+  for (int s = 0; s < B.n; ++s) all = all && B.active[s];
+  if (all && B.lists_ok) return DUALIP_OK;
+  std::fill(B.active.begin(), B.active.end(), 1);
+  B.lists_ok = false;
+  cudaError_t e = rebuild_lists(B);
+  return e ? cuda_fail(e, "building the batch lists") : DUALIP_OK;
+}
+
+// order stream b after stream a
+cudaError_t order(Batch& B, cudaStream_t a, cudaStream_t b) {
+  cudaError_t e = cudaEventRecord(B.ev, a);
+  if (!e) e = cudaStreamWaitEvent(b, B.ev, 0);
+  return e;
+}
+
+dualip_status stage_gammas(Batch& B, const double* gammas, cudaStream_t s) {
+  for (int k = 0; k < B.n; ++k)
+    if (!gamma_ok(gammas[k])) return fail(DUALIP_EINVAL, "every gamma must be in [1e-30, 1e30]");
+  // the staging buffer may still be read by an earlier call's copy
+  cudaError_t e = cudaEventSynchronize(B.ev_stage);
+  if (e) return cuda_fail(e, "waiting for the gamma staging buffer");
+  float* gf = reinterpret_cast<float*>(B.h_gamma + B.n);
+  for (int k = 0; k < B.n; ++k) {
+    B.h_gamma[k] = gammas[k];
+    gf[k] = (float)gammas[k];
+  }
+  if ((e = cudaMemcpyAsync(B.d_gamma_d, B.h_gamma, sizeof(double) * B.n, cudaMemcpyHostToDevice,
+                           s)) ||
+      (e = cudaMemcpyAsync(B.d_gamma_f, gf, sizeof(float) * B.n, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaEventRecord(B.ev_stage, s)))
+    return cuda_fail(e, "uploading gammas");
+  return DUALIP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dualip_status dualip_batch_create(int32_t n, dualip_problem* const* problems, dualip_batch** out) {
+  if (!out) return fail(DUALIP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !problems) return fail(DUALIP_EINVAL, "need n >= 1 problems");
+  for (int k = 0; k < n; ++k) {
+    if (!problems[k]) return fail(DUALIP_EINVAL, "a problem handle is NULL");
+    const Problem& P = problems[k]->p;
+    const Problem& P0 = problems[0]->p;
+    if (P.storage != P0.storage || P.weighted != P0.weighted || P.device != P0.device)
+      return fail(DUALIP_EINVAL, "problems of a batch share storage, primal_scaling and device");
+    for (int m = 0; m < k; ++m)
+      if (problems[m] == problems[k]) return fail(DUALIP_EINVAL, "a problem appears twice");
+  }
+  dualip_batch* h = new dualip_batch();
+  Batch& B = h->b;
+  auto bail = [&](dualip_status st) {
+    batch_free(B);
+    delete h;
+    return st;
+  };
+  B.n = n;
+  B.storage = problems[0]->p.storage;
+  B.weighted = problems[0]->p.weighted;
+  B.num_sms = problems[0]->p.num_sms;
+  B.active.assign(n, 1);
+  B.vecs.assign(n, nullptr);
+  int64_t joff = 0;
+  for (int k = 0; k < n; ++k) {
+    Problem& P = problems[k]->p;
+    B.prob.push_back(&P);
+    SlotDesc d{};
+    d.off = P.off;
+    d.dst = P.dst;
+    d.ca2 = P.ca2;
+    d.ca = P.ca;
+    d.mu_r = P.mu_r;
+    d.y = P.y;
+    d.orig_of = P.orig_of;
+    d.b_r = P.b_r;
+    d.J = P.J;
+    d.h_mu = P.h_mu;
+    d.h_y = P.h_y;
+    d.sy = ldexpf(1.0f, P.exp_y);
+    d.inv_sy = ldexpf(1.0f, -P.exp_y);
+    d.joff = joff;
+    joff += P.J;
+    B.desc.push_back(d);
+  }
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&B.stream, cudaStreamNonBlocking)) ||
+      (e = cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming)) ||
+      (e = cudaEventCreateWithFlags(&B.ev_stage, cudaEventDisableTiming)) ||
+      (e = cudaEventCreateWithFlags(&B.ev_use, cudaEventDisableTiming)) ||
+      (e = cudaMalloc(&B.d_slots, sizeof(SlotDesc) * n)) ||
+      (e = cudaMalloc(&B.d_gamma_f, sizeof(float) * n)) ||
+      (e = cudaMalloc(&B.d_gamma_d, sizeof(double) * n)) ||
+      (e = cudaMalloc(&B.d_slot_part, sizeof(double) * 2 * n)) ||
+      (e = cudaMalloc(&B.d_eval, sizeof(double) * 5 * n)) ||
+      (e = cudaMalloc(&B.d_ss, sizeof(SlotSolve) * n)) ||
+      (e = cudaMalloc(&B.d_act, sizeof(int32_t) * n)) ||
+      (e = cudaMalloc(&B.d_crange, sizeof(int2) * n)) ||
+      (e = cudaMalloc(&B.d_tickets, sizeof(unsigned) * 2)) ||
+      (e = cudaMalloc(&B.d_status, sizeof(DeviceStatus))) ||
+      (e = cudaMallocHost(&B.h_gamma, sizeof(double) * 2 * n)) ||
+      (e = cudaMallocHost(&B.h_eval, sizeof(double) * 5 * n)) ||
+      (e = cudaMallocHost(&B.h_ss, sizeof(SlotSolve) * n)))
+    return bail(cuda_fail(e, "allocating the batch"));
+  if ((e = cudaMemsetAsync(B.d_slot_part, 0, sizeof(double) * 2 * n, B.stream)) ||
+      (e = cudaMemsetAsync(B.d_tickets, 0, sizeof(unsigned) * 2, B.stream)) ||
+      (e = cudaMemsetAsync(B.d_status, 0, sizeof(DeviceStatus), B.stream)) ||
+      (e = cudaMemsetAsync(B.d_eval, 0, sizeof(double) * 5 * n, B.stream)) ||
+      (e = cudaEventRecord(B.ev_stage, B.stream)) || (e = cudaEventRecord(B.ev_use, B.stream)) ||
+      (e = upload_slots(B)) || (e = build_slot_tiles(B)) || (e = rebuild_lists(B)) ||
+      (e = cudaStreamSynchronize(B.stream)))
+    return bail(cuda_fail(e, "initialising the batch"));
+  *out = h;
+  return DUALIP_OK;
+}
+
+void dualip_batch_destroy(dualip_batch* b) {
+  if (!b) return;
+  batch_free(b->b);
+  delete b;
+}
+
+dualip_status dualip_batch_dual_grad_async(dualip_batch* b, const float* lambda,
+                                           const double* gammas, float* grad, double* out_dev,
+                                           void* stream) {
+  if (!b || !lambda || !gammas || !grad) return fail(DUALIP_EINVAL, "NULL argument");
+  Batch& B = b->b;
+  cudaStream_t s = as_stream(stream);
+  dualip_status st = ensure_all_active(B);
+  if (st) return st;
+  if ((st = stage_gammas(B, gammas, s))) return st;
+  cudaError_t e = enqueue_batch_eval(B, lambda, grad, 0, s);
+  if (!e) e = cudaEventRecord(B.ev_use, s);
+  if (!e && out_dev)
+    e = cudaMemcpyAsync(out_dev, B.d_eval, sizeof(double) * 5 * B.n, cudaMemcpyDeviceToDevice, s);
+  return e ? cuda_fail(e, "launching the batched evaluation") : DUALIP_OK;
+}
+
+dualip_status dualip_batch_dual_grad(dualip_batch* b, const float* lambda, const double* gammas,
+                                     float* grad, dualip_eval* out, void* stream) {
+  dualip_status st = dualip_batch_dual_grad_async(b, lambda, gammas, grad, nullptr, stream);
+  if (st) return st;
+  Batch& B = b->b;
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(B.h_eval, B.d_eval, sizeof(double) * 5 * B.n, cudaMemcpyDeviceToHost,
+                           s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(e, "reading the batched scalars");
+  if ((e = order(B, s, B.stream))) return cuda_fail(e, "ordering streams");
+  if ((st = batch_status(B))) return st;
+  if (out)
+    for (int k = 0; k < B.n; ++k) {
+      const double* o = B.h_eval + 5 * k;
+      out[k].dual_obj = o[0];
+      out[k].primal_obj = o[1];
+      out[k].reg = o[2];
+      out[k].infeas_l2 = o[3];
+      out[k].lambda_dot_grad = o[4];
+    }
+  return DUALIP_OK;
+}
+
+dualip_status dualip_batch_set_tile_shape(dualip_batch* b, int32_t edges, int32_t sources) {
+  if (!b) return fail(DUALIP_EINVAL, "batch is NULL");
+  if (edges < 1 || edges > kTileEdges || sources < 1 || sources > kTileSources)
+    return fail(DUALIP_EINVAL, "tile shape out of range");
+  Batch& B = b->b;
+  B.tile_edges = edges;
+  B.tile_sources = sources;
+  cudaError_t e = build_slot_tiles(B);
+  if (!e) e = rebuild_lists(B);
+  return e ? cuda_fail(e, "retiling the batch") : DUALIP_OK;
+}
+
+dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* total_J,
+                                    int64_t* total_E, int64_t* ntiles, int32_t* tile_edges,
+                                    int32_t* tile_sources) {
+  if (!b) return fail(DUALIP_EINVAL, "batch is NULL");
+  const Batch& B = b->b;
+  int64_t J = 0, E = 0, T = 0;
+  for (int s = 0; s < B.n; ++s) {
+    J += B.prob[s]->J;
+    E += B.prob[s]->E;
+    T += (int64_t)B.tiles[s].size();
+  }
+  if (n) *n = B.n;
+  if (total_J) *total_J = J;
+  if (total_E) *total_E = E;
+  if (ntiles) *ntiles = T;
+  if (tile_edges) *tile_edges = (int32_t)B.tile_edges;
+  if (tile_sources) *tile_sources = (int32_t)B.tile_sources;
+  return DUALIP_OK;
+}
+
+dualip_status dualip_batch_solve(dualip_batch* b, const dualip_solve_opts* opts, int32_t n_opts,
+                                 float* lambda_inout, dualip_solve_result* results,
+                                 void* stream) {
+  if (!b || !opts || !lambda_inout) return fail(DUALIP_EINVAL, "NULL argument");
+  Batch& B = b->b;
+  if (n_opts != 1 && n_opts != B.n) return fail(DUALIP_EINVAL, "n_opts must be 1 or n");
+  for (int k = 0; k < n_opts; ++k) {
+    const dualip_solve_opts& o = opts[k];
+    if (!(o.gamma0 > 0) || !(o.gamma_final > 0) || !std::isfinite(o.gamma0) ||
+        o.gamma_final > o.gamma0 || o.gamma_final < 1e-30)
+      return fail(DUALIP_EINVAL, "need 1e-30 <= gamma_final <= gamma0 < inf");
+    if (o.max_iters < 1 || o.check_every < 1 || !(o.max_step > 0) || !(o.init_step > 0))
+      return fail(DUALIP_EINVAL, "need max_iters >= 1, check_every >= 1, positive steps");
+  }
+  auto O = [&](int k) -> const dualip_solve_opts& { return opts[n_opts == 1 ? 0 : k]; };
+  const int check_every = opts[0].check_every;
+  const bool use_graph = opts[0].use_graph != 0;
+  cudaStream_t us = as_stream(stream);
+  cudaError_t e;
+  // solver vectors (renumbered): lam, y, y_prev, G, G_prev, D per slot
+  for (int k = 0; k < B.n; ++k) {
+    if (B.vecs[k]) continue;
+    if ((e = cudaMalloc(&B.vecs[k], sizeof(float) * 6 * std::max<int32_t>(B.prob[k]->J, 1))))
+      return cuda_fail(e, "allocating solver vectors");
+    const int32_t J = B.prob[k]->J;
+    float* v = B.vecs[k];
+    SlotDesc& d = B.desc[k];
+    d.lam = v;
+    d.yv = v + J;
+    d.yp = v + 2 * (size_t)J;
+    d.G = v + 3 * (size_t)J;
+    d.Gp = v + 4 * (size_t)J;
+    d.D = v + 5 * (size_t)J;
+    B.row_normalize = -1;
+  }
+  if ((e = order(B, us, B.stream))) return cuda_fail(e, "ordering streams");
+  const int rn = opts[0].row_normalize ? 1 : 0;
+  if (B.row_normalize != rn) {
+    for (int k = 0; k < B.n; ++k)
+      if ((e = compute_row_scale(*B.prob[k], rn, B.desc[k].D, B.stream)))
+        return cuda_fail(e, "computing row scales");
+    B.row_normalize = rn;
+  }
+  for (int k = 0; k < B.n; ++k) {
+    SlotSolve& S = B.h_ss[k];
+    std::memset(&S, 0, sizeof(S));
+    S.gamma0 = O(k).gamma0;
+    S.gamma_final = O(k).gamma_final;
+    S.max_step = O(k).max_step;
+    S.init_step = O(k).init_step;
+    S.bnorm = B.prob[k]->bnorm;
+    S.halve_every = O(k).halve_every;
+    S.restart = O(k).restart_on_gamma_change ? 1 : 0;
+    S.t = 1.0;
+  }
+  std::fill(B.active.begin(), B.active.end(), 1);
+  B.lists_ok = false;
+  if ((e = upload_slots(B)) ||
+      (e = cudaMemcpyAsync(B.d_ss, B.h_ss, sizeof(SlotSolve) * B.n, cudaMemcpyHostToDevice,
+                           B.stream)) ||
+      (e = rebuild_lists(B)))
+    return cuda_fail(e, "initialising the batched solver");
+  if (B.nchunks) {
+    binit_kernel<<<B.nchunks, 256, 0, B.stream>>>(B.d_rc, B.d_slots, lambda_inout);
+    if ((e = cudaGetLastError())) return cuda_fail(e, "initialising lambda");
+  }
+  std::vector<int32_t> iters(B.n, 0);
+  std::vector<char> conv(B.n, 0);
+  std::vector<double> evals(5 * (size_t)B.n, 0.0);
+  std::vector<SlotSolve> last(B.n);
+  int n_active = B.n;
+  while (n_active > 0) {
+    int n_it = check_every;
+    for (int k = 0; k < B.n; ++k)
+      if (B.active[k]) n_it = std::min(n_it, O(k).max_iters - iters[k]);
+    if ((e = run_batch_chunk(B, n_it, use_graph && n_it == check_every)))
+      return cuda_fail(e, "running batched iterations");
+    if ((e = cudaMemcpyAsync(B.h_ss, B.d_ss, sizeof(SlotSolve) * B.n, cudaMemcpyDeviceToHost,
+                             B.stream)) ||
+        (e = cudaMemcpyAsync(B.h_eval, B.d_eval, sizeof(double) * 5 * B.n,
+                             cudaMemcpyDeviceToHost, B.stream)) ||
+        (e = cudaStreamSynchronize(B.stream)))
+      return cuda_fail(e, "reading the solver state");
+    dualip_status st = batch_status(B);
+    if (st) return st;
+    std::vector<RowChunk> fin;
+    for (int k = 0; k < B.n; ++k) {
+      if (!B.active[k]) continue;
+      iters[k] += n_it;
+      const SlotSolve& S = B.h_ss[k];
+      const bool ok = O(k).stop_on_tol && iters[k] % check_every == 0 &&
+                      S.last_gamma == O(k).gamma_final && S.gap_rel <= O(k).tol_gap &&
+                      S.infeas_rel <= O(k).tol_infeas;
+      if (ok || iters[k] >= O(k).max_iters) {
+        conv[k] = ok ? 1 : 0;
+        last[k] = S;
+        std::copy(B.h_eval + 5 * k, B.h_eval + 5 * k + 5, evals.begin() + 5 * k);
+        B.active[k] = 0;
+        --n_active;
+        for (int32_t r = 0; r < B.prob[k]->J; r += kChunkRows)
+          fin.push_back(RowChunk{k, r, std::min<int32_t>(B.prob[k]->J, r + kChunkRows), 0});
+      }
+    }
+    if (!fin.empty()) {
+      // lambda of the finished problems; the joint lists are rebuilt after
+      if ((e = cudaMemcpyAsync(B.d_rc, fin.data(), sizeof(RowChunk) * fin.size(),
+                               cudaMemcpyHostToDevice, B.stream)))
+        return cuda_fail(e, "uploading chunks");
+      bfinal_kernel<<<(int)fin.size(), 256, 0, B.stream>>>(B.d_rc, B.d_slots, lambda_inout);
+      if ((e = cudaGetLastError()) || (e = cudaStreamSynchronize(B.stream)))
+        return cuda_fail(e, "writing lambda");
+      B.lists_ok = false;
+      if ((e = rebuild_lists(B))) return cuda_fail(e, "rebuilding the batch lists");
+    }
+  }
+  if ((e = order(B, B.stream, us))) return cuda_fail(e, "ordering streams");
+  bool all = true;
+  for (int k = 0; k < B.n; ++k) {
+    all = all && conv[k];
+    if (!results) continue;
+    dualip_solve_result& r = results[k];
+    r.iters = iters[k];
+    r.converged = conv[k];
+    r.last.dual_obj = evals[5 * k];
+    r.last.primal_obj = evals[5 * k + 1];
+    r.last.reg = evals[5 * k + 2];
+    r.last.infeas_l2 = evals[5 * k + 3];
+    r.last.lambda_dot_grad = evals[5 * k + 4];
+    r.gap_rel = last[k].gap_rel;
+    r.infeas_rel = last[k].infeas_rel;
+    r.gamma = last[k].last_gamma;
+  }
+  // the lists of every slot again, for later evaluations
+  std::fill(B.active.begin(), B.active.end(), 1);
+  B.lists_ok = false;
+  if (!all && opts[0].stop_on_tol)
+    return fail(DUALIP_ENOTCONVERGED, "some problem reached max_iters before its tolerances");
+  return DUALIP_OK;
+}
+
+dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* result,
+                                    void* stream) {
+  if (!b) return fail(DUALIP_EINVAL, "batch is NULL");
+  Batch& B = b->b;
+  cudaStream_t s = as_stream(stream);
+  dualip_autotune_result r;
+  std::memset(&r, 0, sizeof(r));
+  // segment-length histogram: sources by degree, log2 buckets
+  int64_t nsrc = 0, nedge = 0;
+  for (int k = 0; k < B.n; ++k) {
+    const std::vector<int64_t>& off = B.prob[k]->off_host;
+    for (size_t i = 0; i + 1 < off.size(); ++i) {
+      const int64_t d = off[i + 1] - off[i];
+      int bk = 0;
+      while (bk < 31 && (int64_t(2) << bk) <= d) ++bk;
+      ++r.degree_hist[bk];
+    }
+    nsrc += (int64_t)off.size() - 1;
+    nedge += off.empty() ? 0 : off.back();
+  }
+  // the degree below which 99% of the sources lie (bucket upper bound)
+  int64_t p99 = 1, acc = 0;
+  for (int bk = 0; bk < 32; ++bk) {
+    acc += r.degree_hist[bk];
+    if (acc >= nsrc - nsrc / 100) {
+      p99 = int64_t(2) << bk;
+      break;
+    }
+  }
+  const double mean = nsrc ? (double)nedge / (double)nsrc : 1.0;
+  // candidates: a shape is dropped when most of its tiles would hold a single
+  // source (p99 degree above half the edge budget) or when its source cap
+  // would stop tiles at under a quarter of the edge budget
+  const int32_t cand[][2] = {{3072, 256}, {3072, 128}, {2048, 256}, {2048, 128},
+                             {1536, 128}, {1024, 128}, {1024, 64},  {512, 64}};
+  std::vector<int> keep;
+  for (int c = 0; c < 8; ++c) {
+    const double e = cand[c][0], src = cand[c][1];
+    if (p99 > e / 2 && c != 0) continue;
+    if (src * mean < e / 4 && c != 0) continue;
+    keep.push_back(c);
+  }
+  dualip_status st = DUALIP_OK;
+  std::vector<float*> bufs(2, nullptr);
+  int64_t Jt = 0;
+  for (int k = 0; k < B.n; ++k) Jt += B.prob[k]->J;
+  cudaError_t e;
+  if ((e = cudaMalloc(&bufs[0], sizeof(float) * std::max<int64_t>(Jt, 1))) ||
+      (e = cudaMalloc(&bufs[1], sizeof(float) * std::max<int64_t>(Jt, 1))) ||
+      (e = cudaMemsetAsync(bufs[0], 0, sizeof(float) * std::max<int64_t>(Jt, 1), s)))
+    st = cuda_fail(e, "allocating autotune buffers");
+  std::vector<double> gam(B.n, 1e-2);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!st && ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))))
+    st = cuda_fail(e, "creating events");
+  double best = 1e300;
+  int best_c = keep.empty() ? 0 : keep[0];
+  for (size_t q = 0; q < keep.size() && !st; ++q) {
+    const int c = keep[q];
+    if ((st = dualip_batch_set_tile_shape(b, cand[c][0], cand[c][1]))) break;
+    if ((st = ensure_all_active(B))) break;
+    const int reps = 3;
+    float ms = 0.f;
+    for (int w = 0; w < 1 + reps && !st; ++w) {
+      if (w == 1 && (e = cudaEventRecord(e0, s))) st = cuda_fail(e, "timing");
+      if (!st) st = dualip_batch_dual_grad_async(b, bufs[0], gam.data(), bufs[1], nullptr, s);
+    }
+    if (st) break;
+    if ((e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) ||
+        (e = cudaEventElapsedTime(&ms, e0, e1))) {
+      st = cuda_fail(e, "timing");
+      break;
+    }
+    const int slot = (int)q;
+    r.tile_edges[slot] = cand[c][0];
+    r.tile_sources[slot] = cand[c][1];
+    r.ms[slot] = ms / reps;
+    r.n_candidates = slot + 1;
+    if (ms / reps < best) {
+      best = ms / reps;
+      best_c = c;
+      r.chosen = slot;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  for (float* p : bufs)
+    if (p) cudaFree(p);
+  if (st) return st;
+  if ((st = dualip_batch_set_tile_shape(b, cand[best_c][0], cand[best_c][1]))) return st;
+  if ((st = batch_status(B))) return st;
+  if (result) *result = r;
+  return DUALIP_OK;
+}
+
+}  // extern "C"

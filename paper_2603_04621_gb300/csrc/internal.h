@@ -22,9 +22,6 @@ namespace dualip {
 #ifndef DUALIP_CONSUMER_WARPS
 #define DUALIP_CONSUMER_WARPS 16
 #endif
-#ifndef DUALIP_L2_PREFETCH_TILES
-#define DUALIP_L2_PREFETCH_TILES 0
-#endif
 #ifndef DUALIP_PRIV_DESTS
 #define DUALIP_PRIV_DESTS 2048
 #endif
@@ -34,7 +31,6 @@ constexpr int kTileEdges = DUALIP_TILE_EDGES;       // edge capacity of a stage
 #endif
 constexpr int kTileSources = DUALIP_TILE_SOURCES;   // source capacity of a stage
 constexpr int kStages = DUALIP_STAGES;               // depth of the staging ring
-constexpr int kL2PrefetchTiles = DUALIP_L2_PREFETCH_TILES;  // L2 prefetch distance (tiles)
 constexpr int kConsumerWarps = DUALIP_CONSUMER_WARPS;  // warps that project sources
 #ifndef DUALIP_SMEM_RED64
 #define DUALIP_SMEM_RED64 0
@@ -82,6 +78,53 @@ struct EpiParams {
   DeviceStatus* status;
 };
 
+// ------------------------------------------------------------ batches ----
+// Several problems evaluated by one launch of the pass.  Every problem keeps
+// its own packed edges, renumbering, fixed-point scale and J-length arrays;
+// it occupies a slot of a device table.  The pass walks a joint list of tiles
+// (each tile belongs to one slot; tiles of a slot are contiguous), and the
+// J-length kernels walk a joint list of row chunks.
+
+// One tile of a batched pass: a run of whole sources of one slot's problem.
+struct JointTile {
+  int64_t s0, s1;  // sources [s0, s1) of the slot's problem
+  int64_t e0, e1;  // edges [e0, e1)
+  int32_t slot;
+  int32_t pad;
+};
+// Rows [r0, r1) of one slot's problem, for the batched J-length kernels.
+struct RowChunk {
+  int32_t slot;
+  int32_t r0, r1;
+  int32_t pad;
+};
+// Per-slot arrays and scalars (device table).
+struct SlotDesc {
+  // the problem's own device arrays
+  const int64_t* off;
+  const int32_t* dst;
+  const float2* ca2;
+  const uint32_t* ca;
+  float* mu_r;                // [J] renumbered dual point of the pass
+  unsigned long long* y;      // [J] fixed-point A x (reset by the epilogue)
+  const int32_t* orig_of;     // [J] renumbered -> caller's id
+  const float* b_r;           // [J] budgets, renumbered
+  int32_t J, h_mu, h_y, pad;
+  float sy, inv_sy;           // 2^exp_y, 2^-exp_y
+  int64_t joff;               // offset of this problem in joint caller vectors
+  // solver vectors in the caller's numbering (null outside the solver)
+  float *lam, *yv, *yp, *G, *Gp, *D;
+};
+// Solver scalars of one slot (the ascent of the single-problem solver, per
+// problem; every field is written on the device except the options).
+struct SlotSolve {
+  double gamma0, gamma_final, max_step, init_step, bnorm;
+  double t, eta, beta;
+  double gap_rel, infeas_rel, last_gamma;
+  double sdy, sdg;            // ||y_k - y_{k-1}||^2, ||G_k - G_{k-1}||^2
+  int32_t k, halve_every, restart, pad;
+};
+
 // Kernel parameters of one pass (one dual evaluation).
 struct PassParams {
   // edges
@@ -107,6 +150,12 @@ struct PassParams {
                           // pair hi + lo (double-float)
   float* x_out;           // [E] optional primal output (edge order)
   DeviceStatus* status;
+  // batched pass: tiles from jt, per-slot arrays from slots, per-slot gamma,
+  // per-slot FP64 partials (sum c x, sum w x^2) by atomics
+  const JointTile* jt;
+  const SlotDesc* slots;
+  const float* gamma_of;
+  double* slot_part;
 };
 
 struct Problem {
@@ -143,6 +192,7 @@ struct Problem {
   double bnorm = 0.0;           // ||b||_2
   void* solve_ctx = nullptr;    // solver state, created by the first dualip_solve
   std::vector<cudaEvent_t> prof_ev;  // 4 per recorded evaluation
+  std::vector<int64_t> off_host;     // source offsets (tiling of batched passes)
   int prof_max = 0, prof_used = 0;
   std::vector<void*> allocations;
 };
@@ -153,6 +203,13 @@ cudaError_t configure_pass_kernels();
 cudaError_t launch_prep(const Problem& P, const float* lambda, const float* D, cudaStream_t s);
 cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, float* x_out,
                         cudaStream_t s);
+// solve.cu: D_j = (sum_{e->j} a_e^2 / w_e)^(-1/2) (1 for an empty row), or 1
+// everywhere without row normalisation, in renumbered order.  Synchronises s.
+cudaError_t compute_row_scale(const Problem& P, int row_normalize, float* D, cudaStream_t s);
+// Batched pass over the joint tile list (ntiles entries) with the given grid.
+cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, int64_t ntiles,
+                              const SlotDesc* slots, const float* gamma_of, double* slot_part,
+                              DeviceStatus* status, int grid, cudaStream_t s);
 cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const float* gamma_dev,
                             double gamma, double* eval_out, cudaStream_t s, bool identity = false);
 cudaError_t launch_renumber(const int32_t* dst_in, int32_t* dst_out, const int32_t* new_of,
@@ -170,6 +227,12 @@ cudaError_t launch_absmax(const float* v, int64_t n, unsigned* out, cudaStream_t
 void solve_ctx_free(Problem& P);
 
 // api.cu helpers
+// Tiles of whole sources: runs with at most max_edges edges and max_sources
+// sources; a source larger than max_edges forms a tile of its own.
+void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
+                 std::vector<int64_t>& tile_e, int64_t max_edges = kTileEdges,
+                 int64_t max_sources = kTileSources);
+cudaStream_t as_stream(void* s);
 void set_error(const std::string& msg);
 dualip_status fail(dualip_status st, const std::string& msg);
 dualip_status cuda_fail(cudaError_t e, const char* what);

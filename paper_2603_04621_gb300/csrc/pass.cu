@@ -147,9 +147,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -219,7 +216,7 @@ struct StageInfo {
   int64_t a0;      // first staged edge (multiple of 4)
   int64_t o0;      // first staged offset (even)
   int32_t big;     // single source larger than a stage: read from global
-  int32_t pad;
+  int32_t slot;    // batched pass: the slot whose problem the tile belongs to
 };
 
 template <bool BF16>
@@ -235,7 +232,8 @@ struct Layout {
   static constexpr size_t kMu = kStages * kStageBytes;
   static constexpr size_t kY = kMu + sizeof(float) * kMaxCachedDests;
   static constexpr size_t kBars = kY + sizeof(unsigned long long) * kMaxPrivDests;
-  static constexpr size_t kInfo = kBars + sizeof(uint64_t) * 2 * kStages;
+  // full[kStages], empty[kStages], and two consumer barriers (batched pass)
+  static constexpr size_t kInfo = kBars + sizeof(uint64_t) * (2 * kStages + 2);
   static constexpr size_t kMisc = kInfo + sizeof(StageInfo) * kStages;
   static constexpr size_t kTotal = kMisc + 512;
   static_assert(kOffBytes % 16 == 0 && kEdgeArr % 16 == 0 && kDstArr % 16 == 0,
@@ -309,6 +307,10 @@ struct Ctx {
   float gamma, inv_gamma;
   float sy;  // 2^ey: fixed-point scale of A x
   float* x_out;
+  // edge arrays in global memory (sources larger than a stage)
+  const int32_t* dst_g;
+  const float2* ca2_g;
+  const uint32_t* ca_g;
 
   __device__ __forceinline__ float mu_smem(int j) const { return lds_f32(mu_a + 4u * j); }
   __device__ __forceinline__ float mu(int j) const {
@@ -346,8 +348,7 @@ __device__ __forceinline__ float edge_alpha(const Ctx& cx, float w) {
 }
 
 // Per-lane objective partials sum c x and sum w x^2: FP32 running sums with
-// an exact TwoSum compensation each (FMA-pipe work only); the per-lane order
-// is fixed, so the partials are reproducible.
+// an exact TwoSum compensation each (FMA-pipe work only).
 struct Acc {
   float s = 0.f, e = 0.f;
   __device__ __forceinline__ void add(float v) {
@@ -459,7 +460,9 @@ __device__ __forceinline__ void load4(const StageView<BF16>& sv, int e, int (&j)
 // as (stage slot of the first edge, degree; 0 = no source).  Returns, per
 // group, whether the source is unsaturated or has near-ties at the top: those
 // take the general path.
-template <int G, int S, bool BF16, bool W, bool MU_SMEM>
+// SAFE: window slots outside the source may hold ids of another problem
+// (batched pass), so they read mu of id 0 instead.
+template <int G, int S, bool BF16, bool W, bool MU_SMEM, bool SAFE>
 __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base, int d,
                                              int lane, const Ctx& cx, Sums& acc) {
   constexpr int K = 4 * S;
@@ -479,7 +482,8 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
     for (int i = 0; i < 4; ++i) {
       const int k = 4 * st + i;
       const bool v = (unsigned)(e + i - base) < (unsigned)d;
-      const int j = jv[i];  // a valid id even outside the source (see Layout)
+      // a valid id even outside the source (see Layout), unless SAFE
+      const int j = SAFE ? (v ? jv[i] : 0) : jv[i];
       const float m = MU_SMEM ? cx.mu_smem(j) : cx.mu(j);
       const float r = v ? -__fmaf_rn(av[i], m, cv[i]) : -CUDART_INF_F;
       rf[k] = r;
@@ -562,7 +566,7 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
 // batch), 32/G at a time: group g takes the g-th remaining set bit.  bq / dq
 // are held by lane q: the stage slot of source q's first edge and its degree.
 // Returns the mask of sources that need the general path.
-template <int G, int S, bool BF16, bool W, bool MU_SMEM>
+template <int G, int S, bool BF16, bool W, bool MU_SMEM, bool SAFE>
 __device__ __forceinline__ unsigned lean_over(const StageView<BF16>& sv, unsigned mask, int bq,
                                               int dq, int lane, const Ctx& cx, Sums& acc) {
   unsigned needm = 0u;
@@ -579,7 +583,8 @@ __device__ __forceinline__ unsigned lean_over(const StageView<BF16>& sv, unsigne
     const int qs = q < 0 ? 0 : q;
     const int b = __shfl_sync(0xffffffffu, bq, qs);
     const int dd = __shfl_sync(0xffffffffu, dq, qs);
-    const bool nd = project_lean<G, S, BF16, W, MU_SMEM>(sv, b, q >= 0 ? dd : 0, lane, cx, acc);
+    const bool nd =
+        project_lean<G, S, BF16, W, MU_SMEM, SAFE>(sv, b, q >= 0 ? dd : 0, lane, cx, acc);
     needm |= __reduce_or_sync(0xffffffffu, ((lane % G) == 0 && nd && q >= 0) ? (1u << q) : 0u);
 #pragma unroll
     for (int r = 0; r < 32 / G; ++r) mask &= mask - 1u;
@@ -738,11 +743,28 @@ __device__ __forceinline__ void epi_write(const EpiParams& q, double cxs, double
   q.eval_out[4] = mug;
 }
 
+// A warp's objective partials of one problem, added to its slot's FP64 pair
+// (batched pass; a few atomics per warp and slot).
+__device__ __forceinline__ void flush_sums(const Sums& acc, double* dst, int lane) {
+  float ch = acc.cx.s, cl = acc.cx.e, wh = acc.wxx.s, wl = acc.wxx.e;
+  pair_add(wh, wl, (float)acc.units);
+  warp_pair_sum(ch, cl);
+  warp_pair_sum(wh, wl);
+  if (lane == 0) {
+    atomicAdd(dst, pair_value(ch, cl));
+    atomicAdd(dst + 1, pair_value(wh, wl));
+  }
+}
+
 // ----------------------------------------------------------- the pass ----
 // MU_SMEM: every destination's mu is cached in shared memory (J <= the cache).
 // WRITE_X: the primal x is written for every edge (dualip_get_primal); every
 // source then takes the general path.
-template <bool BF16, bool W, bool MU_SMEM, bool WRITE_X>
+// BATCH: the tiles come from a joint list over several problems (slots).  At
+// a tile of another slot the consumer warps meet at a shared barrier, flush
+// the previous slot's shared bins and objective partials, load the new slot's
+// mu cache, and meet again; the producer never waits for them there.
+template <bool BF16, bool W, bool MU_SMEM, bool WRITE_X, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p) {
   using L = Layout<BF16>;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -750,6 +772,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
   unsigned long long* y_s = reinterpret_cast<unsigned long long*>(smem + L::kY);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBars);
   uint64_t* empty = full + kStages;
+  uint64_t* cbar = empty + kStages;  // consumer-only barriers (slot switch)
   StageInfo* info = reinterpret_cast<StageInfo*>(smem + L::kInfo);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + L::kMisc);
   // [kMisc+16, kMisc+320): per-warp reduction slots (float4)
@@ -768,11 +791,17 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       mbar_init(&empty[s], kConsumerWarps);
       claim[s] = 0u;
     }
+    if (BATCH) {
+      mbar_init(&cbar[0], kConsumerWarps);
+      mbar_init(&cbar[1], kConsumerWarps);
+    }
     *abort = 0;
     fence_mbar_init();
   }
-  for (int j = tid; j < p.h_mu; j += blockDim.x) mu_s[j] = p.mu_r[j];
-  for (int j = tid; j < p.h_y; j += blockDim.x) y_s[j] = 0ull;
+  if (!BATCH) {
+    for (int j = tid; j < p.h_mu; j += blockDim.x) mu_s[j] = p.mu_r[j];
+    for (int j = tid; j < p.h_y; j += blockDim.x) y_s[j] = 0ull;
+  }
   for (int s = 0; s < kStages; ++s) {
     uint32_t* d = reinterpret_cast<uint32_t*>(smem + (size_t)s * L::kStageBytes + L::kOffBytes);
     for (int k = tid; k < (int)(L::kDstArr / 4); k += blockDim.x) d[k] = 0u;
@@ -782,55 +811,86 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
   Ctx cx;
   Sums acc;
   cx.mu_a = smem_u32(mu_s);
-  cx.mu_g = p.mu_r;
-  cx.h_mu = p.h_mu;
   cx.y_a = smem_u32(y_s);
-  cx.h_y = p.h_y;
-  cx.y = p.y;
-  cx.sy = ldexpf(1.f, p.ey);
-  cx.gamma = p.gamma_dev ? *p.gamma_dev : p.gamma;
-  cx.inv_gamma = __frcp_rn(cx.gamma);
   cx.x_out = WRITE_X ? p.x_out : nullptr;
+  if (!BATCH) {
+    cx.mu_g = p.mu_r;
+    cx.h_mu = p.h_mu;
+    cx.h_y = p.h_y;
+    cx.y = p.y;
+    cx.sy = ldexpf(1.f, p.ey);
+    cx.gamma = p.gamma_dev ? *p.gamma_dev : p.gamma;
+    cx.inv_gamma = __frcp_rn(cx.gamma);
+    cx.dst_g = p.dst;
+    cx.ca2_g = p.ca2;
+    cx.ca_g = p.ca;
+  } else {  // set at the first tile (slot switch)
+    cx.mu_g = nullptr;
+    cx.h_mu = 0;
+    cx.h_y = 0;
+    cx.y = nullptr;
+    cx.sy = 1.f;
+    cx.gamma = 1.f;
+    cx.inv_gamma = 1.f;
+    cx.dst_g = nullptr;
+    cx.ca2_g = nullptr;
+    cx.ca_g = nullptr;
+  }
+  int cur = -1;  // batched pass: the slot of the consumers' current tile
 
   if (warp == 0) {
     // ------------------------------------------------------ producer ----
     // The warp fetches 32 tile descriptors per load; lane 0 waits and issues.
     int64_t it = 0;
     bool stop = false;
-    // L2 prefetch frontier: edges up to kL2PrefetchTiles tiles ahead of the
-    // tile being staged are requested into L2 (no shared memory involved),
-    // which keeps more of HBM's latency covered than the ring alone
-    const int64_t e_end = (p.tile_e[t_end] + 3) & ~int64_t(3);
-    int64_t pf = p.tile_e[t_begin] & ~int64_t(3);
-    auto prefetch_to = [&](int64_t target) {
-      target = target < e_end ? ((target + 3) & ~int64_t(3)) : e_end;
-      while (pf < target) {
-        const int64_t n = target - pf < (int64_t)kTileEdges ? target - pf : (int64_t)kTileEdges;
-        bulk_prefetch_l2(p.dst + pf, (uint32_t)n * 4u);
-        if (BF16) {
-          bulk_prefetch_l2(p.ca + pf, (uint32_t)n * 4u);
-        } else {
-          bulk_prefetch_l2(p.ca2 + pf, (uint32_t)n * 8u);
-        }
-        pf += n;
-      }
-    };
-    if (kL2PrefetchTiles > 0 && lane == 0 && t_begin < t_end)
-      prefetch_to(p.tile_e[t_begin] + (int64_t)kL2PrefetchTiles * kTileEdges);
+    int pslot = -1;  // batched pass: slot of the edge pointers below
+    const int64_t* offp = p.off;
+    const int32_t* dstp = p.dst;
+    const float2* ca2p = p.ca2;
+    const uint32_t* cap = p.ca;
     for (int64_t t0 = t_begin; t0 < t_end && !stop; t0 += 32) {
-      const int64_t tl = t0 + lane < t_end ? t0 + lane : t_end;
-      const int64_t my_s = p.tiles[tl], my_e = p.tile_e[tl];
-      const int64_t ext = t0 + 32 < t_end ? t0 + 32 : t_end;
-      const int64_t ext_s = p.tiles[ext], ext_e = p.tile_e[ext];
+      int64_t my_s, my_e, my_s1 = 0, my_e1 = 0, ext_s = 0, ext_e = 0;
+      int my_slot = 0;
+      if (BATCH) {
+        const JointTile jt = p.jt[t0 + lane < t_end ? t0 + lane : t_end - 1];
+        my_s = jt.s0;
+        my_e = jt.e0;
+        my_s1 = jt.s1;
+        my_e1 = jt.e1;
+        my_slot = jt.slot;
+      } else {
+        const int64_t tl = t0 + lane < t_end ? t0 + lane : t_end;
+        my_s = p.tiles[tl];
+        my_e = p.tile_e[tl];
+        const int64_t ext = t0 + 32 < t_end ? t0 + 32 : t_end;
+        ext_s = p.tiles[ext];
+        ext_e = p.tile_e[ext];
+      }
       const int cnt = (int)(t_end - t0 < 32 ? t_end - t0 : 32);
       for (int k = 0; k < cnt; ++k, ++it) {
         const int64_t s0 = __shfl_sync(0xffffffffu, my_s, k);
         const int64_t e0 = __shfl_sync(0xffffffffu, my_e, k);
-        const int64_t s1n = __shfl_sync(0xffffffffu, my_s, (k + 1) & 31);
-        const int64_t e1n = __shfl_sync(0xffffffffu, my_e, (k + 1) & 31);
-        const int64_t s1 = k < 31 ? s1n : ext_s;
-        const int64_t e1 = k < 31 ? e1n : ext_e;
+        int64_t s1, e1;
+        int slot = 0;
+        if (BATCH) {
+          s1 = __shfl_sync(0xffffffffu, my_s1, k);
+          e1 = __shfl_sync(0xffffffffu, my_e1, k);
+          slot = __shfl_sync(0xffffffffu, my_slot, k);
+        } else {
+          const int64_t s1n = __shfl_sync(0xffffffffu, my_s, (k + 1) & 31);
+          const int64_t e1n = __shfl_sync(0xffffffffu, my_e, (k + 1) & 31);
+          s1 = k < 31 ? s1n : ext_s;
+          e1 = k < 31 ? e1n : ext_e;
+        }
         if (lane == 0) {
+          if (BATCH && slot != pslot) {
+            const SlotDesc* d = p.slots + slot;
+            offp = d->off;
+            dstp = d->dst;
+            ca2p = d->ca2;
+            cap = d->ca;
+            pslot = slot;
+          }
           const int s = (int)(it % kStages);
           const uint32_t round = (uint32_t)(it / kStages);
           if (round > 0 && !wait_phase(&empty[s], (round - 1) & 1u, abort, p.status, 1)) {
@@ -849,6 +909,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
               si.s1 = s0;  // skip the tile; results are flagged invalid
             }
             si.big = (!bad && e1 - e0 > kTileEdges) ? 1 : 0;
+            si.slot = slot;
             si.a0 = e0 & ~int64_t(3);
             si.o0 = s0 & ~int64_t(1);
             info[s] = si;
@@ -861,14 +922,13 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
               const uint32_t bytes = no * 8u + ne * (BF16 ? 8u : 12u);
               mbar_arrive_expect_tx(&full[s], bytes);
               unsigned char* base = smem + (size_t)s * L::kStageBytes;
-              if (kL2PrefetchTiles > 0) prefetch_to(e0 + (int64_t)(kL2PrefetchTiles + 1) * kTileEdges);
-              bulk_g2s(base, p.off + si.o0, no * 8u, &full[s]);
+              bulk_g2s(base, offp + si.o0, no * 8u, &full[s]);
               if (ne) {
-                bulk_g2s(base + L::kOffBytes, p.dst + si.a0, ne * 4u, &full[s]);
+                bulk_g2s(base + L::kOffBytes, dstp + si.a0, ne * 4u, &full[s]);
                 if (BF16) {
-                  bulk_g2s(base + L::kOffBytes + L::kDstArr, p.ca + si.a0, ne * 4u, &full[s]);
+                  bulk_g2s(base + L::kOffBytes + L::kDstArr, cap + si.a0, ne * 4u, &full[s]);
                 } else {
-                  bulk_g2s(base + L::kOffBytes + L::kDstArr, p.ca2 + si.a0, ne * 8u, &full[s]);
+                  bulk_g2s(base + L::kOffBytes + L::kDstArr, ca2p + si.a0, ne * 8u, &full[s]);
                 }
               }
             }
@@ -904,12 +964,51 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     // past the tile's batches; the producer resets the counter only after
     // every warp has left, so no claim can reach a refilled stage.
     int64_t it = 0;
+    uint32_t nsw = 0;  // slot switches so far (phase of the consumer barriers)
     for (int64_t t = t_begin; t < t_end; ++t, ++it) {
       const int s = (int)(it % kStages);
       const uint32_t round = (uint32_t)(it / kStages);
       const bool ok = wait_phase(&full[s], round & 1u, abort, p.status, 2);
       if (!__all_sync(0xffffffffu, ok)) break;
       const StageInfo si = info[s];
+      if (BATCH && si.slot != cur) {
+        // Every consumer warp visits every tile, so all of them switch here.
+        // Meet once the previous slot's tiles are done, move the shared
+        // bins and the mu cache to the new slot, meet again.
+        if (cur >= 0) flush_sums(acc, p.slot_part + 2 * cur, lane);
+        acc = Sums{};
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&cbar[0]);
+        if (!__all_sync(0xffffffffu, wait_phase(&cbar[0], nsw & 1u, abort, p.status, 4))) break;
+        const SlotDesc* d = p.slots + si.slot;
+        const int h_mu = d->h_mu, h_y = d->h_y;
+        const float* mu_r = d->mu_r;
+        const int hy_old = cur >= 0 ? cx.h_y : 0;
+        const int hmax = hy_old > h_y ? hy_old : h_y;
+        for (int j = tid - 32; j < hmax; j += kConsumerWarps * 32) {
+          if (j < hy_old) {
+            const unsigned long long v = y_s[j];
+            if (v != 0ull) atomicAdd(cx.y + j, v);
+          }
+          y_s[j] = 0ull;
+        }
+        for (int j = tid - 32; j < h_mu; j += kConsumerWarps * 32) mu_s[j] = mu_r[j];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&cbar[1]);
+        if (!__all_sync(0xffffffffu, wait_phase(&cbar[1], nsw & 1u, abort, p.status, 5))) break;
+        ++nsw;
+        cur = si.slot;
+        cx.mu_g = mu_r;
+        cx.h_mu = h_mu;
+        cx.h_y = h_y;
+        cx.y = d->y;
+        cx.sy = d->sy;
+        cx.gamma = p.gamma_of[cur];
+        cx.inv_gamma = __frcp_rn(cx.gamma);
+        cx.dst_g = d->dst;
+        cx.ca2_g = d->ca2;
+        cx.ca_g = d->ca;
+      }
       const uint32_t claim_a = smem_u32(claim + s);
       if (si.big) {
         // the warp that claims it projects a source larger than a stage
@@ -918,7 +1017,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         if (lane == 0) b = atoms_add_u32(claim_a, 1u);
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b == 0u) {
-          GlobalView<BF16> gv{p.dst, p.ca2, p.ca};
+          GlobalView<BF16> gv{cx.dst_g, cx.ca2_g, cx.ca_g};
           project_multipass<BF16, W>(gv, si.e0, si.e1 - si.e0, si.e0, lane, cx, acc);
         }
       } else {
@@ -953,10 +1052,10 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
             const unsigned m256 = __ballot_sync(0xffffffffu, spq > 128 && spq <= 256);
             const unsigned m512 = __ballot_sync(0xffffffffu, spq > 256 && spq <= 512);
             needm = __ballot_sync(0xffffffffu, spq > 512);
-            if (m64) needm |= lean_over<4, 4, BF16, W, MU_SMEM>(sv, m64, bq, dq, lane, cx, acc);
-            if (m128) needm |= lean_over<8, 4, BF16, W, MU_SMEM>(sv, m128, bq, dq, lane, cx, acc);
-            if (m256) needm |= lean_over<16, 4, BF16, W, MU_SMEM>(sv, m256, bq, dq, lane, cx, acc);
-            if (m512) needm |= lean_over<32, 4, BF16, W, MU_SMEM>(sv, m512, bq, dq, lane, cx, acc);
+            if (m64) needm |= lean_over<4, 4, BF16, W, MU_SMEM, BATCH>(sv, m64, bq, dq, lane, cx, acc);
+            if (m128) needm |= lean_over<8, 4, BF16, W, MU_SMEM, BATCH>(sv, m128, bq, dq, lane, cx, acc);
+            if (m256) needm |= lean_over<16, 4, BF16, W, MU_SMEM, BATCH>(sv, m256, bq, dq, lane, cx, acc);
+            if (m512) needm |= lean_over<32, 4, BF16, W, MU_SMEM, BATCH>(sv, m512, bq, dq, lane, cx, acc);
           }
           while (needm) {
             const int q = __ffs(needm) - 1;
@@ -970,31 +1069,42 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
+    if (BATCH && cur >= 0) flush_sums(acc, p.slot_part + 2 * cur, lane);
   }
   __syncthreads();
 
-  // flush the shared-memory accumulators of the hot destinations
-  for (int j = tid; j < p.h_y; j += blockDim.x) {
-    const unsigned long long v = y_s[j];
-    if (v != 0ull) atomicAdd(p.y + j, v);
-  }
-  // per-CTA objective partials: FP32 pairs through the shuffle and warp
-  // trees; the units are exact small integers
-  float ch = acc.cx.s, cl = acc.cx.e, wh = acc.wxx.s, wl = acc.wxx.e;
-  pair_add(wh, wl, (float)acc.units);
-  warp_pair_sum(ch, cl);
-  warp_pair_sum(wh, wl);
-  float4* wred = reinterpret_cast<float4*>(dred);  // one per warp
-  if (lane == 0) wred[warp] = make_float4(ch, cl, wh, wl);
-  __syncthreads();
-  if (tid == 0) {
-    float4 t = wred[0];
-    for (int w = 1; w < kThreads / 32; ++w) {
-      const float4 u = wred[w];
-      pair_addp(t.x, t.y, u.x, u.y);
-      pair_addp(t.z, t.w, u.z, u.w);
+  if (BATCH) {
+    // the last slot's shared bins (consumer threads hold its pointers)
+    if (warp > 0 && cur >= 0) {
+      for (int j = tid - 32; j < cx.h_y; j += kConsumerWarps * 32) {
+        const unsigned long long v = y_s[j];
+        if (v != 0ull) atomicAdd(cx.y + j, v);
+      }
     }
-    p.part[blockIdx.x] = t;
+  } else {
+    // flush the shared-memory accumulators of the hot destinations
+    for (int j = tid; j < p.h_y; j += blockDim.x) {
+      const unsigned long long v = y_s[j];
+      if (v != 0ull) atomicAdd(p.y + j, v);
+    }
+    // per-CTA objective partials: FP32 pairs through the shuffle and warp
+    // trees; the units are exact small integers
+    float ch = acc.cx.s, cl = acc.cx.e, wh = acc.wxx.s, wl = acc.wxx.e;
+    pair_add(wh, wl, (float)acc.units);
+    warp_pair_sum(ch, cl);
+    warp_pair_sum(wh, wl);
+    float4* wred = reinterpret_cast<float4*>(dred);  // one per warp
+    if (lane == 0) wred[warp] = make_float4(ch, cl, wh, wl);
+    __syncthreads();
+    if (tid == 0) {
+      float4 t = wred[0];
+      for (int w = 1; w < kThreads / 32; ++w) {
+        const float4 u = wred[w];
+        pair_addp(t.x, t.y, u.x, u.y);
+        pair_addp(t.z, t.w, u.z, u.w);
+      }
+      p.part[blockIdx.x] = t;
+    }
   }
 }
 
@@ -1142,9 +1252,9 @@ size_t pass_smem_bytes(int storage) {
   return storage == DUALIP_EDGE_BF16 ? Layout<true>::kTotal : Layout<false>::kTotal;
 }
 
-template <bool BF16, bool W, bool MU, bool WX>
+template <bool BF16, bool W, bool MU, bool WX, bool B = false>
 static cudaError_t set_smem() {
-  return cudaFuncSetAttribute(dualgrad_pass_kernel<BF16, W, MU, WX>,
+  return cudaFuncSetAttribute(dualgrad_pass_kernel<BF16, W, MU, WX, B>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Layout<BF16>::kTotal);
 }
@@ -1156,7 +1266,9 @@ cudaError_t configure_pass_kernels() {
       set_smem<true, false, false, false>(),  set_smem<true, false, true, false>(),
       set_smem<true, true, false, false>(),   set_smem<true, true, true, false>(),
       set_smem<false, false, false, true>(),  set_smem<false, true, false, true>(),
-      set_smem<true, false, false, true>(),   set_smem<true, true, false, true>()};
+      set_smem<true, false, false, true>(),   set_smem<true, true, false, true>(),
+      set_smem<false, false, false, false, true>(), set_smem<false, true, false, false, true>(),
+      set_smem<true, false, false, false, true>(),  set_smem<true, true, false, false, true>()};
   for (cudaError_t e : es)
     if (e != cudaSuccess) return e;
   return cudaSuccess;
@@ -1190,6 +1302,10 @@ static PassParams pass_params(const Problem& P, const float* gamma_dev, float ga
   p.part = P.part;
   p.x_out = x_out;
   p.status = P.status;
+  p.jt = nullptr;
+  p.slots = nullptr;
+  p.gamma_of = nullptr;
+  p.slot_part = nullptr;
   return p;
 }
 
@@ -1207,7 +1323,7 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
   const bool mu_all = P.J <= P.h_mu;
   const size_t smem = pass_smem_bytes(P.storage);
   const dim3 grid(P.grid), block(kThreads);
-#define DUALIP_LAUNCH(B, W, M, X) dualgrad_pass_kernel<B, W, M, X><<<grid, block, smem, s>>>(p)
+#define DUALIP_LAUNCH(B, W, M, X) dualgrad_pass_kernel<B, W, M, X, false><<<grid, block, smem, s>>>(p)
   if (x_out) {
     if (bf16) {
       if (P.weighted) DUALIP_LAUNCH(true, true, false, true);
@@ -1234,6 +1350,30 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
     }
   }
 #undef DUALIP_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, int64_t ntiles,
+                              const SlotDesc* slots, const float* gamma_of, double* slot_part,
+                              DeviceStatus* status, int grid, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  PassParams p{};
+  p.ntiles = ntiles;
+  p.jt = jt;
+  p.slots = slots;
+  p.gamma_of = gamma_of;
+  p.slot_part = slot_part;
+  p.status = status;
+  const bool bf16 = storage == DUALIP_EDGE_BF16;
+  const size_t smem = pass_smem_bytes(storage);
+  const int g = (int)(ntiles < grid ? ntiles : grid);
+  if (bf16) {
+    if (weighted) dualgrad_pass_kernel<true, true, false, false, true><<<g, kThreads, smem, s>>>(p);
+    else dualgrad_pass_kernel<true, false, false, false, true><<<g, kThreads, smem, s>>>(p);
+  } else {
+    if (weighted) dualgrad_pass_kernel<false, true, false, false, true><<<g, kThreads, smem, s>>>(p);
+    else dualgrad_pass_kernel<false, false, false, false, true><<<g, kThreads, smem, s>>>(p);
+  }
   return cudaGetLastError();
 }
 

@@ -270,29 +270,34 @@ static cudaError_t solve_ctx_get(Problem& P, SolveCtx** out) {
   return cudaSuccess;
 }
 
-static cudaError_t ensure_row_scale(Problem& P, SolveCtx& C, int row_normalize, cudaStream_t s) {
-  if (C.row_normalize == row_normalize) return cudaSuccess;
+cudaError_t compute_row_scale(const Problem& P, int row_normalize, float* D, cudaStream_t s) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((P.J + 255) / 256, 2 * P.num_sms));
   cudaError_t e;
   if (!row_normalize) {
-    fill_kernel<<<C.blocks, 256, 0, s>>>(P.J, C.D, 1.0f);
-    if ((e = cudaGetLastError())) return e;
-  } else {
-    double* acc = nullptr;
-    if ((e = cudaMalloc(&acc, sizeof(double) * P.J))) return e;
-    e = cudaMemsetAsync(acc, 0, sizeof(double) * P.J, s);
-    if (!e && P.E > 0) {
-      const int64_t g = std::min<int64_t>((P.E + 255) / 256, 8192);
-      row_norm_kernel<<<(int)g, 256, 0, s>>>(P.dst, P.ca2, P.ca, P.E, P.weighted, acc);
-      e = cudaGetLastError();
-    }
-    if (!e) {
-      row_scale_kernel<<<C.blocks, 256, 0, s>>>(P.J, acc, C.D);
-      e = cudaGetLastError();
-    }
-    cudaStreamSynchronize(s);
-    cudaFree(acc);
-    if (e) return e;
+    fill_kernel<<<blocks, 256, 0, s>>>(P.J, D, 1.0f);
+    return cudaGetLastError();
   }
+  double* acc = nullptr;
+  if ((e = cudaMalloc(&acc, sizeof(double) * std::max<int32_t>(P.J, 1)))) return e;
+  e = cudaMemsetAsync(acc, 0, sizeof(double) * P.J, s);
+  if (!e && P.E > 0) {
+    const int64_t g = std::min<int64_t>((P.E + 255) / 256, 8192);
+    row_norm_kernel<<<(int)g, 256, 0, s>>>(P.dst, P.ca2, P.ca, P.E, P.weighted, acc);
+    e = cudaGetLastError();
+  }
+  if (!e) {
+    row_scale_kernel<<<blocks, 256, 0, s>>>(P.J, acc, D);
+    e = cudaGetLastError();
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(acc);
+  return e;
+}
+
+static cudaError_t ensure_row_scale(Problem& P, SolveCtx& C, int row_normalize, cudaStream_t s) {
+  if (C.row_normalize == row_normalize) return cudaSuccess;
+  cudaError_t e = compute_row_scale(P, row_normalize, C.D, s);
+  if (e) return e;
   C.row_normalize = row_normalize;
   return cudaSuccess;
 }
