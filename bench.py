@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: 1M x 10k, ~50M edges (default); c3: 25M x 1M, ~2.0B edges")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+                    help="c2: 1M x 10k, ~50M edges (default); c3: 25M x 1M, ~2.0B edges; "
+                         "c4: 256 problems in one batched pass, ~3.4B edges")
     ap.add_argument("--storage", default=None, choices=["f32", "bf16"],
                     help="edge storage (default f32 for c2, bf16 for c3)")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the sources")
@@ -76,6 +77,9 @@ WORKLOADS = {
            "Zipf(1.1) destinations, c=-LogNormal(0,1), a~U(0.5,1.5), b=0.2*sum(a), int32 dst"),
     "c3": ("c3: matching LP, 25M sources x 1M destinations, Poisson(80) degrees in [1,2000], "
            "Zipf(1.1) destinations, c=-LogNormal(0,1), a~U(0.5,1.5), b=0.2*sum(a), int64 offsets"),
+    "c4": ("c4: 256 independent matching LPs in one batched pass, sources LogUniform[1k,2M], "
+           "destinations LogUniform[10,50k], degrees Uniform[5,100] (<= J), Zipf(1.1) "
+           "destinations, c=-LogNormal(0,1), a~U(0.5,1.5), greedy-load budgets (App. B rule)"),
 }
 
 
@@ -265,7 +269,142 @@ def time_to_gap(d, torch, base, name, storage):
             "dual_obj": res["dual_obj"]}
 
 
+def batch_time_to_gap(d, torch, probs, B):
+    """Batched ascent of every problem to the 1e-4 gap, against the lone
+    dualip_solve of each problem one after the other (same options)."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, res = B.solve()
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lone = [P.solve()[1] for P in probs]
+    torch.cuda.synchronize()
+    tl = time.perf_counter() - t0
+    return {"workload": "c4 problems, greedy-load budgets", "batched_seconds": tb,
+            "batched_converged": sum(r["converged"] for r in res),
+            "batched_max_iters": max(r["iters"] for r in res),
+            "lone_sequential_seconds": tl,
+            "lone_converged": sum(r["converged"] for r in lone), "n": len(probs),
+            "speedup_batched_vs_lone": tl / tb}
+
+
+def run_batch(args):
+    """c4: every problem of the batch in one batched pass per step."""
+    import torch
+    import synth
+
+    torch.cuda.set_device(0)
+    from paper_2603_04621_gb300 import build
+
+    build.build()
+    import paper_2603_04621_gb300 as d
+
+    shapes = synth.batch_shapes(256)
+    if args.scale != 1.0:
+        shapes = [(max(1, int(I * args.scale)), J, sd) for I, J, sd in shapes]
+    probs, sample = [], None
+    I_t = J_t = E_t = 0
+    for I, J, sd in shapes:
+        inst = synth.greedy_budgets(synth.batch_instance(I, J, sd))
+        probs.append(d.Problem.from_instance(inst, storage=args.storage))
+        I_t, J_t, E_t = I_t + inst.I, J_t + inst.J, E_t + inst.E
+        if sample is None and inst.I >= 100_000:
+            sample = inst
+        del inst
+    B = d.Batch(probs)
+    tune = B.autotune()
+    lam_h = np.random.default_rng(LAM_SEED).uniform(0.0, 1.0, J_t).astype(np.float32)
+    lam = torch.from_numpy(lam_h).cuda()
+    grad = torch.empty_like(lam)
+    out_dev = torch.empty(5 * len(probs), dtype=torch.float64, device="cuda")
+    gam = [GAMMA] * len(probs)
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+
+    def step():
+        d.dualip_batch_dual_grad_async(B.h, lam.data_ptr(), gam, grad.data_ptr(),
+                                       out_dev.data_ptr(), sp)
+
+    with ClockSampler(0) as clk:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        t_end = time.perf_counter() + 1.0
+        while time.perf_counter() < t_end:
+            for _ in range(5):
+                step()
+            torch.cuda.synchronize()
+        d.dualip_batch_profile_enable(B.h, args.steps)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = d.dualip_batch_profile_collect(B.h)
+        # end to end with host buffers: lambda in, gradient out, scalars to host
+        lam_pin = torch.from_numpy(lam_h).pin_memory()
+        grad_pin = torch.empty(J_t, dtype=torch.float32).pin_memory()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            lam.copy_(lam_pin, non_blocking=True)
+            B.dual_grad(lam, gam)
+            grad_pin.copy_(grad, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+    ttg = None if args.no_solve else batch_time_to_gap(d, torch, probs, B)
+    alg = 12 * E_t + 8 * (I_t + len(probs)) + 12 * J_t
+    if args.storage == "bf16":
+        alg -= 4 * E_t
+    pass_ms = prof["ms_pass"] / max(prof["count"], 1)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs") or 6800.0
+    achieved = alg / (pass_ms / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": E_t * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["c4"] if args.scale == 1.0 else
+                   f"c4 at {args.scale:g} of the sources", "storage": args.storage,
+                   "problems": len(probs), "I": I_t, "J": J_t, "E": E_t, "gamma": GAMMA,
+                   "lambda": f"U(0,1) seed {LAM_SEED}",
+                   "l2": "inputs larger than L2; no flush", "parallelism": "replicas",
+                   "tile_shape": [tune["tile_edges"][tune["chosen"]],
+                                  tune["tile_sources"][tune["chosen"]]]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "dualgrad_pass_kernel (batched)", "kernel_ms": pass_ms,
+                     "algorithmic_bytes": alg,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
+        "kernel_ms": {"prologue": prof["ms_prologue"] / max(prof["count"], 1), "pass": pass_ms,
+                      "epilogue": prof["ms_epilogue"] / max(prof["count"], 1)},
+        "autotune": {"tile_edges": tune["tile_edges"], "tile_sources": tune["tile_sources"],
+                     "ms": tune["ms"], "chosen": tune["chosen"]},
+        "e2e": {"value": E_t * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * J_t,
+                "d2h_bytes_per_step": 4 * J_t + 40 * len(probs),
+                "api": "dualip_batch_dual_grad (lambda and grad through pinned host buffers)"},
+        "clocks": clk.summary(),
+        "gpu_launches": 3 * args.steps,
+        "time_to_gap": ttg,
+    }
+    if not args.no_cpu_baseline and sample is not None:
+        out["cpu_baseline"] = cpu_baseline(sample, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    B.close()
+    return 0
+
+
 def run_ours(args):
+    if args.workload == "c4":
+        return run_batch(args)
     import torch
 
     ws, rank, local = dist_env()

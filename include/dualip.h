@@ -293,6 +293,11 @@ typedef struct {
   int64_t degree_hist[32];     /* sources with degree in [2^k, 2^(k+1)) (k = 0: 0 or 1) */
 } dualip_autotune_result;
 dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* result, void* stream);
+/* Kernel timing of the next max_evals batched evaluations, as for a problem
+ * (dualip_profile_enable / _collect): prologue, pass and epilogue, in ms. */
+dualip_status dualip_batch_profile_enable(dualip_batch* b, int32_t max_evals);
+dualip_status dualip_batch_profile_collect(dualip_batch* b, double* ms_prologue, double* ms_pass,
+                                           double* ms_epilogue, int32_t* count);
 /* Explicit tile shape: 1 <= edges <= 3072, 1 <= sources <= 256. */
 dualip_status dualip_batch_set_tile_shape(dualip_batch* b, int32_t edges, int32_t sources);
 dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* total_J,

@@ -31,7 +31,8 @@ EXPORTS = [
     "dualip_profile_enable", "dualip_profile_collect", "dualip_dual_grad_noalloc",
     "dualip_batch_create", "dualip_batch_destroy", "dualip_batch_dual_grad",
     "dualip_batch_dual_grad_async", "dualip_batch_solve", "dualip_batch_autotune",
-    "dualip_batch_set_tile_shape", "dualip_batch_get_info",
+    "dualip_batch_set_tile_shape", "dualip_batch_get_info", "dualip_batch_profile_enable",
+    "dualip_batch_profile_collect",
 ]
 
 
@@ -146,6 +147,10 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(i64), ctypes.POINTER(i64),
                                             ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.dualip_batch_get_info.restype = st
+        L.dualip_batch_profile_enable.argtypes = [vp, i32]
+        L.dualip_batch_profile_enable.restype = st
+        L.dualip_batch_profile_collect.argtypes = [vp, pd, pd, pd, ctypes.POINTER(i32)]
+        L.dualip_batch_profile_collect.restype = st
         L.dualip_last_error.argtypes = []
         L.dualip_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -310,6 +315,18 @@ def dualip_batch_get_info(b: int) -> dict:
                                        ctypes.byref(T), ctypes.byref(te), ctypes.byref(ts)))
     return dict(n=n.value, J=J.value, E=E.value, ntiles=T.value, tile_edges=te.value,
                 tile_sources=ts.value)
+
+
+def dualip_batch_profile_enable(b: int, max_evals: int) -> None:
+    _check(lib().dualip_batch_profile_enable(b, max_evals))
+
+
+def dualip_batch_profile_collect(b: int) -> dict:
+    t = [ctypes.c_double() for _ in range(3)]
+    n = ctypes.c_int32()
+    _check(lib().dualip_batch_profile_collect(b, *[ctypes.byref(x) for x in t], ctypes.byref(n)))
+    return dict(ms_prologue=t[0].value, ms_pass=t[1].value, ms_epilogue=t[2].value,
+                count=n.value)
 
 
 # ------------------------------------------------- convenience (marshalling) ----

@@ -349,7 +349,17 @@ struct Batch {
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
   int grid = 0;
+  // kernel timing of API evaluations (4 events each)
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_used = 0, prof_max = 0;
 };
+
+void free_prof(Batch& B) {
+  for (cudaEvent_t ev : B.prof_ev)
+    if (ev) cudaEventDestroy(ev);
+  B.prof_ev.clear();
+  B.prof_used = B.prof_max = 0;
+}
 
 template <class T>
 cudaError_t grow(T** p, size_t& cap, size_t need) {
@@ -378,6 +388,7 @@ void batch_free(Batch& B) {
   if (B.ev) cudaEventDestroy(B.ev);
   if (B.ev_stage) cudaEventDestroy(B.ev_stage);
   if (B.ev_use) cudaEventDestroy(B.ev_use);
+  free_prof(B);
   if (B.stream) cudaStreamDestroy(B.stream);
 }
 
@@ -458,16 +469,23 @@ cudaError_t enqueue_batch_eval(Batch& B, const float* lam, float* grad, int solv
                                cudaStream_t s) {
   if (B.nchunks == 0) return cudaSuccess;
   cudaError_t e;
+  cudaEvent_t* ev = nullptr;
+  if (!solver && B.prof_used < B.prof_max) ev = &B.prof_ev[4 * (size_t)B.prof_used++];
+  if (ev && (e = cudaEventRecord(ev[0], s))) return e;
   bprep_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.d_slots, lam, solver, B.d_ss, B.d_gamma_f,
                                          B.d_gamma_d);
   if ((e = cudaGetLastError())) return e;
+  if (ev && (e = cudaEventRecord(ev[1], s))) return e;
   if ((e = launch_pass_batch(B.storage, B.weighted, B.d_jt, B.ntiles, B.d_slots, B.d_gamma_f,
                              B.d_slot_part, B.d_status, B.grid, s)))
     return e;
+  if (ev && (e = cudaEventRecord(ev[2], s))) return e;
   bepi_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.nchunks, B.d_slots, grad, solver, B.d_cpart,
                                         B.d_act, (int)B.act_host.size(), B.d_crange,
                                         B.d_slot_part, B.d_gamma_d, B.d_eval, B.d_tickets);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError())) return e;
+  if (ev && (e = cudaEventRecord(ev[3], s))) return e;
+  return cudaSuccess;
 }
 
 cudaError_t enqueue_batch_iteration(Batch& B, cudaStream_t s) {
@@ -963,6 +981,49 @@ dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* res
   if ((st = dualip_batch_set_tile_shape(b, cand[best_c][0], cand[best_c][1]))) return st;
   if ((st = batch_status(B))) return st;
   if (result) *result = r;
+  return DUALIP_OK;
+}
+
+dualip_status dualip_batch_profile_enable(dualip_batch* b, int32_t max_evals) {
+  if (!b || max_evals < 1) return fail(DUALIP_EINVAL, "need a batch and max_evals >= 1");
+  Batch& B = b->b;
+  free_prof(B);
+  B.prof_ev.resize(4 * (size_t)max_evals, nullptr);
+  for (auto& ev : B.prof_ev) {
+    const cudaError_t e = cudaEventCreate(&ev);
+    if (e) {
+      ev = nullptr;
+      free_prof(B);
+      return cuda_fail(e, "creating timing events");
+    }
+  }
+  B.prof_max = max_evals;
+  return DUALIP_OK;
+}
+
+dualip_status dualip_batch_profile_collect(dualip_batch* b, double* ms_prologue, double* ms_pass,
+                                           double* ms_epilogue, int32_t* count) {
+  if (!b) return fail(DUALIP_EINVAL, "batch is NULL");
+  Batch& B = b->b;
+  double t[3] = {0, 0, 0};
+  for (int i = 0; i < B.prof_used; ++i) {
+    cudaEvent_t* ev = &B.prof_ev[4 * (size_t)i];
+    cudaError_t e = cudaEventSynchronize(ev[3]);
+    for (int k = 0; k < 3 && !e; ++k) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      t[k] += ms;
+    }
+    if (e) {
+      free_prof(B);
+      return cuda_fail(e, "reading timing events");
+    }
+  }
+  if (ms_prologue) *ms_prologue = t[0];
+  if (ms_pass) *ms_pass = t[1];
+  if (ms_epilogue) *ms_epilogue = t[2];
+  if (count) *count = B.prof_used;
+  free_prof(B);
   return DUALIP_OK;
 }
 
