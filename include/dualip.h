@@ -304,6 +304,74 @@ dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* 
                                     int64_t* total_E, int64_t* ntiles, int32_t* tile_edges,
                                     int32_t* tile_sources);
 
+/* ------------------------------------------------------------ serving ----
+ * A request loop (continuous batching) over the batched ascent.  Requests
+ * (matching LPs with their solve options) are queued; one is admitted, in
+ * arrival order, when a slot is free and its estimated device footprint fits
+ * the HBM budget next to the problems already resident.  An admitted request
+ * is built on the device (dualip_create, on its own stream, while the others
+ * keep iterating) and joins the running ascent at the next chunk boundary
+ * (every check_every iterations); its lambda, optimiser state and edges stay
+ * on the device until it meets its tolerances or max_iters, then its lambda
+ * goes to host memory and its memory is freed.  Requests with FP32 and BF16
+ * storage (and with or without primal scaling) run in separate batches, one
+ * after the other in every chunk.  A request's result is the one it gets
+ * alone: its gradients are exact whatever shares the launch, and its step,
+ * momentum and stopping test use its own quantities only.
+ *
+ * Footprint estimate (bytes): E (4 + bytes(c, a)) + 8 (I + 4) + 16 tiles
+ * + 56 J, plus 12 E while host inputs are staged at creation.
+ */
+typedef struct dualip_server dualip_server;
+
+typedef struct {
+  int64_t hbm_budget_bytes;  /* > 0 */
+  int32_t max_slots;         /* resident requests per storage kind, 1..1024 */
+  int32_t check_every;       /* iterations per chunk (joins, exits, stopping tests), >= 1 */
+} dualip_server_opts;
+
+typedef enum {
+  DUALIP_REQ_QUEUED = 0,
+  DUALIP_REQ_RUNNING = 1,  /* admitted: being built or iterating */
+  DUALIP_REQ_DONE = 2,
+  DUALIP_REQ_FAILED = 3
+} dualip_request_state;
+
+typedef struct {
+  int32_t state;              /* dualip_request_state */
+  int32_t status;             /* dualip_status of a failed request */
+  dualip_solve_result result; /* valid when DONE */
+  double t_submit, t_admit, t_done;  /* seconds since the server started (-1: not yet) */
+  int64_t footprint_bytes;
+  int32_t num_dests;
+  int32_t pad;
+} dualip_request_info;
+
+typedef struct {
+  int64_t submitted, queued, running, done, failed;
+  int64_t resident_bytes, peak_resident_bytes;
+  int64_t chunks;             /* chunk launches (each: check_every iterations of a batch) */
+  int64_t slot_iterations;    /* iterations summed over requests */
+  double busy_seconds;        /* time spent running chunks */
+} dualip_server_stats;
+
+dualip_status dualip_server_create(const dualip_server_opts* opts, dualip_server** out);
+/* Queues a request.  The arrays of desc (host or device) must stay valid
+ * until the request has left the QUEUED state; opts NULL = defaults. */
+dualip_status dualip_server_submit(dualip_server* s, const dualip_problem_desc* desc,
+                                   const dualip_solve_opts* opts, int64_t* ticket);
+/* State of a request; lambda_out (host [J], may be NULL) receives its dual
+ * point once DONE. */
+dualip_status dualip_server_poll(dualip_server* s, int64_t ticket, dualip_request_info* info,
+                                 float* lambda_out);
+/* As poll, after waiting up to timeout_s for DONE or FAILED
+ * (DUALIP_ETIMEOUT if neither came). */
+dualip_status dualip_server_wait(dualip_server* s, int64_t ticket, double timeout_s,
+                                 dualip_request_info* info, float* lambda_out);
+dualip_status dualip_server_get_stats(dualip_server* s, dualip_server_stats* stats);
+/* Stops the loop; queued and running requests are dropped. */
+void dualip_server_destroy(dualip_server* s);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* dualip_last_error(void);
 

@@ -32,8 +32,11 @@ EXPORTS = [
     "dualip_batch_create", "dualip_batch_destroy", "dualip_batch_dual_grad",
     "dualip_batch_dual_grad_async", "dualip_batch_solve", "dualip_batch_autotune",
     "dualip_batch_set_tile_shape", "dualip_batch_get_info", "dualip_batch_profile_enable",
-    "dualip_batch_profile_collect",
+    "dualip_batch_profile_collect", "dualip_server_create", "dualip_server_submit",
+    "dualip_server_poll", "dualip_server_wait", "dualip_server_get_stats",
+    "dualip_server_destroy",
 ]
+DUALIP_REQ_QUEUED, DUALIP_REQ_RUNNING, DUALIP_REQ_DONE, DUALIP_REQ_FAILED = 0, 1, 2, 3
 
 
 class DualipError(RuntimeError):
@@ -52,6 +55,21 @@ class AutotuneResult(ctypes.Structure):
         return dict(n_candidates=n, chosen=self.chosen, tile_edges=list(self.tile_edges[:n]),
                     tile_sources=list(self.tile_sources[:n]), ms=list(self.ms[:n]),
                     degree_hist=list(self.degree_hist))
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
+                ("check_every", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "queued", "running", "done", "failed",
+                                              "resident_bytes", "peak_resident_bytes", "chunks",
+                                              "slot_iterations")] + \
+               [("busy_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class ProblemDesc(ctypes.Structure):
@@ -85,6 +103,21 @@ class SolveResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("last", Eval),
                 ("gap_rel", ctypes.c_double), ("infeas_rel", ctypes.c_double),
                 ("gamma", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("result", SolveResult),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("footprint_bytes", ctypes.c_int64),
+                ("num_dests", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def as_dict(self):
+        r = self.result
+        return dict(state=self.state, status=self.status, t_submit=self.t_submit,
+                    t_admit=self.t_admit, t_done=self.t_done,
+                    footprint_bytes=self.footprint_bytes, iters=r.iters,
+                    converged=bool(r.converged), gap_rel=r.gap_rel, infeas_rel=r.infeas_rel,
+                    gamma=r.gamma, **r.last.as_dict())
 
 
 def lib() -> ctypes.CDLL:
@@ -151,6 +184,19 @@ def lib() -> ctypes.CDLL:
         L.dualip_batch_profile_enable.restype = st
         L.dualip_batch_profile_collect.argtypes = [vp, pd, pd, pd, ctypes.POINTER(i32)]
         L.dualip_batch_profile_collect.restype = st
+        L.dualip_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+        L.dualip_server_create.restype = st
+        L.dualip_server_submit.argtypes = [vp, ctypes.POINTER(ProblemDesc),
+                                           ctypes.POINTER(SolveOpts), ctypes.POINTER(i64)]
+        L.dualip_server_submit.restype = st
+        L.dualip_server_poll.argtypes = [vp, i64, ctypes.POINTER(RequestInfo), vp]
+        L.dualip_server_poll.restype = st
+        L.dualip_server_wait.argtypes = [vp, i64, dbl, ctypes.POINTER(RequestInfo), vp]
+        L.dualip_server_wait.restype = st
+        L.dualip_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.dualip_server_get_stats.restype = st
+        L.dualip_server_destroy.argtypes = [vp]
+        L.dualip_server_destroy.restype = None
         L.dualip_last_error.argtypes = []
         L.dualip_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -329,6 +375,44 @@ def dualip_batch_profile_collect(b: int) -> dict:
                 count=n.value)
 
 
+def dualip_server_create(budget_bytes: int, max_slots: int, check_every: int = 10) -> int:
+    o = ServerOpts(int(budget_bytes), int(max_slots), int(check_every))
+    out = ctypes.c_void_p()
+    _check(lib().dualip_server_create(ctypes.byref(o), ctypes.byref(out)))
+    return out.value
+
+
+def dualip_server_submit(srv: int, desc: "ProblemDesc", opts) -> int:
+    t = ctypes.c_int64()
+    _check(lib().dualip_server_submit(srv, ctypes.byref(desc),
+                                      ctypes.byref(opts) if opts is not None else None,
+                                      ctypes.byref(t)))
+    return t.value
+
+
+def dualip_server_poll(srv: int, ticket: int, lam_ptr: int = 0) -> dict:
+    info = RequestInfo()
+    _check(lib().dualip_server_poll(srv, ticket, ctypes.byref(info), lam_ptr or None))
+    return info.as_dict()
+
+
+def dualip_server_wait(srv: int, ticket: int, timeout_s: float, lam_ptr: int = 0) -> dict:
+    info = RequestInfo()
+    _check(lib().dualip_server_wait(srv, ticket, float(timeout_s), ctypes.byref(info),
+                                    lam_ptr or None))
+    return info.as_dict()
+
+
+def dualip_server_get_stats(srv: int) -> dict:
+    st = ServerStats()
+    _check(lib().dualip_server_get_stats(srv, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def dualip_server_destroy(srv: int) -> None:
+    lib().dualip_server_destroy(srv)
+
+
 # ------------------------------------------------- convenience (marshalling) ----
 class Problem:
     """Owns one dualip handle built from host (numpy) or device (torch) arrays.
@@ -492,3 +576,57 @@ class Batch:
 
     def info(self) -> dict:
         return dualip_batch_get_info(self.h)
+
+
+class Server:
+    """The serving loop.  submit() keeps the request's host arrays alive until
+    it has been admitted; wait() returns (info dict, lambda ndarray or None)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, check_every: int = 10):
+        self.h = dualip_server_create(budget_bytes, max_slots, check_every)
+        self._keep = {}
+        self._J = {}
+
+    def submit(self, inst, storage: str = "f32", primal_scaling: bool = False, **opts) -> int:
+        arrs = (np.ascontiguousarray(inst.off, dtype=np.int64),
+                np.ascontiguousarray(inst.dst, dtype=np.int32),
+                np.ascontiguousarray(inst.c, dtype=np.float32),
+                np.ascontiguousarray(inst.a, dtype=np.float32),
+                np.ascontiguousarray(inst.b, dtype=np.float32))
+        d = ProblemDesc(inst.I, inst.E, inst.J, *[a.ctypes.data for a in arrs], 0,
+                        DUALIP_EDGE_BF16 if storage == "bf16" else DUALIP_EDGE_F32,
+                        1 if primal_scaling else 0)
+        o = dualip_solve_opts_default()
+        for k, v in opts.items():
+            setattr(o, "restart_on_gamma_change" if k == "restart" else k, v)
+        t = dualip_server_submit(self.h, d, o)
+        self._keep[t] = arrs
+        self._J[t] = inst.J
+        return t
+
+    def poll(self, ticket: int) -> dict:
+        info = dualip_server_poll(self.h, ticket)
+        if info["state"] != DUALIP_REQ_QUEUED:
+            self._keep.pop(ticket, None)
+        return info
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        lam = np.empty(self._J[ticket], dtype=np.float32)
+        info = dualip_server_wait(self.h, ticket, timeout_s, lam.ctypes.data)
+        self._keep.pop(ticket, None)
+        return info, (lam if info["state"] == DUALIP_REQ_DONE else None)
+
+    def stats(self) -> dict:
+        return dualip_server_get_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", 0):
+            dualip_server_destroy(self.h)
+            self.h = 0
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

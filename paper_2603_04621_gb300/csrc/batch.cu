@@ -16,12 +16,10 @@
 #include <cstring>
 #include <vector>
 
-#include "internal.h"
+#include "batch.h"
 
 namespace dualip {
 namespace {
-
-constexpr int kChunkRows = 2048;  // rows of a J-length chunk
 
 // ------------------------------------------------ double-float helpers ----
 __device__ __forceinline__ float b_two_sum_err(float u, float v, float s) {
@@ -271,13 +269,14 @@ __global__ void bstep_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __
   }
 }
 
-// lambda' = max(0, lambda_caller / D) in renumbered order, y = y_prev = lambda'.
+// lambda' = max(0, lambda_caller / D) in renumbered order (0 without an
+// input), y = y_prev = lambda'.
 __global__ void binit_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __restrict__ sd,
                              const float* __restrict__ lam_in) {
   const RowChunk ch = rc[blockIdx.x];
   const SlotDesc& d = sd[ch.slot];
   for (int j = ch.r0 + threadIdx.x; j < ch.r1; j += blockDim.x) {
-    const float l = lam_in[d.joff + d.orig_of[j]] / d.D[j];
+    const float l = lam_in ? lam_in[d.joff + d.orig_of[j]] / d.D[j] : 0.f;
     const float c = l > 0.f ? l : 0.f;
     d.lam[j] = c;
     d.yv[j] = c;
@@ -299,60 +298,6 @@ __global__ void bfinal_kernel(const RowChunk* __restrict__ rc, const SlotDesc* _
 }  // namespace
 
 // ------------------------------------------------------------ host side ----
-namespace {
-
-struct Batch {
-  int n = 0;
-  int storage = DUALIP_EDGE_F32, weighted = 0;
-  int num_sms = 0;
-  std::vector<Problem*> prob;     // per slot
-  std::vector<SlotDesc> desc;     // host copy of the slot table
-  std::vector<char> active;       // slots in the joint lists
-  int64_t tile_edges = kTileEdges, tile_sources = kTileSources;
-  // per-slot tile lists for the current tile shape (host), and their joint
-  // concatenation for the active slots (device)
-  std::vector<std::vector<JointTile>> tiles;
-  std::vector<JointTile> jt_host;
-  std::vector<RowChunk> rc_host;
-  std::vector<int32_t> act_host;
-  std::vector<int2> crange_host;
-  int64_t ntiles = 0;
-  int nchunks = 0;
-  bool lists_ok = false;
-  // device
-  SlotDesc* d_slots = nullptr;
-  float* d_gamma_f = nullptr;
-  double* d_gamma_d = nullptr;
-  double* d_slot_part = nullptr;
-  double* d_eval = nullptr;
-  SlotSolve* d_ss = nullptr;
-  int32_t* d_act = nullptr;
-  int2* d_crange = nullptr;
-  unsigned* d_tickets = nullptr;
-  DeviceStatus* d_status = nullptr;
-  JointTile* d_jt = nullptr;
-  size_t jt_cap = 0;
-  RowChunk* d_rc = nullptr;
-  float4* d_cpart = nullptr;
-  size_t rc_cap = 0;
-  // pinned staging
-  double* h_gamma = nullptr;  // n doubles then n floats
-  double* h_eval = nullptr;   // 5 n
-  SlotSolve* h_ss = nullptr;  // n
-  // solver vectors (6 per slot, renumbered order), allocated by the solver
-  std::vector<float*> vecs;
-  int row_normalize = -1;
-  cudaStream_t stream = nullptr;
-  cudaEvent_t ev = nullptr;        // stream ordering
-  cudaEvent_t ev_stage = nullptr;  // the gamma staging copies have been read
-  cudaEvent_t ev_use = nullptr;    // the last queued use of the joint lists
-  cudaGraphExec_t graph = nullptr;
-  int graph_len = 0;
-  int grid = 0;
-  // kernel timing of API evaluations (4 events each)
-  std::vector<cudaEvent_t> prof_ev;
-  int prof_used = 0, prof_max = 0;
-};
 
 void free_prof(Batch& B) {
   for (cudaEvent_t ev : B.prof_ev)
@@ -361,23 +306,12 @@ void free_prof(Batch& B) {
   B.prof_used = B.prof_max = 0;
 }
 
-template <class T>
-cudaError_t grow(T** p, size_t& cap, size_t need) {
-  if (need <= cap && *p) return cudaSuccess;
-  if (*p) cudaFree(*p);
-  *p = nullptr;
-  cap = 0;
-  const size_t n = std::max<size_t>(need, 1) * 5 / 4 + 16;
-  cudaError_t e = cudaMalloc(p, sizeof(T) * n);
-  if (e == cudaSuccess) cap = n;
-  return e;
-}
 
 void batch_free(Batch& B) {
   if (B.stream) cudaStreamSynchronize(B.stream);
   if (B.graph) cudaGraphExecDestroy(B.graph);
   void* bufs[] = {B.d_slots, B.d_gamma_f, B.d_gamma_d, B.d_slot_part, B.d_eval, B.d_ss, B.d_act,
-                  B.d_crange, B.d_tickets, B.d_status, B.d_jt, B.d_rc, B.d_cpart};
+                  B.d_crange, B.d_tickets, B.d_status, B.d_jt, B.d_rc, B.d_cpart, B.d_rc2};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (float* p : B.vecs)
@@ -404,7 +338,8 @@ void slot_tiles(const Problem& P, int slot, int64_t max_e, int64_t max_s,
 
 cudaError_t build_slot_tiles(Batch& B) {
   B.tiles.assign(B.n, {});
-  for (int s = 0; s < B.n; ++s) slot_tiles(*B.prob[s], s, B.tile_edges, B.tile_sources, B.tiles[s]);
+  for (int s = 0; s < B.n; ++s)
+    if (B.prob[s]) slot_tiles(*B.prob[s], s, B.tile_edges, B.tile_sources, B.tiles[s]);
   B.lists_ok = false;
   return cudaSuccess;
 }
@@ -536,7 +471,172 @@ dualip_status batch_status(Batch& B) {
   return DUALIP_OK;
 }
 
-}  // namespace
+cudaError_t batch_alloc(Batch& B, int capacity, int storage, int weighted, int num_sms) {
+  const int n = capacity;
+  B.n = n;
+  B.storage = storage;
+  B.weighted = weighted;
+  B.num_sms = num_sms;
+  B.prob.assign(n, nullptr);
+  B.desc.assign(n, SlotDesc{});
+  B.active.assign(n, 0);
+  B.vecs.assign(n, nullptr);
+  B.tiles.assign(n, {});
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&B.stream, cudaStreamNonBlocking)) ||
+      (e = cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming)) ||
+      (e = cudaEventCreateWithFlags(&B.ev_stage, cudaEventDisableTiming)) ||
+      (e = cudaEventCreateWithFlags(&B.ev_use, cudaEventDisableTiming)) ||
+      (e = cudaMalloc(&B.d_slots, sizeof(SlotDesc) * n)) ||
+      (e = cudaMalloc(&B.d_gamma_f, sizeof(float) * n)) ||
+      (e = cudaMalloc(&B.d_gamma_d, sizeof(double) * n)) ||
+      (e = cudaMalloc(&B.d_slot_part, sizeof(double) * 2 * n)) ||
+      (e = cudaMalloc(&B.d_eval, sizeof(double) * 5 * n)) ||
+      (e = cudaMalloc(&B.d_ss, sizeof(SlotSolve) * n)) ||
+      (e = cudaMalloc(&B.d_act, sizeof(int32_t) * n)) ||
+      (e = cudaMalloc(&B.d_crange, sizeof(int2) * n)) ||
+      (e = cudaMalloc(&B.d_tickets, sizeof(unsigned) * 2)) ||
+      (e = cudaMalloc(&B.d_status, sizeof(DeviceStatus))) ||
+      (e = cudaMallocHost(&B.h_gamma, sizeof(double) * 2 * n)) ||
+      (e = cudaMallocHost(&B.h_eval, sizeof(double) * 5 * n)) ||
+      (e = cudaMallocHost(&B.h_ss, sizeof(SlotSolve) * n)))
+    return e;
+  if ((e = cudaMemsetAsync(B.d_slot_part, 0, sizeof(double) * 2 * n, B.stream)) ||
+      (e = cudaMemsetAsync(B.d_tickets, 0, sizeof(unsigned) * 2, B.stream)) ||
+      (e = cudaMemsetAsync(B.d_status, 0, sizeof(DeviceStatus), B.stream)) ||
+      (e = cudaMemsetAsync(B.d_eval, 0, sizeof(double) * 5 * n, B.stream)) ||
+      (e = cudaMemsetAsync(B.d_ss, 0, sizeof(SlotSolve) * n, B.stream)) ||
+      (e = cudaMemsetAsync(B.d_slots, 0, sizeof(SlotDesc) * n, B.stream)) ||
+      (e = cudaEventRecord(B.ev_stage, B.stream)) || (e = cudaEventRecord(B.ev_use, B.stream)) ||
+      (e = cudaStreamSynchronize(B.stream)))
+    return e;
+  return cudaSuccess;
+}
+
+SlotDesc slot_desc(Problem& P, int64_t joff) {
+  SlotDesc d{};
+  d.off = P.off;
+  d.dst = P.dst;
+  d.ca2 = P.ca2;
+  d.ca = P.ca;
+  d.mu_r = P.mu_r;
+  d.y = P.y;
+  d.orig_of = P.orig_of;
+  d.b_r = P.b_r;
+  d.J = P.J;
+  d.h_mu = P.h_mu;
+  d.h_y = P.h_y;
+  d.sy = ldexpf(1.0f, P.exp_y);
+  d.inv_sy = ldexpf(1.0f, -P.exp_y);
+  d.joff = joff;
+  return d;
+}
+
+static cudaError_t slot_chunks(Batch& B, int slot) {
+  std::vector<RowChunk> rc;
+  for (int32_t r = 0; r < B.prob[slot]->J; r += kChunkRows)
+    rc.push_back(RowChunk{slot, r, std::min<int32_t>(B.prob[slot]->J, r + kChunkRows), 0});
+  cudaError_t e;
+  if ((e = grow(&B.d_rc2, B.rc2_cap, rc.size()))) return e;
+  B.nrc2 = (int)rc.size();
+  return rc.empty() ? cudaSuccess
+                    : cudaMemcpyAsync(B.d_rc2, rc.data(), sizeof(RowChunk) * rc.size(),
+                                      cudaMemcpyHostToDevice, B.stream);
+}
+
+SlotSolve slot_solve_init(const dualip_solve_opts& o, double bnorm) {
+  SlotSolve S;
+  std::memset(&S, 0, sizeof(S));
+  S.gamma0 = o.gamma0;
+  S.gamma_final = o.gamma_final;
+  S.max_step = o.max_step;
+  S.init_step = o.init_step;
+  S.bnorm = bnorm;
+  S.halve_every = o.halve_every;
+  S.restart = o.restart_on_gamma_change ? 1 : 0;
+  S.t = 1.0;
+  return S;
+}
+
+int batch_attach(Batch& B, Problem* P, const dualip_solve_opts& o, cudaError_t* err) {
+  *err = cudaSuccess;
+  int s = -1;
+  for (int k = 0; k < B.n && s < 0; ++k)
+    if (!B.prob[k]) s = k;
+  if (s < 0) return -1;
+  cudaError_t e;
+  float* v = nullptr;
+  const int32_t J = P->J;
+  if ((e = cudaMalloc(&v, sizeof(float) * 6 * std::max<int32_t>(J, 1)))) {
+    *err = e;
+    return -1;
+  }
+  B.prob[s] = P;
+  B.vecs[s] = v;
+  SlotDesc d = slot_desc(*P, 0);
+  d.lam = v;
+  d.yv = v + J;
+  d.yp = v + 2 * (size_t)J;
+  d.G = v + 3 * (size_t)J;
+  d.Gp = v + 4 * (size_t)J;
+  d.D = v + 5 * (size_t)J;
+  B.desc[s] = d;
+  slot_tiles(*P, s, B.tile_edges, B.tile_sources, B.tiles[s]);
+  B.h_ss[s] = slot_solve_init(o, P->bnorm);
+  if ((e = compute_row_scale(*P, o.row_normalize ? 1 : 0, d.D, B.stream)) ||
+      (e = upload_slots(B)) ||
+      (e = cudaMemcpyAsync(B.d_ss + s, B.h_ss + s, sizeof(SlotSolve), cudaMemcpyHostToDevice,
+                           B.stream)) ||
+      (e = cudaMemsetAsync(B.d_slot_part + 2 * s, 0, 2 * sizeof(double), B.stream)) ||
+      (e = slot_chunks(B, s))) {
+    *err = e;
+    batch_detach(B, s);
+    return -1;
+  }
+  if (B.nrc2) {
+    binit_kernel<<<B.nrc2, 256, 0, B.stream>>>(B.d_rc2, B.d_slots, nullptr);
+    if ((e = cudaGetLastError()) || (e = cudaStreamSynchronize(B.stream))) {
+      *err = e;
+      batch_detach(B, s);
+      return -1;
+    }
+  }
+  B.active[s] = 1;
+  B.lists_ok = false;
+  return s;
+}
+
+cudaError_t batch_write_lambda(Batch& B, int slot, float* lam_out) {
+  cudaError_t e = slot_chunks(B, slot);
+  if (e) return e;
+  if (B.nrc2) {
+    bfinal_kernel<<<B.nrc2, 256, 0, B.stream>>>(B.d_rc2, B.d_slots, lam_out);
+    if ((e = cudaGetLastError())) return e;
+  }
+  return cudaStreamSynchronize(B.stream);
+}
+
+void batch_detach(Batch& B, int slot) {
+  cudaStreamSynchronize(B.stream);
+  if (B.vecs[slot]) cudaFree(B.vecs[slot]);
+  B.vecs[slot] = nullptr;
+  B.prob[slot] = nullptr;
+  B.desc[slot] = SlotDesc{};
+  B.tiles[slot].clear();
+  B.active[slot] = 0;
+  B.lists_ok = false;
+}
+
+cudaError_t batch_read_state(Batch& B) {
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(B.h_ss, B.d_ss, sizeof(SlotSolve) * B.n, cudaMemcpyDeviceToHost,
+                           B.stream)) ||
+      (e = cudaMemcpyAsync(B.h_eval, B.d_eval, sizeof(double) * 5 * B.n, cudaMemcpyDeviceToHost,
+                           B.stream)))
+    return e;
+  return cudaStreamSynchronize(B.stream);
+}
+
 }  // namespace dualip
 
 struct dualip_batch {
@@ -610,59 +710,18 @@ dualip_status dualip_batch_create(int32_t n, dualip_problem* const* problems, du
     delete h;
     return st;
   };
-  B.n = n;
-  B.storage = problems[0]->p.storage;
-  B.weighted = problems[0]->p.weighted;
-  B.num_sms = problems[0]->p.num_sms;
-  B.active.assign(n, 1);
-  B.vecs.assign(n, nullptr);
+  cudaError_t e = batch_alloc(B, n, problems[0]->p.storage, problems[0]->p.weighted,
+                              problems[0]->p.num_sms);
+  if (e) return bail(cuda_fail(e, "allocating the batch"));
   int64_t joff = 0;
   for (int k = 0; k < n; ++k) {
     Problem& P = problems[k]->p;
-    B.prob.push_back(&P);
-    SlotDesc d{};
-    d.off = P.off;
-    d.dst = P.dst;
-    d.ca2 = P.ca2;
-    d.ca = P.ca;
-    d.mu_r = P.mu_r;
-    d.y = P.y;
-    d.orig_of = P.orig_of;
-    d.b_r = P.b_r;
-    d.J = P.J;
-    d.h_mu = P.h_mu;
-    d.h_y = P.h_y;
-    d.sy = ldexpf(1.0f, P.exp_y);
-    d.inv_sy = ldexpf(1.0f, -P.exp_y);
-    d.joff = joff;
+    B.prob[k] = &P;
+    B.desc[k] = slot_desc(P, joff);
+    B.active[k] = 1;
     joff += P.J;
-    B.desc.push_back(d);
   }
-  cudaError_t e;
-  if ((e = cudaStreamCreateWithFlags(&B.stream, cudaStreamNonBlocking)) ||
-      (e = cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming)) ||
-      (e = cudaEventCreateWithFlags(&B.ev_stage, cudaEventDisableTiming)) ||
-      (e = cudaEventCreateWithFlags(&B.ev_use, cudaEventDisableTiming)) ||
-      (e = cudaMalloc(&B.d_slots, sizeof(SlotDesc) * n)) ||
-      (e = cudaMalloc(&B.d_gamma_f, sizeof(float) * n)) ||
-      (e = cudaMalloc(&B.d_gamma_d, sizeof(double) * n)) ||
-      (e = cudaMalloc(&B.d_slot_part, sizeof(double) * 2 * n)) ||
-      (e = cudaMalloc(&B.d_eval, sizeof(double) * 5 * n)) ||
-      (e = cudaMalloc(&B.d_ss, sizeof(SlotSolve) * n)) ||
-      (e = cudaMalloc(&B.d_act, sizeof(int32_t) * n)) ||
-      (e = cudaMalloc(&B.d_crange, sizeof(int2) * n)) ||
-      (e = cudaMalloc(&B.d_tickets, sizeof(unsigned) * 2)) ||
-      (e = cudaMalloc(&B.d_status, sizeof(DeviceStatus))) ||
-      (e = cudaMallocHost(&B.h_gamma, sizeof(double) * 2 * n)) ||
-      (e = cudaMallocHost(&B.h_eval, sizeof(double) * 5 * n)) ||
-      (e = cudaMallocHost(&B.h_ss, sizeof(SlotSolve) * n)))
-    return bail(cuda_fail(e, "allocating the batch"));
-  if ((e = cudaMemsetAsync(B.d_slot_part, 0, sizeof(double) * 2 * n, B.stream)) ||
-      (e = cudaMemsetAsync(B.d_tickets, 0, sizeof(unsigned) * 2, B.stream)) ||
-      (e = cudaMemsetAsync(B.d_status, 0, sizeof(DeviceStatus), B.stream)) ||
-      (e = cudaMemsetAsync(B.d_eval, 0, sizeof(double) * 5 * n, B.stream)) ||
-      (e = cudaEventRecord(B.ev_stage, B.stream)) || (e = cudaEventRecord(B.ev_use, B.stream)) ||
-      (e = upload_slots(B)) || (e = build_slot_tiles(B)) || (e = rebuild_lists(B)) ||
+  if ((e = upload_slots(B)) || (e = build_slot_tiles(B)) || (e = rebuild_lists(B)) ||
       (e = cudaStreamSynchronize(B.stream)))
     return bail(cuda_fail(e, "initialising the batch"));
   *out = h;
@@ -791,18 +850,7 @@ dualip_status dualip_batch_solve(dualip_batch* b, const dualip_solve_opts* opts,
         return cuda_fail(e, "computing row scales");
     B.row_normalize = rn;
   }
-  for (int k = 0; k < B.n; ++k) {
-    SlotSolve& S = B.h_ss[k];
-    std::memset(&S, 0, sizeof(S));
-    S.gamma0 = O(k).gamma0;
-    S.gamma_final = O(k).gamma_final;
-    S.max_step = O(k).max_step;
-    S.init_step = O(k).init_step;
-    S.bnorm = B.prob[k]->bnorm;
-    S.halve_every = O(k).halve_every;
-    S.restart = O(k).restart_on_gamma_change ? 1 : 0;
-    S.t = 1.0;
-  }
+  for (int k = 0; k < B.n; ++k) B.h_ss[k] = slot_solve_init(O(k), B.prob[k]->bnorm);
   std::fill(B.active.begin(), B.active.end(), 1);
   B.lists_ok = false;
   if ((e = upload_slots(B)) ||
