@@ -43,9 +43,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: 1M x 10k, ~50M edges (default); c3: 25M x 1M, ~2.0B edges; "
-                         "c4: 256 problems in one batched pass, ~3.4B edges")
+                         "c4: 256 problems in one batched pass, ~3.4B edges; "
+                         "c5: a Poisson stream of solve requests through the server")
+    ap.add_argument("--requests", type=int, default=60,
+                    help="c5: the first N requests of the seeded trace")
+    ap.add_argument("--budget-gib", type=float, default=160.0, help="c5: HBM budget")
     ap.add_argument("--storage", default=None, choices=["f32", "bf16"],
                     help="edge storage (default f32 for c2, bf16 for c3)")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the sources")
@@ -77,6 +81,9 @@ WORKLOADS = {
            "Zipf(1.1) destinations, c=-LogNormal(0,1), a~U(0.5,1.5), b=0.2*sum(a), int32 dst"),
     "c3": ("c3: matching LP, 25M sources x 1M destinations, Poisson(80) degrees in [1,2000], "
            "Zipf(1.1) destinations, c=-LogNormal(0,1), a~U(0.5,1.5), b=0.2*sum(a), int64 offsets"),
+    "c5": ("c5: Poisson(20/s) stream of matching-LP solves, sources LogUniform[10k,5M], "
+           "destinations LogUniform[100,200k], degrees Poisson(40) in [1,J], FP32 or BF16 storage "
+           "(1/2 each), greedy-load budgets (App. B rule), each solved to a 1e-4 gap"),
     "c4": ("c4: 256 independent matching LPs in one batched pass, sources LogUniform[1k,2M], "
            "destinations LogUniform[10,50k], degrees Uniform[5,100] (<= J), Zipf(1.1) "
            "destinations, c=-LogNormal(0,1), a~U(0.5,1.5), greedy-load budgets (App. B rule)"),
@@ -402,9 +409,86 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """c5: replay the first N requests of the trace in real time through the
+    server; then solve each request alone with the plain FP32 form."""
+    import torch
+    import synth
+
+    torch.cuda.set_device(0)
+    from paper_2603_04621_gb300 import build
+
+    build.build()
+    import paper_2603_04621_gb300 as d
+
+    trace = synth.request_trace(400)[: args.requests]
+    insts = [synth.greedy_budgets(synth.request_instance(r)) for r in trace]
+    srv = d.Server(int(args.budget_gib * (1 << 30)), max_slots=64, check_every=10)
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        tickets = []
+        for r, x in zip(trace, insts):
+            dt = r["t"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(x, storage=r["storage"]))
+        out = [srv.wait(t, 3600.0) for t in tickets]
+        span = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    infos = [o[0] for o in out]
+    ok = [i for i in infos if i["state"] == d.DUALIP_REQ_DONE]
+    ttg = np.array([i["t_done"] - i["t_submit"] for i in ok])
+    qd = np.array([i["t_admit"] - i["t_submit"] for i in ok])
+    conv = sum(i["converged"] for i in ok)
+    work = sum(x.E * i["iters"] for x, i in zip(insts, infos) if i["state"] == d.DUALIP_REQ_DONE)
+    # the plain FP32 single-instance form, one request after another
+    lone_t, lone_conv = 0.0, 0
+    for x in insts:
+        P = d.Problem.from_instance(x)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, r1 = P.solve()
+        torch.cuda.synchronize()
+        lone_t += time.perf_counter() - t1
+        lone_conv += r1["converged"]
+        P.close()
+    n = len(insts)
+    out_line = {
+        "metric": "serve time-to-1e-4-gap p50", "value": float(np.median(ttg)), "unit": "s",
+        "n_gpus": 1, "steps": n, "warmup": 0, "ms_per_step": 1e3 * span / n,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["c5"], "requests": n, "arrival_rate_per_s": 20.0,
+                   "budget_gib": args.budget_gib, "max_slots": 64, "check_every": 10,
+                   "E_mean": float(np.mean([x.E for x in insts])),
+                   "bf16_requests": sum(r["storage"] == "bf16" for r in trace),
+                   "parallelism": "replicas"},
+        "serve": {"p50_s": float(np.median(ttg)), "p99_s": float(np.quantile(ttg, 0.99)),
+                  "queue_p50_s": float(np.median(qd)), "queue_p99_s": float(np.quantile(qd, 0.99)),
+                  "done": len(ok), "converged": conv, "failed": n - len(ok),
+                  "solves_per_s": len(ok) / span, "span_s": span,
+                  "arrival_span_s": trace[-1]["t"],
+                  "edge_iterations_per_s": work / span,
+                  "busy_s": st["busy_seconds"], "peak_resident_gib": st["peak_resident_bytes"] / 2**30},
+        "lone_fp32_sequential": {"seconds": lone_t, "solves_per_s": n / lone_t,
+                                 "converged": lone_conv},
+        "e2e": {"value": float(np.median(ttg)), "unit": "s",
+                "h2d_bytes_per_step": int(np.mean([12 * x.E + 8 * x.I + 4 * x.J for x in insts])),
+                "d2h_bytes_per_step": int(np.mean([4 * x.J for x in insts])),
+                "api": "dualip_server_submit / _wait (host arrays in, lambda to host)"},
+        "clocks": clk.summary(),
+        "gpu_launches": int(st["chunks"] * 10 * 5),
+    }
+    print(json.dumps(out_line), flush=True)
+    return 0
+
+
 def run_ours(args):
     if args.workload == "c4":
         return run_batch(args)
+    if args.workload == "c5":
+        return run_serve(args)
     import torch
 
     ws, rank, local = dist_env()
