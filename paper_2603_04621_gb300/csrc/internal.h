@@ -20,7 +20,7 @@ namespace dualip {
 #define DUALIP_STAGES 4
 #endif
 #ifndef DUALIP_CONSUMER_WARPS
-#define DUALIP_CONSUMER_WARPS 16
+#define DUALIP_CONSUMER_WARPS 18
 #endif
 #ifndef DUALIP_PRIV_DESTS
 #define DUALIP_PRIV_DESTS 2048

@@ -240,6 +240,7 @@ struct Layout {
                 "16-byte staging");
   static_assert(kTotal <= 227 * 1024, "shared memory budget");
   static_assert(kMisc % 16 == 0, "float4 reduction slots at kMisc + 16");
+  static_assert(16 + 16 * (kThreads / 32) <= 320, "reduction slots end before the claim counters");
 };
 
 // Stage layout: offsets | dst (4 B per slot, padded) | c, a (8 B per slot:
@@ -1047,12 +1048,27 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
           if (WRITE_X) {
             needm = __ballot_sync(0xffffffffu, dq > 0);
           } else {
-            const unsigned m64 = __ballot_sync(0xffffffffu, dq > 0 && spq <= 64);
-            const unsigned m128 = __ballot_sync(0xffffffffu, spq > 64 && spq <= 128);
+            // 4-lane groups take spans up to 80 in one pass, with the window
+            // (runs of 4 edges per lane) sized by the batch's largest span
+            const bool in4 = dq > 0 && spq <= 80;
+            const unsigned m4 = __ballot_sync(0xffffffffu, in4);
+            const unsigned m128 = __ballot_sync(0xffffffffu, spq > 80 && spq <= 128);
             const unsigned m256 = __ballot_sync(0xffffffffu, spq > 128 && spq <= 256);
             const unsigned m512 = __ballot_sync(0xffffffffu, spq > 256 && spq <= 512);
             needm = __ballot_sync(0xffffffffu, spq > 512);
-            if (m64) needm |= lean_over<4, 4, BF16, W, MU_SMEM, BATCH>(sv, m64, bq, dq, lane, cx, acc);
+            if (m4) {
+              const unsigned w4 = __reduce_max_sync(0xffffffffu, in4 ? (unsigned)spq : 0u);
+              if (w4 <= 16)
+                needm |= lean_over<4, 1, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
+              else if (w4 <= 32)
+                needm |= lean_over<4, 2, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
+              else if (w4 <= 48)
+                needm |= lean_over<4, 3, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
+              else if (w4 <= 64)
+                needm |= lean_over<4, 4, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
+              else
+                needm |= lean_over<4, 5, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
+            }
             if (m128) needm |= lean_over<8, 4, BF16, W, MU_SMEM, BATCH>(sv, m128, bq, dq, lane, cx, acc);
             if (m256) needm |= lean_over<16, 4, BF16, W, MU_SMEM, BATCH>(sv, m256, bq, dq, lane, cx, acc);
             if (m512) needm |= lean_over<32, 4, BF16, W, MU_SMEM, BATCH>(sv, m512, bq, dq, lane, cx, acc);
