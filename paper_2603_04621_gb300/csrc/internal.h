@@ -56,7 +56,8 @@ struct DeviceStatus {
   int err;        // OR of kErr* bits
   int where;      // first wait site that timed out
   unsigned ticket;  // last-block counter of the epilogue (reset by the last block)
-  int pad;
+  unsigned done;    // CTAs of the pass that have finished (reset by the last one)
+  unsigned long long tile_next;  // next tile of the pass's dynamic schedule
 };
 
 // Kernel parameters of the J-length epilogue.

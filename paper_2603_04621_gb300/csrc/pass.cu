@@ -210,7 +210,7 @@ __device__ __forceinline__ long long to_fixed(float v, float scale) {
 }
 
 // --------------------------------------------------------- smem layout ----
-struct StageInfo {
+struct alignas(16) StageInfo {
   int64_t s0, s1;  // sources [s0, s1)
   int64_t e0, e1;  // edges [e0, e1)
   int64_t a0;      // first staged edge (multiple of 4)
@@ -799,10 +799,6 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     *abort = 0;
     fence_mbar_init();
   }
-  if (!BATCH) {
-    for (int j = tid; j < p.h_mu; j += blockDim.x) mu_s[j] = p.mu_r[j];
-    for (int j = tid; j < p.h_y; j += blockDim.x) y_s[j] = 0ull;
-  }
   for (int s = 0; s < kStages; ++s) {
     uint32_t* d = reinterpret_cast<uint32_t*>(smem + (size_t)s * L::kStageBytes + L::kOffBytes);
     for (int k = tid; k < (int)(L::kDstArr / 4); k += blockDim.x) d[k] = 0u;
@@ -841,7 +837,8 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
 
   if (warp == 0) {
     // ------------------------------------------------------ producer ----
-    // The warp fetches 32 tile descriptors per load; lane 0 waits and issues.
+    // The warp fetches tile descriptors a group at a time; lane 0 waits and
+    // issues the copies.
     int64_t it = 0;
     bool stop = false;
     int pslot = -1;  // batched pass: slot of the edge pointers below
@@ -849,94 +846,110 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     const int32_t* dstp = p.dst;
     const float2* ca2p = p.ca2;
     const uint32_t* cap = p.ca;
-    for (int64_t t0 = t_begin; t0 < t_end && !stop; t0 += 32) {
-      int64_t my_s, my_e, my_s1 = 0, my_e1 = 0, ext_s = 0, ext_e = 0;
-      int my_slot = 0;
-      if (BATCH) {
-        const JointTile jt = p.jt[t0 + lane < t_end ? t0 + lane : t_end - 1];
-        my_s = jt.s0;
-        my_e = jt.e0;
-        my_s1 = jt.s1;
-        my_e1 = jt.e1;
-        my_slot = jt.slot;
-      } else {
-        const int64_t tl = t0 + lane < t_end ? t0 + lane : t_end;
-        my_s = p.tiles[tl];
-        my_e = p.tile_e[tl];
-        const int64_t ext = t0 + 32 < t_end ? t0 + 32 : t_end;
-        ext_s = p.tiles[ext];
-        ext_e = p.tile_e[ext];
+    // Lane 0 stages one tile (or, with done, the end marker) into the next
+    // ring slot once every consumer has left the slot's previous tile.
+    auto stage = [&](int64_t s0, int64_t s1, int64_t e0, int64_t e1, int slot, bool done) {
+      if (lane != 0) return;
+      if (BATCH && slot != pslot) {
+        const SlotDesc* d = p.slots + slot;
+        offp = d->off;
+        dstp = d->dst;
+        ca2p = d->ca2;
+        cap = d->ca;
+        pslot = slot;
       }
-      const int cnt = (int)(t_end - t0 < 32 ? t_end - t0 : 32);
-      for (int k = 0; k < cnt; ++k, ++it) {
-        const int64_t s0 = __shfl_sync(0xffffffffu, my_s, k);
-        const int64_t e0 = __shfl_sync(0xffffffffu, my_e, k);
-        int64_t s1, e1;
-        int slot = 0;
-        if (BATCH) {
-          s1 = __shfl_sync(0xffffffffu, my_s1, k);
-          e1 = __shfl_sync(0xffffffffu, my_e1, k);
-          slot = __shfl_sync(0xffffffffu, my_slot, k);
+      const int s = (int)(it % kStages);
+      const uint32_t round = (uint32_t)(it / kStages);
+      if (round > 0 && !wait_phase(&empty[s], (round - 1) & 1u, abort, p.status, 1)) {
+        stop = true;
+        return;
+      }
+      claim[s] = 0u;  // every consumer has left this stage's last tile
+      StageInfo si;
+      si.s0 = s0;
+      si.s1 = s1;
+      si.e0 = e0;
+      si.e1 = e1;
+      const bool bad = !done && (s1 - s0 > kTileSources || s1 < s0 || e1 < e0 ||
+                                 (e1 - e0 > kTileEdges && s1 - s0 != 1));
+      if (bad) {
+        atomicOr(&p.status->err, kErrBounds);
+        si.s1 = s0;  // skip the tile; results are flagged invalid
+      }
+      si.big = done ? 2 : ((!bad && e1 - e0 > kTileEdges) ? 1 : 0);
+      si.slot = slot;
+      si.a0 = e0 & ~int64_t(3);
+      si.o0 = s0 & ~int64_t(1);
+      info[s] = si;
+      if (bad || si.big) {
+        mbar_arrive(&full[s]);
+        return;
+      }
+      const int64_t a1 = (e1 + 3) & ~int64_t(3);
+      const int64_t o1 = (s1 + 2) & ~int64_t(1);
+      const uint32_t ne = (uint32_t)(a1 - si.a0), no = (uint32_t)(o1 - si.o0);
+      const uint32_t bytes = no * 8u + ne * (BF16 ? 8u : 12u);
+      mbar_arrive_expect_tx(&full[s], bytes);
+      unsigned char* base = smem + (size_t)s * L::kStageBytes;
+      bulk_g2s(base, offp + si.o0, no * 8u, &full[s]);
+      if (ne) {
+        bulk_g2s(base + L::kOffBytes, dstp + si.a0, ne * 4u, &full[s]);
+        if (BF16) {
+          bulk_g2s(base + L::kOffBytes + L::kDstArr, cap + si.a0, ne * 4u, &full[s]);
         } else {
-          const int64_t s1n = __shfl_sync(0xffffffffu, my_s, (k + 1) & 31);
-          const int64_t e1n = __shfl_sync(0xffffffffu, my_e, (k + 1) & 31);
-          s1 = k < 31 ? s1n : ext_s;
-          e1 = k < 31 ? e1n : ext_e;
+          bulk_g2s(base + L::kOffBytes + L::kDstArr, ca2p + si.a0, ne * 8u, &full[s]);
         }
-        if (lane == 0) {
-          if (BATCH && slot != pslot) {
-            const SlotDesc* d = p.slots + slot;
-            offp = d->off;
-            dstp = d->dst;
-            ca2p = d->ca2;
-            cap = d->ca;
-            pslot = slot;
-          }
-          const int s = (int)(it % kStages);
-          const uint32_t round = (uint32_t)(it / kStages);
-          if (round > 0 && !wait_phase(&empty[s], (round - 1) & 1u, abort, p.status, 1)) {
-            stop = true;
-          } else {
-            claim[s] = 0u;  // every consumer has left this stage's last tile
-            StageInfo si;
-            si.s0 = s0;
-            si.s1 = s1;
-            si.e0 = e0;
-            si.e1 = e1;
-            const bool bad = s1 - s0 > kTileSources || s1 < s0 || e1 < e0 ||
-                             (e1 - e0 > kTileEdges && s1 - s0 != 1);
-            if (bad) {
-              atomicOr(&p.status->err, kErrBounds);
-              si.s1 = s0;  // skip the tile; results are flagged invalid
-            }
-            si.big = (!bad && e1 - e0 > kTileEdges) ? 1 : 0;
-            si.slot = slot;
-            si.a0 = e0 & ~int64_t(3);
-            si.o0 = s0 & ~int64_t(1);
-            info[s] = si;
-            if (bad || si.big) {
-              mbar_arrive(&full[s]);
-            } else {
-              const int64_t a1 = (e1 + 3) & ~int64_t(3);
-              const int64_t o1 = (s1 + 2) & ~int64_t(1);
-              const uint32_t ne = (uint32_t)(a1 - si.a0), no = (uint32_t)(o1 - si.o0);
-              const uint32_t bytes = no * 8u + ne * (BF16 ? 8u : 12u);
-              mbar_arrive_expect_tx(&full[s], bytes);
-              unsigned char* base = smem + (size_t)s * L::kStageBytes;
-              bulk_g2s(base, offp + si.o0, no * 8u, &full[s]);
-              if (ne) {
-                bulk_g2s(base + L::kOffBytes, dstp + si.a0, ne * 4u, &full[s]);
-                if (BF16) {
-                  bulk_g2s(base + L::kOffBytes + L::kDstArr, cap + si.a0, ne * 4u, &full[s]);
-                } else {
-                  bulk_g2s(base + L::kOffBytes + L::kDstArr, ca2p + si.a0, ne * 8u, &full[s]);
-                }
-              }
-            }
-          }
+      }
+    };
+    if (BATCH) {
+      // a contiguous range of the joint list (slot switches stay rare)
+      for (int64_t t0 = t_begin; t0 < t_end && !stop; t0 += 32) {
+        const JointTile jt = p.jt[t0 + lane < t_end ? t0 + lane : t_end - 1];
+        const int cnt = (int)(t_end - t0 < 32 ? t_end - t0 : 32);
+        for (int k = 0; k < cnt; ++k) {
+          const int64_t s0 = __shfl_sync(0xffffffffu, jt.s0, k);
+          const int64_t e0 = __shfl_sync(0xffffffffu, jt.e0, k);
+          const int64_t s1 = __shfl_sync(0xffffffffu, jt.s1, k);
+          const int64_t e1 = __shfl_sync(0xffffffffu, jt.e1, k);
+          const int slot = __shfl_sync(0xffffffffu, jt.slot, k);
+          stage(s0, s1, e0, e1, slot, false);
+          ++it;
+          stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
+          if (stop) break;
         }
-        stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
-        if (stop) break;
+      }
+    } else {
+      // Dynamic tile grabs of kGrab tiles from a counter shared by all CTAs
+      // (balanced ends); the next grab is requested while this one is
+      // staged.  The end marker stops the consumers.
+      constexpr int kGrab = 4;
+      unsigned long long* next = &p.status->tile_next;
+      long long nxt = 0;
+      if (lane == 0) nxt = (long long)atomicAdd(next, (unsigned long long)kGrab);
+      nxt = __shfl_sync(0xffffffffu, nxt, 0);
+      while (!stop && nxt < p.ntiles) {
+        const int64_t t0 = nxt;
+        const int64_t te = t0 + kGrab < p.ntiles ? t0 + kGrab : p.ntiles;
+        long long fut = 0;
+        if (lane == 0) fut = (long long)atomicAdd(next, (unsigned long long)kGrab);
+        const int64_t tl = t0 + lane < te ? t0 + lane : te;
+        const int64_t my_s = p.tiles[tl], my_e = p.tile_e[tl];
+        const int cnt = (int)(te - t0);
+        for (int k = 0; k < cnt; ++k) {
+          const int64_t s0 = __shfl_sync(0xffffffffu, my_s, k);
+          const int64_t e0 = __shfl_sync(0xffffffffu, my_e, k);
+          const int64_t s1 = __shfl_sync(0xffffffffu, my_s, k + 1);
+          const int64_t e1 = __shfl_sync(0xffffffffu, my_e, k + 1);
+          stage(s0, s1, e0, e1, 0, false);
+          ++it;
+          stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
+          if (stop) break;
+        }
+        nxt = __shfl_sync(0xffffffffu, fut, 0);
+      }
+      if (!stop) {
+        stage(0, 0, 0, 0, 0, true);
+        ++it;
       }
     }
     // drain: every armed stage must have landed before the CTA may exit
@@ -958,6 +971,13 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     __syncwarp();
   } else {
     // ------------------------------------------------------ consumers ----
+    // The mu cache and the shared bins, while the producer already streams;
+    // the consumer warps then meet (the producer does not take part).
+    if (!BATCH) {
+      for (int j = tid - 32; j < p.h_mu; j += kConsumerWarps * 32) mu_s[j] = p.mu_r[j];
+      for (int j = tid - 32; j < p.h_y; j += kConsumerWarps * 32) y_s[j] = 0ull;
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
     // Every consumer warp visits every tile and claims work from it through
     // the stage's counter (one batch of eight sources per claim), so a warp
     // that is done early takes the next batch, of this tile or the next.  A
@@ -966,12 +986,15 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     // every warp has left, so no claim can reach a refilled stage.
     int64_t it = 0;
     uint32_t nsw = 0;  // slot switches so far (phase of the consumer barriers)
-    for (int64_t t = t_begin; t < t_end; ++t, ++it) {
+    // (a batched pass takes a fixed range of tiles; otherwise the producer's
+    // end marker closes the stream)
+    for (int64_t t = t_begin; !BATCH || t < t_end; ++t, ++it) {
       const int s = (int)(it % kStages);
       const uint32_t round = (uint32_t)(it / kStages);
       const bool ok = wait_phase(&full[s], round & 1u, abort, p.status, 2);
       if (!__all_sync(0xffffffffu, ok)) break;
       const StageInfo si = info[s];
+      if (si.big == 2) break;
       if (BATCH && si.slot != cur) {
         // Every consumer warp visits every tile, so all of them switch here.
         // Meet once the previous slot's tiles are done, move the shared
@@ -1120,6 +1143,12 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         pair_addp(t.z, t.w, u.z, u.w);
       }
       p.part[blockIdx.x] = t;
+      // the last CTA to finish rewinds the tile counter for the next launch
+      __threadfence();
+      if (atomicAdd(&p.status->done, 1u) == gridDim.x - 1) {
+        p.status->tile_next = 0ull;
+        p.status->done = 0u;
+      }
     }
   }
 }
