@@ -79,6 +79,7 @@ __device__ inline bool slot_restart(const SlotSolve& s, int32_t k) {
 __global__ void bprep_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __restrict__ sd,
                              const float* __restrict__ lam, int solver, SlotSolve* ss,
                              float* gamma_f, double* gamma_d) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the pass may launch
   const RowChunk ch = rc[blockIdx.x];
   const SlotDesc& d = sd[ch.slot];
   if (!solver) {
@@ -113,6 +114,8 @@ __global__ void bepi_kernel(const RowChunk* __restrict__ rc, int nchunks,
                             float4* __restrict__ cpart, const int32_t* __restrict__ act, int nact,
                             const int2* __restrict__ crange, double* slot_part,
                             const double* __restrict__ gamma_d, double* eval, unsigned* ticket) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // A x and the partials of the pass
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const RowChunk ch = rc[blockIdx.x];
   const SlotDesc& d = sd[ch.slot];
   float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -415,10 +418,11 @@ cudaError_t enqueue_batch_eval(Batch& B, const float* lam, float* grad, int solv
                              B.d_slot_part, B.d_status, B.grid, s)))
     return e;
   if (ev && (e = cudaEventRecord(ev[2], s))) return e;
-  bepi_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.nchunks, B.d_slots, grad, solver, B.d_cpart,
-                                        B.d_act, (int)B.act_host.size(), B.d_crange,
-                                        B.d_slot_part, B.d_gamma_d, B.d_eval, B.d_tickets);
-  if ((e = cudaGetLastError())) return e;
+  if ((e = launch_pdl(bepi_kernel, dim3(B.nchunks), dim3(256), 0, s, (const RowChunk*)B.d_rc,
+                      B.nchunks, (const SlotDesc*)B.d_slots, grad, solver, B.d_cpart,
+                      (const int32_t*)B.d_act, (int)B.act_host.size(), (const int2*)B.d_crange,
+                      B.d_slot_part, (const double*)B.d_gamma_d, B.d_eval, B.d_tickets)))
+    return e;
   if (ev && (e = cudaEventRecord(ev[3], s))) return e;
   return cudaSuccess;
 }

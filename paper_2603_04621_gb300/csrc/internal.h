@@ -32,6 +32,11 @@ constexpr int kTileEdges = DUALIP_TILE_EDGES;       // edge capacity of a stage
 constexpr int kTileSources = DUALIP_TILE_SOURCES;   // source capacity of a stage
 constexpr int kStages = DUALIP_STAGES;               // depth of the staging ring
 constexpr int kConsumerWarps = DUALIP_CONSUMER_WARPS;  // warps that project sources
+// Programmatic dependent launch of the pass after the prologue and of the
+// epilogue after the pass (1), or plain stream order (0).
+#ifndef DUALIP_PDL
+#define DUALIP_PDL 1
+#endif
 #ifndef DUALIP_SMEM_RED64
 #define DUALIP_SMEM_RED64 0
 #endif
@@ -207,6 +212,25 @@ cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, f
 // solve.cu: D_j = (sum_{e->j} a_e^2 / w_e)^(-1/2) (1 for an empty row), or 1
 // everywhere without row normalisation, in renumbered order.  Synchronises s.
 cudaError_t compute_row_scale(const Problem& P, int row_normalize, float* D, cudaStream_t s);
+// Launch with programmatic stream serialisation: the kernel may start before
+// the preceding kernel of the stream has finished and must call
+// griddepcontrol.wait before it reads what that kernel writes.
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*k)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = DUALIP_PDL;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
+}
+
 // Batched pass over the joint tile list (ntiles entries) with the given grid.
 cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, int64_t ntiles,
                               const SlotDesc* slots, const float* gamma_of, double* slot_part,

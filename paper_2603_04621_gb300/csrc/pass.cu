@@ -172,6 +172,16 @@ __device__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort,
   }
 }
 
+// Programmatic dependent launch.  wait: the preceding kernel of the stream
+// has finished and its writes are visible (immediate without the launch
+// attribute).  trigger: the next kernel may start launching; every kernel of
+// the chain triggers only after its own wait, so a kernel that starts early
+// may rely on everything launched two kernels before it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------- FP32 helpers ----
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -973,6 +983,8 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     // ------------------------------------------------------ consumers ----
     // The mu cache and the shared bins, while the producer already streams;
     // the consumer warps then meet (the producer does not take part).
+    pdl_wait();  // mu (and every per-evaluation input) comes from the prologue
+    pdl_trigger();
     if (!BATCH) {
       for (int j = tid - 32; j < p.h_mu; j += kConsumerWarps * 32) mu_s[j] = p.mu_r[j];
       for (int j = tid - 32; j < p.h_y; j += kConsumerWarps * 32) y_s[j] = 0ull;
@@ -1157,6 +1169,8 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
 __global__ void prep_mu_kernel(int32_t J, const float* __restrict__ lambda,
                                const float* __restrict__ D, const int32_t* __restrict__ orig_of,
                                float* __restrict__ mu_r) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t jr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; jr < J;
        jr += (int64_t)gridDim.x * blockDim.x) {
     const int jo = orig_of ? orig_of[jr] : (int)jr;
@@ -1170,6 +1184,8 @@ __global__ void epilogue_kernel(EpiParams q) {
   __shared__ float4 fin[2][32];
   __shared__ bool last;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  pdl_wait();  // A x and the partials of the pass
+  pdl_trigger();
   EpiAcc r;
   epi_rows(q, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, r);
   warp_pair_sum(r.mh, r.ml);
@@ -1368,7 +1384,9 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
   const bool mu_all = P.J <= P.h_mu;
   const size_t smem = pass_smem_bytes(P.storage);
   const dim3 grid(P.grid), block(kThreads);
-#define DUALIP_LAUNCH(B, W, M, X) dualgrad_pass_kernel<B, W, M, X, false><<<grid, block, smem, s>>>(p)
+  cudaError_t e = cudaSuccess;
+#define DUALIP_LAUNCH(B, W, M, X) \
+  e = launch_pdl(dualgrad_pass_kernel<B, W, M, X, false>, grid, block, smem, s, p)
   if (x_out) {
     if (bf16) {
       if (P.weighted) DUALIP_LAUNCH(true, true, false, true);
@@ -1395,7 +1413,7 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
     }
   }
 #undef DUALIP_LAUNCH
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, int64_t ntiles,
@@ -1412,14 +1430,13 @@ cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, in
   const bool bf16 = storage == DUALIP_EDGE_BF16;
   const size_t smem = pass_smem_bytes(storage);
   const int g = (int)(ntiles < grid ? ntiles : grid);
+  const dim3 gd(g), bd(kThreads);
   if (bf16) {
-    if (weighted) dualgrad_pass_kernel<true, true, false, false, true><<<g, kThreads, smem, s>>>(p);
-    else dualgrad_pass_kernel<true, false, false, false, true><<<g, kThreads, smem, s>>>(p);
-  } else {
-    if (weighted) dualgrad_pass_kernel<false, true, false, false, true><<<g, kThreads, smem, s>>>(p);
-    else dualgrad_pass_kernel<false, false, false, false, true><<<g, kThreads, smem, s>>>(p);
+    if (weighted) return launch_pdl(dualgrad_pass_kernel<true, true, false, false, true>, gd, bd, smem, s, p);
+    return launch_pdl(dualgrad_pass_kernel<true, false, false, false, true>, gd, bd, smem, s, p);
   }
-  return cudaGetLastError();
+  if (weighted) return launch_pdl(dualgrad_pass_kernel<false, true, false, false, true>, gd, bd, smem, s, p);
+  return launch_pdl(dualgrad_pass_kernel<false, false, false, false, true>, gd, bd, smem, s, p);
 }
 
 cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const float* gamma_dev,
@@ -1440,8 +1457,7 @@ cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const
   q.gamma = gamma;
   q.eval_out = eval_out;
   q.status = P.status;
-  epilogue_kernel<<<P.epi_blocks, 256, 0, s>>>(q);
-  return cudaGetLastError();
+  return launch_pdl(epilogue_kernel, dim3(P.epi_blocks), dim3(256), 0, s, q);
 }
 
 cudaError_t launch_histogram(const int32_t* dst, int64_t E, int32_t J, unsigned* counts,
