@@ -973,8 +973,8 @@ dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* res
   // candidates: a shape is dropped when most of its tiles would hold a single
   // source (p99 degree above half the edge budget) or when its source cap
   // would stop tiles at under a quarter of the edge budget
-  const int32_t cand[][2] = {{3072, 256}, {3072, 128}, {2048, 256}, {2048, 128},
-                             {1536, 128}, {1024, 128}, {1024, 64},  {512, 64}};
+  const int32_t cand[][2] = {{kTileEdges, 256}, {kTileEdges, 128}, {2048, 256}, {2048, 128},
+                             {1536, 128}, {1024, 128}, {1024, 64},   {512, 64}};
   std::vector<int> keep;
   for (int c = 0; c < 8; ++c) {
     const double e = cand[c][0], src = cand[c][1];

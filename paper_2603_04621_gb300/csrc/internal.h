@@ -14,7 +14,7 @@ namespace dualip {
 // ---- pass geometry --------------------------------------------------------
 // A tile is a run of whole sources whose edges fit one shared-memory stage.
 #ifndef DUALIP_TILE_EDGES
-#define DUALIP_TILE_EDGES 3072
+#define DUALIP_TILE_EDGES 3200
 #endif
 #ifndef DUALIP_STAGES
 #define DUALIP_STAGES 4
@@ -23,7 +23,7 @@ namespace dualip {
 #define DUALIP_CONSUMER_WARPS 18
 #endif
 #ifndef DUALIP_PRIV_DESTS
-#define DUALIP_PRIV_DESTS 2048
+#define DUALIP_PRIV_DESTS 1024
 #endif
 constexpr int kTileEdges = DUALIP_TILE_EDGES;       // edge capacity of a stage
 #ifndef DUALIP_TILE_SOURCES
@@ -32,6 +32,10 @@ constexpr int kTileEdges = DUALIP_TILE_EDGES;       // edge capacity of a stage
 constexpr int kTileSources = DUALIP_TILE_SOURCES;   // source capacity of a stage
 constexpr int kStages = DUALIP_STAGES;               // depth of the staging ring
 constexpr int kConsumerWarps = DUALIP_CONSUMER_WARPS;  // warps that project sources
+// Tiles per grab of the single-problem pass's dynamic schedule (<= 31).
+#ifndef DUALIP_GRAB
+#define DUALIP_GRAB 4
+#endif
 // Programmatic dependent launch of the pass after the prologue and of the
 // epilogue after the pass (1), or plain stream order (0).
 #ifndef DUALIP_PDL

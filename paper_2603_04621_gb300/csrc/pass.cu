@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       // Dynamic tile grabs of kGrab tiles from a counter shared by all CTAs
       // (balanced ends); the next grab is requested while this one is
       // staged.  The end marker stops the consumers.
-      constexpr int kGrab = 4;
+      constexpr int kGrab = DUALIP_GRAB;
       unsigned long long* next = &p.status->tile_next;
       long long nxt = 0;
       if (lane == 0) nxt = (long long)atomicAdd(next, (unsigned long long)kGrab);
