@@ -59,6 +59,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """The largest value of x over the ranks (gloo; every rank gets it)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, steps: int, ws: int, seconds: float) -> float:
+    """Units of every rank (independent replicas) per second of the slowest rank."""
+    return units_per_rank * steps * ws / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -551,10 +568,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         prof = d.dualip_profile_collect(P.h)
         d.dualip_check_device_status(P.h, sp)
+        ms = max_over_ranks(ms, ws)
         if ws > 1:
-            t = torch.tensor([ms], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         # end to end through the public API with host buffers (pinned)
         lam_pin = torch.from_numpy(lam_h).pin_memory()
@@ -565,10 +580,7 @@ def run_ours(args):
         for _ in range(args.steps):
             d.dualip_dual_grad_host(P.h, lam_pin.data_ptr(), GAMMA, grad_pin.data_ptr(), sp)
         e2e_s = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, ws)
     ttg = None
     if not args.no_solve and rank == 0 and args.scale == 1.0:
         P.close()
@@ -579,7 +591,7 @@ def run_ours(args):
         return 0
 
     E = inst.E
-    value = E * args.steps * ws / (ms / 1e3)
+    value = whole_job_rate(E, args.steps, ws, ms / 1e3)
     pass_ms = prof["ms_pass"] / max(prof["count"], 1)
     alg = algorithmic_bytes(inst, args.storage)
     peaks = {}
@@ -604,7 +616,7 @@ def run_ours(args):
         "kernel_ms": {"prologue": prof["ms_prologue"] / max(prof["count"], 1), "pass": pass_ms,
                       "epilogue": prof["ms_epilogue"] / max(prof["count"], 1)},
         "hbm_roofline_pct": 100.0 * achieved / peak,
-        "e2e": {"value": E * args.steps * ws / e2e_s, "unit": UNIT,
+        "e2e": {"value": whole_job_rate(E, args.steps, ws, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * inst.J, "d2h_bytes_per_step": 4 * inst.J + 40,
                 "api": "dualip_dual_grad_host (lambda in, grad + FP64 scalars out, pinned)"},
         "clocks": clk.summary(),
