@@ -43,7 +43,8 @@ typedef enum {
   DUALIP_ETIMEOUT = 4,      /* a bounded device-side wait gave up; results are invalid */
   DUALIP_EBUSY = 5,         /* the resource is in use (e.g. serving slots full) */
   DUALIP_ENOTCONVERGED = 6, /* dualip_solve stopped at max_iters before the tolerances */
-  DUALIP_EDEVICE = 7        /* a device-side consistency check failed */
+  DUALIP_EDEVICE = 7,       /* a device-side consistency check failed */
+  DUALIP_ECANCELED = 8      /* a serving request was cancelled */
 } dualip_status;
 
 typedef enum { DUALIP_EDGE_F32 = 0, DUALIP_EDGE_BF16 = 1 } dualip_edge_dtype;
@@ -369,8 +370,22 @@ dualip_status dualip_server_poll(dualip_server* s, int64_t ticket, dualip_reques
 dualip_status dualip_server_wait(dualip_server* s, int64_t ticket, double timeout_s,
                                  dualip_request_info* info, float* lambda_out);
 dualip_status dualip_server_get_stats(dualip_server* s, dualip_server_stats* stats);
+/* Cancels a request: a queued one leaves the queue at once, an admitted one
+ * leaves at the next chunk boundary; it ends FAILED with DUALIP_ECANCELED
+ * and no lambda.  A request already DONE or FAILED is left as it is. */
+dualip_status dualip_server_cancel(dualip_server* s, int64_t ticket);
 /* Stops the loop; queued and running requests are dropped. */
 void dualip_server_destroy(dualip_server* s);
+
+/*
+ * Fault injection from the host (for tests of the failure path; no device
+ * fault is involved).  Sets, stream-ordered, a flag in the problem's device
+ * status: the next evaluation's pass stops staging tiles and every bounded
+ * device wait gives up at once, as a timed-out wait would, so the call that
+ * reads the status returns DUALIP_ETIMEOUT.  Reading the status clears the
+ * flag; the handle stays usable.
+ */
+dualip_status dualip_debug_abort_waits(dualip_problem* p, void* stream);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* dualip_last_error(void);

@@ -19,9 +19,10 @@ _lib = None
 
 DUALIP_OK, DUALIP_EINVAL, DUALIP_ENOMEM, DUALIP_ECUDA = 0, 1, 2, 3
 DUALIP_ETIMEOUT, DUALIP_EBUSY, DUALIP_ENOTCONVERGED, DUALIP_EDEVICE = 4, 5, 6, 7
+DUALIP_ECANCELED = 8
 DUALIP_EDGE_F32, DUALIP_EDGE_BF16 = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY",
-                6: "ENOTCONVERGED", 7: "EDEVICE"}
+                6: "ENOTCONVERGED", 7: "EDEVICE", 8: "ECANCELED"}
 
 # every entry point declared in include/dualip.h
 EXPORTS = [
@@ -34,7 +35,7 @@ EXPORTS = [
     "dualip_batch_set_tile_shape", "dualip_batch_get_info", "dualip_batch_profile_enable",
     "dualip_batch_profile_collect", "dualip_server_create", "dualip_server_submit",
     "dualip_server_poll", "dualip_server_wait", "dualip_server_get_stats",
-    "dualip_server_destroy",
+    "dualip_server_destroy", "dualip_debug_abort_waits", "dualip_server_cancel",
 ]
 DUALIP_REQ_QUEUED, DUALIP_REQ_RUNNING, DUALIP_REQ_DONE, DUALIP_REQ_FAILED = 0, 1, 2, 3
 
@@ -197,6 +198,10 @@ def lib() -> ctypes.CDLL:
         L.dualip_server_get_stats.restype = st
         L.dualip_server_destroy.argtypes = [vp]
         L.dualip_server_destroy.restype = None
+        L.dualip_server_cancel.argtypes = [vp, i64]
+        L.dualip_server_cancel.restype = st
+        L.dualip_debug_abort_waits.argtypes = [vp, vp]
+        L.dualip_debug_abort_waits.restype = st
         L.dualip_last_error.argtypes = []
         L.dualip_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -409,8 +414,16 @@ def dualip_server_get_stats(srv: int) -> dict:
     return st.as_dict()
 
 
+def dualip_server_cancel(srv: int, ticket: int) -> None:
+    _check(lib().dualip_server_cancel(srv, ticket))
+
+
 def dualip_server_destroy(srv: int) -> None:
     lib().dualip_server_destroy(srv)
+
+
+def dualip_debug_abort_waits(h: int, stream: int) -> None:
+    _check(lib().dualip_debug_abort_waits(h, stream))
 
 
 # ------------------------------------------------- convenience (marshalling) ----
@@ -618,6 +631,9 @@ class Server:
 
     def stats(self) -> dict:
         return dualip_server_get_stats(self.h)
+
+    def cancel(self, ticket: int) -> None:
+        dualip_server_cancel(self.h, ticket)
 
     def close(self):
         if getattr(self, "h", 0):

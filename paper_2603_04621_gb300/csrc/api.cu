@@ -93,10 +93,11 @@ dualip_status read_status(Problem& P, cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(&h, P.status, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
-  if (h.err == 0) return DUALIP_OK;
+  if (h.err == 0 && h.abort_req == 0) return DUALIP_OK;
   DeviceStatus z{};
   cudaMemcpyAsync(P.status, &z, sizeof(z), cudaMemcpyHostToDevice, s);
   cudaStreamSynchronize(s);
+  if (h.err == 0) return DUALIP_OK;  // an abort request that no wait saw
   if (h.err & kErrTimeout)
     return fail(DUALIP_ETIMEOUT, "a bounded device wait gave up (site " + std::to_string(h.where) +
                                      "); results of the call are invalid");
@@ -478,6 +479,16 @@ dualip_status dualip_profile_collect(dualip_problem* h, double* ms_prep, double*
   if (count) *count = P.prof_used;
   free_events(P);
   return DUALIP_OK;
+}
+
+dualip_status dualip_debug_abort_waits(dualip_problem* h, void* stream) {
+  if (!h) return fail(DUALIP_EINVAL, "problem handle is NULL");
+  static const int one = 1;
+  const cudaError_t e =
+      cudaMemcpyAsync(&h->p.status->abort_req, &one, sizeof(int), cudaMemcpyHostToDevice,
+                      as_stream(stream));
+  if (e == cudaSuccess) cudaStreamSynchronize(as_stream(stream));
+  return e ? cuda_fail(e, "setting the abort request") : DUALIP_OK;
 }
 
 dualip_status dualip_check_device_status(dualip_problem* h, void* stream) {

@@ -61,12 +61,15 @@ constexpr int kStageOffSlots = kTileSources + 4;
 constexpr int kErrTimeout = 1;
 constexpr int kErrBounds = 2;
 
-struct DeviceStatus {
+struct alignas(128) DeviceStatus {
   int err;        // OR of kErr* bits
   int where;      // first wait site that timed out
   unsigned ticket;  // last-block counter of the epilogue (reset by the last block)
   unsigned done;    // CTAs of the pass that have finished (reset by the last one)
-  unsigned long long tile_next;  // next tile of the pass's dynamic schedule
+  int abort_req;    // set by the host: device waits give up at once (fault injection)
+  int pad;
+  // the dynamic schedule's counter takes every CTA's atomics: a line of its own
+  alignas(128) unsigned long long tile_next;
 };
 
 // Kernel parameters of the J-length epilogue.

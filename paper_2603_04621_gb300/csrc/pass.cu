@@ -152,8 +152,9 @@ __device__ __forceinline__ uint64_t globaltimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait on an mbarrier phase.  Gives up after kWaitLimitNs or when
-// another thread has raised `abort`, recording the site in the status word.
+// Bounded wait on an mbarrier phase.  Gives up after kWaitLimitNs, when
+// another thread has raised `abort`, or when the host has set abort_req in
+// the status word, recording the site.
 __device__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort,
                            DeviceStatus* st, int site) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -162,7 +163,8 @@ __device__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort,
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63u) == 0) {
       if (*abort) return false;
-      if (globaltimer() - t0 > kWaitLimitNs) {
+      if (*reinterpret_cast<volatile int*>(&st->abort_req) ||
+          globaltimer() - t0 > kWaitLimitNs) {
         *abort = 1;
         atomicOr(&st->err, kErrTimeout);
         atomicCAS(&st->where, 0, site);
@@ -857,7 +859,8 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     const float2* ca2p = p.ca2;
     const uint32_t* cap = p.ca;
     // Lane 0 stages one tile (or, with done, the end marker) into the next
-    // ring slot once every consumer has left the slot's previous tile.
+    // ring slot once every consumer has left the slot's previous tile, and
+    // counts it in `it` (so the drain below waits only for armed stages).
     auto stage = [&](int64_t s0, int64_t s1, int64_t e0, int64_t e1, int slot, bool done) {
       if (lane != 0) return;
       if (BATCH && slot != pslot) {
@@ -891,6 +894,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       si.a0 = e0 & ~int64_t(3);
       si.o0 = s0 & ~int64_t(1);
       info[s] = si;
+      ++it;
       if (bad || si.big) {
         mbar_arrive(&full[s]);
         return;
@@ -911,10 +915,24 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         }
       }
     };
+    // A host-set abort request (fault injection) stops the staging; it is
+    // read once per group of descriptors, next to them.
+    auto injected_abort = [&](int flag) {
+      if (!__any_sync(0xffffffffu, flag != 0)) return false;
+      if (lane == 0) {
+        *abort = 1;
+        atomicOr(&p.status->err, kErrTimeout);
+        atomicCAS(&p.status->where, 0, 6);
+      }
+      stop = true;
+      return true;
+    };
     if (BATCH) {
       // a contiguous range of the joint list (slot switches stay rare)
       for (int64_t t0 = t_begin; t0 < t_end && !stop; t0 += 32) {
         const JointTile jt = p.jt[t0 + lane < t_end ? t0 + lane : t_end - 1];
+        const int ab = lane == 31 ? *reinterpret_cast<volatile int*>(&p.status->abort_req) : 0;
+        if (injected_abort(ab)) break;
         const int cnt = (int)(t_end - t0 < 32 ? t_end - t0 : 32);
         for (int k = 0; k < cnt; ++k) {
           const int64_t s0 = __shfl_sync(0xffffffffu, jt.s0, k);
@@ -923,7 +941,6 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
           const int64_t e1 = __shfl_sync(0xffffffffu, jt.e1, k);
           const int slot = __shfl_sync(0xffffffffu, jt.slot, k);
           stage(s0, s1, e0, e1, slot, false);
-          ++it;
           stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
           if (stop) break;
         }
@@ -944,6 +961,9 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         if (lane == 0) fut = (long long)atomicAdd(next, (unsigned long long)kGrab);
         const int64_t tl = t0 + lane < te ? t0 + lane : te;
         const int64_t my_s = p.tiles[tl], my_e = p.tile_e[tl];
+        // issued after the descriptor loads, so both are in flight together
+        const int ab = lane == 31 ? *reinterpret_cast<volatile int*>(&p.status->abort_req) : 0;
+        if (injected_abort(ab)) break;
         const int cnt = (int)(te - t0);
         for (int k = 0; k < cnt; ++k) {
           const int64_t s0 = __shfl_sync(0xffffffffu, my_s, k);
@@ -951,15 +971,14 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
           const int64_t s1 = __shfl_sync(0xffffffffu, my_s, k + 1);
           const int64_t e1 = __shfl_sync(0xffffffffu, my_e, k + 1);
           stage(s0, s1, e0, e1, 0, false);
-          ++it;
           stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
           if (stop) break;
         }
         nxt = __shfl_sync(0xffffffffu, fut, 0);
       }
       if (!stop) {
-        stage(0, 0, 0, 0, 0, true);
-        ++it;
+        const int ab = lane == 31 ? *reinterpret_cast<volatile int*>(&p.status->abort_req) : 0;
+        if (!injected_abort(ab)) stage(0, 0, 0, 0, 0, true);
       }
     }
     // drain: every armed stage must have landed before the CTA may exit

@@ -40,6 +40,7 @@ struct Request {
   dualip_problem* h = nullptr;  // built, waiting for a slot, or resident
   int kind = 0, slot = -1;
   int32_t iters = 0;
+  bool cancel = false;  // leaves at the next chunk boundary
   dualip_solve_result result{};
   std::vector<float> lam;
 };
@@ -167,21 +168,23 @@ void Server::run_chunks() {
       const int64_t t = slot_ticket[k][s];
       Request* rp;
       int32_t iters;
+      bool cancelled;
       {
         std::lock_guard<std::mutex> lk(mu);
         rp = &reqs[t];
         rp->iters += o.check_every;
         iters = rp->iters;
+        cancelled = rp->cancel;
         slot_iters += o.check_every;
       }
       Request& r = *rp;  // the fields below are written by this thread only
       const SlotSolve& S = B.h_ss[s];
       const bool conv = !st && r.opts.stop_on_tol && S.last_gamma == r.opts.gamma_final &&
                         S.gap_rel <= r.opts.tol_gap && S.infeas_rel <= r.opts.tol_infeas;
-      if (!st && !conv && iters < r.opts.max_iters) continue;
+      if (!st && !cancelled && !conv && iters < r.opts.max_iters) continue;
       // retire: lambda to host, slot and memory back
       std::vector<float> lam;
-      dualip_status rst = st;
+      dualip_status rst = st ? st : (cancelled ? DUALIP_ECANCELED : DUALIP_OK);
       if (!rst) {
         float* lam_dev = nullptr;
         e = cudaMalloc(&lam_dev, sizeof(float) * std::max<int32_t>(r.desc.num_dests, 1));
@@ -207,7 +210,8 @@ void Server::run_chunks() {
       res.gamma = S.last_gamma;
       batch_detach(B, s);
       dualip_destroy(r.h);
-      const std::string msg = rst ? dualip_last_error() : "";
+      const std::string msg =
+          rst == DUALIP_ECANCELED ? std::string("cancelled") : (rst ? dualip_last_error() : "");
       std::lock_guard<std::mutex> lk(mu);
       r.h = nullptr;
       r.slot = -1;
@@ -248,6 +252,20 @@ void Server::schedule_loop() {
       }
       Request& r = *rp;
       const int k = r.kind;
+      bool cancelled;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        cancelled = r.cancel;
+      }
+      if (cancelled) {
+        dualip_destroy(r.h);
+        std::lock_guard<std::mutex> lk(mu);
+        r.h = nullptr;
+        r.status = DUALIP_ECANCELED;
+        r.error = "cancelled";
+        finish_locked(r, DUALIP_REQ_FAILED);
+        continue;
+      }
       cudaError_t e = cudaSuccess;
       if (!batch_ok[k]) {
         e = batch_alloc(batch[k], o.max_slots, r.desc.storage, r.desc.primal_scaling, num_sms);
@@ -414,6 +432,31 @@ dualip_status dualip_server_get_stats(dualip_server* h, dualip_server_stats* st)
   st->chunks = S.chunks;
   st->slot_iterations = S.slot_iters;
   st->busy_seconds = S.busy;
+  return DUALIP_OK;
+}
+
+dualip_status dualip_server_cancel(dualip_server* h, int64_t ticket) {
+  if (!h) return fail(DUALIP_EINVAL, "server is NULL");
+  Server& S = h->s;
+  std::lock_guard<std::mutex> lk(S.mu);
+  auto it = S.reqs.find(ticket);
+  if (it == S.reqs.end()) return fail(DUALIP_EINVAL, "unknown ticket");
+  Request& r = it->second;
+  if (r.state == DUALIP_REQ_QUEUED) {
+    for (auto q = S.queue.begin(); q != S.queue.end(); ++q)
+      if (*q == ticket) {
+        S.queue.erase(q);
+        break;
+      }
+    r.state = DUALIP_REQ_FAILED;
+    r.status = DUALIP_ECANCELED;
+    r.error = "cancelled";
+    r.t_done = S.now();
+    ++S.n_failed;
+    S.cv.notify_all();
+  } else if (r.state == DUALIP_REQ_RUNNING) {
+    r.cancel = true;
+  }
   return DUALIP_OK;
 }
 
