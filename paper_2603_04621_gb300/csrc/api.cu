@@ -139,6 +139,7 @@ extern "C" {
 const char* dualip_last_error(void) { return g_last_error.c_str(); }
 
 dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_problem** out) {
+  NvtxRange nvtx_("dualip_create");
   if (!out) return fail(DUALIP_EINVAL, "out is NULL");
   *out = nullptr;
   if (!d) return fail(DUALIP_EINVAL, "desc is NULL");
@@ -380,6 +381,7 @@ dualip_status dualip_get_info(const dualip_problem* h, int64_t* I, int32_t* J, i
 
 dualip_status dualip_dual_grad_async(dualip_problem* h, const float* lambda, double gamma,
                                      float* grad, double* out_dev, void* stream) {
+  NvtxRange nvtx_("dualip_dual_grad_async");
   dualip_status st = check_eval_args(h, lambda, gamma, grad);
   if (st) return st;
   if (!out_dev) return fail(DUALIP_EINVAL, "out_dev is NULL");
@@ -391,6 +393,7 @@ dualip_status dualip_dual_grad_async(dualip_problem* h, const float* lambda, dou
 
 dualip_status dualip_dual_grad(dualip_problem* h, const float* lambda, double gamma, float* grad,
                                dualip_eval* out, void* stream) {
+  NvtxRange nvtx_("dualip_dual_grad");
   dualip_status st = check_eval_args(h, lambda, gamma, grad);
   if (st) return st;
   Problem& P = h->p;
@@ -428,6 +431,7 @@ dualip_status dualip_dual_grad_host(dualip_problem* h, const float* lambda_host,
 
 dualip_status dualip_get_primal(dualip_problem* h, const float* lambda, double gamma, float* x,
                                 void* stream) {
+  NvtxRange nvtx_("dualip_get_primal");
   dualip_status st = check_eval_args(h, lambda, gamma, x);
   if (st) return st;
   Problem& P = h->p;

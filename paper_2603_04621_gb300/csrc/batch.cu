@@ -741,6 +741,7 @@ void dualip_batch_destroy(dualip_batch* b) {
 dualip_status dualip_batch_dual_grad_async(dualip_batch* b, const float* lambda,
                                            const double* gammas, float* grad, double* out_dev,
                                            void* stream) {
+  NvtxRange nvtx_("dualip_batch_dual_grad");
   if (!b || !lambda || !gammas || !grad) return fail(DUALIP_EINVAL, "NULL argument");
   Batch& B = b->b;
   cudaStream_t s = as_stream(stream);
@@ -814,6 +815,7 @@ dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* 
 dualip_status dualip_batch_solve(dualip_batch* b, const dualip_solve_opts* opts, int32_t n_opts,
                                  float* lambda_inout, dualip_solve_result* results,
                                  void* stream) {
+  NvtxRange nvtx_("dualip_batch_solve");
   if (!b || !opts || !lambda_inout) return fail(DUALIP_EINVAL, "NULL argument");
   Batch& B = b->b;
   if (n_opts != 1 && n_opts != B.n) return fail(DUALIP_EINVAL, "n_opts must be 1 or n");
@@ -942,6 +944,7 @@ dualip_status dualip_batch_solve(dualip_batch* b, const dualip_solve_opts* opts,
 
 dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* result,
                                     void* stream) {
+  NvtxRange nvtx_("dualip_batch_autotune");
   if (!b) return fail(DUALIP_EINVAL, "batch is NULL");
   Batch& B = b->b;
   cudaStream_t s = as_stream(stream);

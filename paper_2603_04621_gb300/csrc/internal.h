@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/dualip.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace dualip {
 
@@ -265,6 +266,15 @@ void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
                  std::vector<int64_t>& tile_e, int64_t max_edges = kTileEdges,
                  int64_t max_sources = kTileSources);
 cudaStream_t as_stream(void* s);
+// NVTX range for the lifetime of a scope (shown by profilers; nothing
+// happens without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 void set_error(const std::string& msg);
 dualip_status fail(dualip_status st, const std::string& msg);
 dualip_status cuda_fail(cudaError_t e, const char* what);

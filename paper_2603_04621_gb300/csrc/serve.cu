@@ -150,6 +150,7 @@ void Server::admit_loop() {
 
 // One chunk of every non-empty batch, then the stopping tests.
 void Server::run_chunks() {
+  NvtxRange nvtx_("serve_chunk");
   for (int k = 0; k < kKinds; ++k) {
     Batch& B = batch[k];
     if (!batch_ok[k]) continue;

@@ -371,6 +371,7 @@ void dualip_solve_opts_default(dualip_solve_opts* o) {
 
 dualip_status dualip_solve(dualip_problem* h, const dualip_solve_opts* o, float* lambda_io,
                            dualip_solve_result* res, double* trace, void* stream) {
+  NvtxRange nvtx_("dualip_solve");
   if (!h || !o || !lambda_io) return fail(DUALIP_EINVAL, "handle, opts and lambda must be non-NULL");
   if (!(o->gamma0 > 0) || !(o->gamma_final > 0) || !std::isfinite(o->gamma0) ||
       o->gamma_final > o->gamma0 || o->gamma_final < 1e-30)
