@@ -284,14 +284,18 @@ dualip_status dualip_batch_solve(dualip_batch* b, const dualip_solve_opts* opts,
 
 /* Tile shape autotuner: candidate (edges, sources) shapes are pruned by the
  * degree (segment length) histogram of the batch, each survivor is timed
- * over a few passes, and the fastest is kept. */
+ * over a few evaluations, and the fastest is kept; then the lean-window
+ * policy (4-lane groups taking spans up to 64 or up to 80) is timed on it. */
 typedef struct {
   int32_t n_candidates;
   int32_t chosen;              /* index of the shape kept */
   int32_t tile_edges[8];
   int32_t tile_sources[8];
-  double ms[8];                /* mean pass time of each candidate */
+  double ms[8];                /* mean evaluation time of each candidate shape */
   int64_t degree_hist[32];     /* sources with degree in [2^k, 2^(k+1)) (k = 0: 0 or 1) */
+  int32_t lean80;              /* 1: 4-lane windows of up to 80 edges were kept (else 64) */
+  int32_t pad;
+  double ms_lean80;            /* the chosen shape timed with 80-edge windows */
 } dualip_autotune_result;
 dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* result, void* stream);
 /* Kernel timing of the next max_evals batched evaluations, as for a problem

@@ -49,13 +49,15 @@ class DualipError(RuntimeError):
 class AutotuneResult(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int32), ("chosen", ctypes.c_int32),
                 ("tile_edges", ctypes.c_int32 * 8), ("tile_sources", ctypes.c_int32 * 8),
-                ("ms", ctypes.c_double * 8), ("degree_hist", ctypes.c_int64 * 32)]
+                ("ms", ctypes.c_double * 8), ("degree_hist", ctypes.c_int64 * 32),
+                ("lean80", ctypes.c_int32), ("pad", ctypes.c_int32), ("ms_lean80", ctypes.c_double)]
 
     def as_dict(self):
         n = self.n_candidates
         return dict(n_candidates=n, chosen=self.chosen, tile_edges=list(self.tile_edges[:n]),
                     tile_sources=list(self.tile_sources[:n]), ms=list(self.ms[:n]),
-                    degree_hist=list(self.degree_hist))
+                    degree_hist=list(self.degree_hist), lean80=self.lean80,
+                    ms_lean80=self.ms_lean80)
 
 
 class ServerOpts(ctypes.Structure):

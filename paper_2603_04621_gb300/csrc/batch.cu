@@ -365,6 +365,16 @@ cudaError_t rebuild_lists(Batch& B) {
   }
   B.ntiles = (int64_t)B.jt_host.size();
   B.nchunks = (int)B.rc_host.size();
+  if (B.lean_auto) {
+    // 80-edge lean windows pay off when few sources need an 8-lane pass
+    int64_t over = 0, all = 0;
+    for (int s = 0; s < B.n; ++s)
+      if (B.active[s]) {
+        over += B.over76[s];
+        all += B.prob[s]->I;
+      }
+    B.lean80 = over * 50 < all ? 1 : 0;
+  }
   cudaError_t e;
   // the lists may still be read by queued work, here or on a caller's stream
   cudaStreamSynchronize(B.stream);
@@ -415,7 +425,7 @@ cudaError_t enqueue_batch_eval(Batch& B, const float* lam, float* grad, int solv
   if ((e = cudaGetLastError())) return e;
   if (ev && (e = cudaEventRecord(ev[1], s))) return e;
   if ((e = launch_pass_batch(B.storage, B.weighted, B.d_jt, B.ntiles, B.d_slots, B.d_gamma_f,
-                             B.d_slot_part, B.d_status, B.grid, s)))
+                             B.d_slot_part, B.d_status, B.grid, B.lean80, s)))
     return e;
   if (ev && (e = cudaEventRecord(ev[2], s))) return e;
   if ((e = launch_pdl(bepi_kernel, dim3(B.nchunks), dim3(256), 0, s, (const RowChunk*)B.d_rc,
@@ -486,6 +496,7 @@ cudaError_t batch_alloc(Batch& B, int capacity, int storage, int weighted, int n
   B.active.assign(n, 0);
   B.vecs.assign(n, nullptr);
   B.tiles.assign(n, {});
+  B.over76.assign(n, 0);
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&B.stream, cudaStreamNonBlocking)) ||
       (e = cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming)) ||
@@ -586,6 +597,10 @@ int batch_attach(Batch& B, Problem* P, const dualip_solve_opts& o, cudaError_t* 
   d.D = v + 5 * (size_t)J;
   B.desc[s] = d;
   slot_tiles(*P, s, B.tile_edges, B.tile_sources, B.tiles[s]);
+  int64_t over = 0;
+  for (size_t i = 0; i + 1 < P->off_host.size(); ++i)
+    over += P->off_host[i + 1] - P->off_host[i] > 76 ? 1 : 0;
+  B.over76[s] = over;
   B.h_ss[s] = slot_solve_init(o, P->bnorm);
   if ((e = compute_row_scale(*P, o.row_normalize ? 1 : 0, d.D, B.stream)) ||
       (e = upload_slots(B)) ||
@@ -998,34 +1013,47 @@ dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* res
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!st && ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))))
     st = cuda_fail(e, "creating events");
+  // mean time of 3 evaluations (after one more) with the current shape and policy
+  auto time_evals = [&](double* out_ms) -> dualip_status {
+    dualip_status t = ensure_all_active(B);
+    const int reps = 3;
+    for (int w = 0; w < 1 + reps && !t; ++w) {
+      if (w == 1 && (e = cudaEventRecord(e0, s))) t = cuda_fail(e, "timing");
+      if (!t) t = dualip_batch_dual_grad_async(b, bufs[0], gam.data(), bufs[1], nullptr, s);
+    }
+    float ms = 0.f;
+    if (!t && ((e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) ||
+               (e = cudaEventElapsedTime(&ms, e0, e1))))
+      t = cuda_fail(e, "timing");
+    *out_ms = ms / reps;
+    return t;
+  };
   double best = 1e300;
   int best_c = keep.empty() ? 0 : keep[0];
+  B.lean80 = 0;
   for (size_t q = 0; q < keep.size() && !st; ++q) {
     const int c = keep[q];
     if ((st = dualip_batch_set_tile_shape(b, cand[c][0], cand[c][1]))) break;
-    if ((st = ensure_all_active(B))) break;
-    const int reps = 3;
-    float ms = 0.f;
-    for (int w = 0; w < 1 + reps && !st; ++w) {
-      if (w == 1 && (e = cudaEventRecord(e0, s))) st = cuda_fail(e, "timing");
-      if (!st) st = dualip_batch_dual_grad_async(b, bufs[0], gam.data(), bufs[1], nullptr, s);
-    }
-    if (st) break;
-    if ((e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) ||
-        (e = cudaEventElapsedTime(&ms, e0, e1))) {
-      st = cuda_fail(e, "timing");
-      break;
-    }
+    double ms = 0.0;
+    if ((st = time_evals(&ms))) break;
     const int slot = (int)q;
     r.tile_edges[slot] = cand[c][0];
     r.tile_sources[slot] = cand[c][1];
-    r.ms[slot] = ms / reps;
+    r.ms[slot] = ms;
     r.n_candidates = slot + 1;
-    if (ms / reps < best) {
-      best = ms / reps;
+    if (ms < best) {
+      best = ms;
       best_c = c;
       r.chosen = slot;
     }
+  }
+  // the lean-window policy, on the chosen shape: 4-lane windows of up to 80
+  // slots pay off when few batches need an 8-lane pass anyway
+  if (!st && !keep.empty() && !(st = dualip_batch_set_tile_shape(b, cand[best_c][0], cand[best_c][1]))) {
+    B.lean80 = 1;
+    st = time_evals(&r.ms_lean80);
+    r.lean80 = r.ms_lean80 < best ? 1 : 0;
+    B.lean80 = r.lean80;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

@@ -20,6 +20,9 @@ struct Batch {
   std::vector<SlotDesc> desc;     // host copy of the slot table
   std::vector<char> active;       // slots in the joint lists
   int64_t tile_edges = kTileEdges, tile_sources = kTileSources;
+  int lean80 = 0;  // lean-window policy of the pass (the autotuner may change it)
+  bool lean_auto = false;  // pick lean80 from the degrees of the active slots
+  std::vector<int64_t> over76;  // per slot: sources with more than 76 edges
   // per-slot tile lists for the current tile shape (host), and their joint
   // concatenation for the active slots (device)
   std::vector<std::vector<JointTile>> tiles;

@@ -1102,26 +1102,23 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
           if (WRITE_X) {
             needm = __ballot_sync(0xffffffffu, dq > 0);
           } else {
-            // 4-lane groups take spans up to 80 in one pass, with the window
-            // (runs of 4 edges per lane) sized by the batch's largest span
-            const bool in4 = dq > 0 && spq <= 80;
+            // 4-lane groups take spans up to 64 (window 64 slots), or with
+            // lean80 up to 80 in one pass (a window of 64 or 80 slots, by the
+            // batch's largest span) unless the batch needs an 8-lane pass
+            // anyway: then spans over 64 join that pass
+            const bool over80 = !p.lean80 || __any_sync(0xffffffffu, spq > 80 && spq <= 128);
+            const int span4 = over80 ? 64 : 80;
+            const bool in4 = dq > 0 && spq <= span4;
             const unsigned m4 = __ballot_sync(0xffffffffu, in4);
-            const unsigned m128 = __ballot_sync(0xffffffffu, spq > 80 && spq <= 128);
+            const unsigned m128 = __ballot_sync(0xffffffffu, spq > span4 && spq <= 128);
             const unsigned m256 = __ballot_sync(0xffffffffu, spq > 128 && spq <= 256);
             const unsigned m512 = __ballot_sync(0xffffffffu, spq > 256 && spq <= 512);
             needm = __ballot_sync(0xffffffffu, spq > 512);
             if (m4) {
-              const unsigned w4 = __reduce_max_sync(0xffffffffu, in4 ? (unsigned)spq : 0u);
-              if (w4 <= 16)
-                needm |= lean_over<4, 1, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
-              else if (w4 <= 32)
-                needm |= lean_over<4, 2, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
-              else if (w4 <= 48)
-                needm |= lean_over<4, 3, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
-              else if (w4 <= 64)
-                needm |= lean_over<4, 4, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
-              else
+              if (p.lean80 && __any_sync(0xffffffffu, in4 && spq > 64))
                 needm |= lean_over<4, 5, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
+              else
+                needm |= lean_over<4, 4, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
             }
             if (m128) needm |= lean_over<8, 4, BF16, W, MU_SMEM, BATCH>(sv, m128, bq, dq, lane, cx, acc);
             if (m256) needm |= lean_over<16, 4, BF16, W, MU_SMEM, BATCH>(sv, m256, bq, dq, lane, cx, acc);
@@ -1386,6 +1383,7 @@ static PassParams pass_params(const Problem& P, const float* gamma_dev, float ga
   p.slots = nullptr;
   p.gamma_of = nullptr;
   p.slot_part = nullptr;
+  p.lean80 = 1;
   return p;
 }
 
@@ -1437,9 +1435,10 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
 
 cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, int64_t ntiles,
                               const SlotDesc* slots, const float* gamma_of, double* slot_part,
-                              DeviceStatus* status, int grid, cudaStream_t s) {
+                              DeviceStatus* status, int grid, int lean80, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   PassParams p{};
+  p.lean80 = lean80;
   p.ntiles = ntiles;
   p.jt = jt;
   p.slots = slots;

@@ -270,6 +270,7 @@ void Server::schedule_loop() {
       cudaError_t e = cudaSuccess;
       if (!batch_ok[k]) {
         e = batch_alloc(batch[k], o.max_slots, r.desc.storage, r.desc.primal_scaling, num_sms);
+        batch[k].lean_auto = true;
         batch_ok[k] = e == cudaSuccess;
         slot_ticket[k].assign(o.max_slots, 0);
       }
