@@ -1,0 +1,91 @@
+"""The seeded input generators (shared by both sides; no arithmetic of the
+method): they follow the stated laws, are reproducible and independent of the
+thread count, and the sub-instance helper picks exactly the chosen sources."""
+import numpy as np
+import pytest
+
+import synth
+
+
+def test_independent_of_thread_count():
+    a = synth.config("c2", scale=0.005)
+    lib = synth._load()
+    old = lib.synth_set_threads(1)
+    try:
+        b = synth.config("c2", scale=0.005)
+    finally:
+        lib.synth_set_threads(max(old, 1))
+    for x, y in ((a.off, b.off), (a.dst, b.dst), (a.c, b.c), (a.a, b.a), (a.b, b.b)):
+        assert np.array_equal(x, y)
+
+
+def test_c2_degree_law_is_poisson_50():
+    inst = synth.config("c2", scale=0.05)
+    deg = np.diff(inst.off).astype(np.float64)
+    assert abs(deg.mean() - 50.0) < 0.3          # Poisson(50): mean 50
+    assert abs(deg.var() / 50.0 - 1.0) < 0.05    # and variance 50 (clipping is negligible)
+    assert deg.min() >= 1 and deg.max() <= 500
+
+
+def test_c2_zipf_hot_destination():
+    inst = synth.config("c2", scale=0.01)
+    counts = np.bincount(inst.dst, minlength=inst.J)
+    # p1 = 1 / H_1.1(10k) ~ 0.151 per draw: with 50 distinct draws nearly every
+    # source reaches the top destination once
+    assert counts.max() >= 0.99 * inst.I
+    assert counts.max() <= inst.I  # distinct destinations per source
+    # ids carry no hotness order (ranks go through a seeded permutation)
+    assert np.argmax(counts) != 0
+
+
+def test_c1_recipe():
+    inst = synth.config("c1")
+    assert inst.I == 1000 and inst.J == 50 and inst.E == 10_000
+    assert np.all(np.diff(inst.off) == 10)
+    assert np.all((inst.c <= 0) & (inst.c >= -1))
+    cnt = np.bincount(inst.dst, minlength=50)
+    assert cnt.min() > 120 and cnt.max() < 280  # uniform: 200 expected per destination
+    bsum = np.bincount(inst.dst, weights=inst.a.astype(np.float64), minlength=50)
+    assert np.allclose(inst.b, (0.3 * bsum).astype(np.float32), rtol=1e-6)
+
+
+def test_greedy_budgets_follow_the_rule():
+    inst = synth.config("c2", scale=0.002)
+    g = synth.greedy_budgets(inst)
+    # greedy load: every source puts its unit on its largest-a edge
+    load = np.zeros(inst.J)
+    for i in range(inst.I):
+        s, e = inst.off[i], inst.off[i + 1]
+        k = s + int(np.argmax(inst.a[s:e]))
+        load[inst.dst[k]] += inst.a[k]
+    rho = g.b.astype(np.float64) / (load + 0.01)
+    assert np.all(rho >= 0.5 - 1e-5) and np.all(rho <= 1.0 + 1e-5)
+    assert np.array_equal(g.dst, inst.dst)  # the same graph and values
+
+
+def test_batch_and_trace_shapes():
+    shapes = synth.batch_shapes(256)
+    I = np.array([s[0] for s in shapes])
+    J = np.array([s[1] for s in shapes])
+    assert len(shapes) == 256 and I.min() >= 1_000 and I.max() <= 2_000_000
+    assert J.min() >= 10 and J.max() <= 50_000
+    assert len({s[2] for s in shapes}) == 256  # distinct per-instance seeds
+    tr = synth.request_trace(400)
+    t = np.array([r["t"] for r in tr])
+    assert np.all(np.diff(t) >= 0) and t[0] == 0.0
+    assert 400 / t[-1] == pytest.approx(20.0, rel=0.15)  # Poisson arrivals at 20/s
+    assert 150 < sum(r["storage"] == "bf16" for r in tr) < 250
+
+
+def test_subset_sources_picks_exactly_those_sources():
+    inst = synth.config("c2", scale=0.002)
+    idx = np.array([0, 3, 4, 100, inst.I - 1])
+    sub = inst.subset_sources(idx)
+    ref = [(inst.dst[inst.off[i]:inst.off[i + 1]], inst.c[inst.off[i]:inst.off[i + 1]])
+           for i in idx]
+    assert sub.I == len(idx) and sub.J == inst.J
+    for k, (d, c) in enumerate(ref):
+        assert np.array_equal(sub.dst[sub.off[k]:sub.off[k + 1]], d)
+        assert np.array_equal(sub.c[sub.off[k]:sub.off[k + 1]], c)
+    empty = inst.subset_sources(np.array([], dtype=np.int64))
+    assert empty.I == 0 and empty.E == 0
