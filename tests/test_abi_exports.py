@@ -64,3 +64,27 @@ def test_create_rejects_bad_desc_without_a_gpu(libdualip):
     desc = d.ProblemDesc(2, 1, 3, off.ctypes.data, 1, 1, 1, b.ctypes.data, 0, 0, 0)
     assert lib.dualip_create(ctypes.byref(desc), None, ctypes.byref(h)) == d.DUALIP_EINVAL
     assert b"nondecreasing" in lib.dualip_last_error()
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without libdualip.so the binding raises."""
+    import paper_2603_04621_gb300 as d
+
+    monkeypatch.setattr(d, "_lib", None)
+    monkeypatch.setattr(d, "LIB_PATH", str(tmp_path / "libdualip.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        d.lib()
+
+
+def test_host_argument_checks_of_the_forms(libdualip):
+    """Batch and server entry points reject bad arguments before any CUDA call."""
+    import paper_2603_04621_gb300 as d
+
+    lib = d.lib()
+    out = ctypes.c_void_p()
+    assert lib.dualip_batch_create(0, None, ctypes.byref(out)) == d.DUALIP_EINVAL
+    assert lib.dualip_server_create(None, ctypes.byref(out)) == d.DUALIP_EINVAL
+    bad = d.ServerOpts(0, 4, 10)
+    assert lib.dualip_server_create(ctypes.byref(bad), ctypes.byref(out)) == d.DUALIP_EINVAL
+    bad = d.ServerOpts(1 << 30, 0, 10)
+    assert lib.dualip_server_create(ctypes.byref(bad), ctypes.byref(out)) == d.DUALIP_EINVAL
