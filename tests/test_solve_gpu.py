@@ -113,3 +113,22 @@ def test_warm_start_and_invalid_opts(dl):
         P.solve(gamma0=1e-3, gamma_final=1e-2)
     with pytest.raises(dl.DualipError):
         P.solve(max_iters=0)
+
+
+def test_recurring_solve_warm_starts_on_a_perturbed_instance(dl):
+    """Recurring solves: the costs move by about 1%, and the previous optimum
+    started at the final gamma reaches the 1e-4 gap in fewer iterations than
+    the cold schedule, at the same dual value."""
+    base = synth.greedy_budgets(synth.config("c2"))  # converges in 190 iterations
+    P = dl.Problem.from_instance(base)
+    lam, r = P.solve()
+    assert r["converged"]
+    rng = np.random.default_rng(17)
+    c2 = (base.c * (1.0 + 0.01 * rng.standard_normal(base.E))).astype(np.float32)
+    moved = synth.Instance(base.off, base.dst, c2, base.a, base.b, base.J)
+    Q = dl.Problem.from_instance(moved)
+    _, cold = Q.solve()
+    _, warm = Q.solve(lam0=lam, gamma0=1e-3, gamma_final=1e-3, halve_every=0)
+    assert cold["converged"] and warm["converged"]
+    assert warm["iters"] < cold["iters"]
+    assert abs(warm["dual_obj"] - cold["dual_obj"]) <= 3e-4 * abs(cold["dual_obj"])
