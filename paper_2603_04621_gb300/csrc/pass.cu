@@ -624,7 +624,9 @@ __device__ __forceinline__ void project_multipass(const View& v, int64_t base, i
     v.edge(base + k, j, c, a);
     score(c, a, cx.mu(j), hi, lo);
   };
-  float rmax = -CUDART_INF_F, s0 = 0.f;
+  // one pass: the maximum score, the saturation sum and (weighted) the
+  // maximum of r - gamma w, whose shift by the maximum bounds the active set
+  float rmax = -CUDART_INF_F, s0 = 0.f, mb = -CUDART_INF_F;
   for (int64_t k = g.rank(); k < d; k += g.size()) {
     int j;
     float c, a, hi, lo;
@@ -632,21 +634,19 @@ __device__ __forceinline__ void project_multipass(const View& v, int64_t base, i
     const float rf = __fadd_rn(hi, lo);
     rmax = fmaxf(rmax, rf);
     if (rf > 0.f) s0 += __fmul_rn(edge_alpha<W>(cx, edge_w<W>(a)), rf);
+    if (W) mb = fmaxf(mb, __fsub_rn(rf, __fmul_rn(cx.gamma, edge_w<W>(a))));
   }
   rmax = g.max(rmax);
   s0 = g.sum(s0);
   int mode = rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2);
   float t = 0.f;
   if (mode == 2) {
-    float lb = -CUDART_INF_F;
-    for (int64_t k = g.rank(); k < d; k += g.size()) {
-      int j;
-      float c, a, hi, lo;
-      load(k, j, c, a, hi, lo);
-      const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
-      lb = fmaxf(lb, __fsub_rn(dk, W ? __fmul_rn(cx.gamma, edge_w<W>(a)) : cx.gamma));
-    }
-    lb = g.max(lb);
+    // a lower bound of max_e (d_e - gamma w_e), lowered by the FP32 rounding of
+    // the scores, so that {d_e > lb} contains the active set (unweighted: the
+    // top edge has d = 0, so the bound is -gamma)
+    const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
+    const float lb = W ? __fsub_rn(fminf(__fsub_rn(g.max(mb), rmax), 0.f), slack)
+                       : __fsub_rn(-cx.gamma, slack);
     float theta = lb, nprev = -1.f;
     t = lb;
     for (int64_t it = 0; it <= d; ++it) {
