@@ -73,13 +73,14 @@ __device__ inline bool slot_restart(const SlotSolve& s, int32_t k) {
 
 // ------------------------------------------------- J-length kernels ----
 // Rows of chunk c are rows [r0, r1) of the chunk's slot in renumbered order.
-// API mode: mu_r[jr] = lambda[joff + orig_of[jr]].  Solver mode: the ascent's
-// point y (renumbered) times the row scale, with the momentum restart at a
-// gamma change; the first chunk of a slot publishes the slot's gamma.
+// API mode: mu_r[jr] = lambda[joff + orig_of[jr]].  Solver mode (before a
+// slot's first iteration; later ones get theirs from bstep and bnorms): the
+// ascent's point y (renumbered) times the row scale, with the momentum restart
+// at a gamma change; the first chunk of a slot publishes the slot's gamma.
 __global__ void bprep_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __restrict__ sd,
                              const float* __restrict__ lam, int solver, SlotSolve* ss,
                              float* gamma_f, double* gamma_d) {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the pass may launch
+  pdl_trigger();  // the pass may launch (this kernel itself is a plain launch)
   const RowChunk ch = rc[blockIdx.x];
   const SlotDesc& d = sd[ch.slot];
   if (!solver) {
@@ -114,8 +115,8 @@ __global__ void bepi_kernel(const RowChunk* __restrict__ rc, int nchunks,
                             float4* __restrict__ cpart, const int32_t* __restrict__ act, int nact,
                             const int2* __restrict__ crange, double* slot_part,
                             const double* __restrict__ gamma_d, double* eval, unsigned* ticket) {
-  asm volatile("griddepcontrol.wait;" ::: "memory");  // A x and the partials of the pass
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  pdl_wait();  // A x and the partials of the pass
+  pdl_trigger();
   const RowChunk ch = rc[blockIdx.x];
   const SlotDesc& d = sd[ch.slot];
   float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -188,7 +189,10 @@ __global__ void bnorms_kernel(const RowChunk* __restrict__ rc, int nchunks,
                               const SlotDesc* __restrict__ sd, SlotSolve* ss,
                               float4* __restrict__ cpart, const int32_t* __restrict__ act,
                               int nact, const int2* __restrict__ crange,
-                              const double* __restrict__ eval, unsigned* ticket) {
+                              const double* __restrict__ eval, unsigned* ticket,
+                              float* gamma_f, double* gamma_d) {
+  pdl_wait();  // G and the scalars of the epilogue
+  pdl_trigger();
   const RowChunk ch = rc[blockIdx.x];
   const SlotDesc& d = sd[ch.slot];
   const SlotSolve& st = ss[ch.slot];
@@ -246,6 +250,9 @@ __global__ void bnorms_kernel(const RowChunk* __restrict__ rc, int nchunks,
     S.infeas_rel = o[3] / fmax(1.0, S.bnorm);
     S.last_gamma = gk;
     S.k = k + 1;
+    const double gn = slot_gamma(S, k + 1);  // for the next iteration's pass and scalars
+    gamma_f[s] = (float)gn;
+    gamma_d[s] = (double)(float)gn;
   }
   if (threadIdx.x == 0) *ticket = 0u;
 }
@@ -256,19 +263,27 @@ __global__ void bnorms_kernel(const RowChunk* __restrict__ rc, int nchunks,
 // evaluated point.
 __global__ void bstep_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __restrict__ sd,
                              const SlotSolve* __restrict__ ss) {
+  pdl_wait();  // eta and beta of bnorms
+  pdl_trigger();
   const RowChunk ch = rc[blockIdx.x];
   const SlotDesc& d = sd[ch.slot];
-  const float eta = (float)ss[ch.slot].eta, beta = (float)ss[ch.slot].beta;
+  const SlotSolve& st = ss[ch.slot];
+  const float eta = (float)st.eta, beta = (float)st.beta;
+  // the next iteration's point (bnorms has advanced k): a restart at a gamma
+  // change puts y at lambda; then its mu
+  const bool rs = slot_restart(st, st.k);
   for (int j = ch.r0 + threadIdx.x; j < ch.r1; j += blockDim.x) {
     const float yk = d.yv[j], g = d.G[j], lk = d.lam[j];
     float ln = __fmaf_rn(eta, g, yk);
     ln = ln > 0.f ? ln : 0.f;
     float yn = __fmaf_rn(beta, __fsub_rn(ln, lk), ln);
     yn = yn > 0.f ? yn : 0.f;
+    if (rs) yn = ln;
     d.yp[j] = yk;
     d.Gp[j] = g;
     d.lam[j] = ln;
     d.yv[j] = yn;
+    d.mu_r[j] = __fmul_rn(d.D[j], yn);
   }
 }
 
@@ -420,9 +435,11 @@ cudaError_t enqueue_batch_eval(Batch& B, const float* lam, float* grad, int solv
   cudaEvent_t* ev = nullptr;
   if (!solver && B.prof_used < B.prof_max) ev = &B.prof_ev[4 * (size_t)B.prof_used++];
   if (ev && (e = cudaEventRecord(ev[0], s))) return e;
-  bprep_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.d_slots, lam, solver, B.d_ss, B.d_gamma_f,
-                                         B.d_gamma_d);
-  if ((e = cudaGetLastError())) return e;
+  if (!solver) {  // the solver's mu and gamma come from the previous iteration
+    bprep_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.d_slots, lam, solver, B.d_ss, B.d_gamma_f,
+                                           B.d_gamma_d);
+    if ((e = cudaGetLastError())) return e;
+  }
   if (ev && (e = cudaEventRecord(ev[1], s))) return e;
   if ((e = launch_pass_batch(B.storage, B.weighted, B.d_jt, B.ntiles, B.d_slots, B.d_gamma_f,
                              B.d_slot_part, B.d_status, B.grid, B.lean80, s)))
@@ -441,12 +458,13 @@ cudaError_t enqueue_batch_iteration(Batch& B, cudaStream_t s) {
   cudaError_t e;
   if ((e = enqueue_batch_eval(B, nullptr, nullptr, 1, s))) return e;
   if (B.nchunks == 0) return cudaSuccess;
-  bnorms_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.nchunks, B.d_slots, B.d_ss, B.d_cpart,
-                                          B.d_act, (int)B.act_host.size(), B.d_crange, B.d_eval,
-                                          B.d_tickets + 1);
-  if ((e = cudaGetLastError())) return e;
-  bstep_kernel<<<B.nchunks, 256, 0, s>>>(B.d_rc, B.d_slots, B.d_ss);
-  return cudaGetLastError();
+  if ((e = launch_pdl(bnorms_kernel, dim3(B.nchunks), dim3(256), 0, s, (const RowChunk*)B.d_rc,
+                      B.nchunks, (const SlotDesc*)B.d_slots, B.d_ss, B.d_cpart,
+                      (const int32_t*)B.d_act, (int)B.act_host.size(), (const int2*)B.d_crange,
+                      (const double*)B.d_eval, B.d_tickets + 1, B.d_gamma_f, B.d_gamma_d)))
+    return e;
+  return launch_pdl(bstep_kernel, dim3(B.nchunks), dim3(256), 0, s, (const RowChunk*)B.d_rc,
+                    (const SlotDesc*)B.d_slots, (const SlotSolve*)B.d_ss);
 }
 
 cudaError_t run_batch_chunk(Batch& B, int n, bool use_graph) {
@@ -614,6 +632,8 @@ int batch_attach(Batch& B, Problem* P, const dualip_solve_opts& o, cudaError_t* 
   }
   if (B.nrc2) {
     binit_kernel<<<B.nrc2, 256, 0, B.stream>>>(B.d_rc2, B.d_slots, nullptr);
+    bprep_kernel<<<B.nrc2, 256, 0, B.stream>>>(B.d_rc2, B.d_slots, nullptr, 1, B.d_ss,
+                                               B.d_gamma_f, B.d_gamma_d);
     if ((e = cudaGetLastError()) || (e = cudaStreamSynchronize(B.stream))) {
       *err = e;
       batch_detach(B, s);
@@ -882,6 +902,9 @@ dualip_status dualip_batch_solve(dualip_batch* b, const dualip_solve_opts* opts,
   if (B.nchunks) {
     binit_kernel<<<B.nchunks, 256, 0, B.stream>>>(B.d_rc, B.d_slots, lambda_inout);
     if ((e = cudaGetLastError())) return cuda_fail(e, "initialising lambda");
+    bprep_kernel<<<B.nchunks, 256, 0, B.stream>>>(B.d_rc, B.d_slots, nullptr, 1, B.d_ss,
+                                                  B.d_gamma_f, B.d_gamma_d);
+    if ((e = cudaGetLastError())) return cuda_fail(e, "preparing the first iteration");
   }
   std::vector<int32_t> iters(B.n, 0);
   std::vector<char> conv(B.n, 0);

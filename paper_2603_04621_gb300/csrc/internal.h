@@ -221,6 +221,18 @@ cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, f
 // solve.cu: D_j = (sum_{e->j} a_e^2 / w_e)^(-1/2) (1 for an empty row), or 1
 // everywhere without row normalisation, in renumbered order.  Synchronises s.
 cudaError_t compute_row_scale(const Problem& P, int row_normalize, float* D, cudaStream_t s);
+#ifdef __CUDACC__
+// Programmatic dependent launch.  wait: the preceding kernel of the stream
+// has finished and its writes are visible (immediate without the launch
+// attribute).  trigger: the next kernel may start launching.  Every kernel of
+// a chain triggers only after its own wait, so a kernel that starts early may
+// rely on everything launched two kernels before it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+
 // Launch with programmatic stream serialisation: the kernel may start before
 // the preceding kernel of the stream has finished and must call
 // griddepcontrol.wait before it reads what that kernel writes.

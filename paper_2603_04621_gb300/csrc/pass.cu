@@ -174,16 +174,6 @@ __device__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort,
   }
 }
 
-// Programmatic dependent launch.  wait: the preceding kernel of the stream
-// has finished and its writes are visible (immediate without the launch
-// attribute).  trigger: the next kernel may start launching; every kernel of
-// the chain triggers only after its own wait, so a kernel that starts early
-// may rely on everything launched two kernels before it.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // ------------------------------------------------------- FP32 helpers ----
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -64,6 +64,8 @@ __global__ void solve_init_kernel(int32_t J, const float* __restrict__ lam_in,
   }
 }
 
+// mu and gamma of the first iteration (later iterations get them from the
+// step and norms kernels of the iteration before)
 __global__ void solve_prep_kernel(int32_t J, SolveState* st, Vecs v, float* __restrict__ mu_r) {
   const int32_t k = st->k;
   const bool rs = restart_at(*st, k);
@@ -80,6 +82,8 @@ __global__ void solve_prep_kernel(int32_t J, SolveState* st, Vecs v, float* __re
 }
 
 __global__ void solve_norms_kernel(int32_t J, SolveState* st, Vecs v, double* part) {
+  pdl_wait();  // G and the scalars of the epilogue
+  pdl_trigger();
   const int32_t k = st->k;
   const bool have_prev = k > 0 && !restart_at(*st, k);
   double dy = 0.0, dg = 0.0;
@@ -168,11 +172,18 @@ __global__ void solve_norms_kernel(int32_t J, SolveState* st, Vecs v, double* pa
     tr[7] = st->eval[4];
   }
   st->k = k + 1;
+  st->gamma_f = (float)gamma_at(*st, k + 1);  // read by the next iteration's pass
   st->ticket = 0u;
 }
 
-__global__ void solve_step_kernel(int32_t J, const SolveState* st, Vecs v) {
+// The step, then the next iteration's point: y restarts at lambda when gamma
+// changes there (the norms kernel has already advanced k), and its mu.
+__global__ void solve_step_kernel(int32_t J, const SolveState* st, Vecs v,
+                                  float* __restrict__ mu_r) {
+  pdl_wait();  // eta and beta of the norms kernel
+  pdl_trigger();
   const float eta = (float)st->eta, beta = (float)st->beta;
+  const bool rs = restart_at(*st, st->k);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
        j += (int64_t)gridDim.x * blockDim.x) {
     const float yk = v.y[j], g = v.G[j], lk = v.lam[j];
@@ -180,10 +191,12 @@ __global__ void solve_step_kernel(int32_t J, const SolveState* st, Vecs v) {
     ln = ln > 0.f ? ln : 0.f;
     float yn = __fmaf_rn(beta, __fsub_rn(ln, lk), ln);
     yn = yn > 0.f ? yn : 0.f;
+    if (rs) yn = ln;
     v.yp[j] = yk;
     v.Gp[j] = g;
     v.lam[j] = ln;
     v.y[j] = yn;
+    mu_r[j] = __fmul_rn(v.D[j], yn);
   }
 }
 
@@ -305,14 +318,15 @@ static cudaError_t ensure_row_scale(Problem& P, SolveCtx& C, int row_normalize, 
 static cudaError_t enqueue_iteration(Problem& P, SolveCtx& C, cudaStream_t s) {
   Vecs v{C.lam, C.y, C.yp, C.G, C.Gp, C.D};
   cudaError_t e;
-  solve_prep_kernel<<<C.blocks, 256, 0, s>>>(P.J, C.st, v, P.mu_r);
-  if ((e = cudaGetLastError())) return e;
+  // mu and gamma of this iteration come from the previous one (or the prep
+  // before the first); every kernel waits for its predecessor's writes
   if ((e = launch_pass(P, &C.st->gamma_f, 0.f, nullptr, s))) return e;
   if ((e = launch_epilogue(P, C.D, C.G, &C.st->gamma_f, 0.0, C.st->eval, s, true))) return e;
-  solve_norms_kernel<<<C.blocks, 256, 0, s>>>(P.J, C.st, v, C.part);
-  if ((e = cudaGetLastError())) return e;
-  solve_step_kernel<<<C.blocks, 256, 0, s>>>(P.J, C.st, v);
-  return cudaGetLastError();
+  if ((e = launch_pdl(solve_norms_kernel, dim3(C.blocks), dim3(256), 0, s, P.J, C.st, v,
+                      C.part)))
+    return e;
+  return launch_pdl(solve_step_kernel, dim3(C.blocks), dim3(256), 0, s, P.J,
+                    (const SolveState*)C.st, v, P.mu_r);
 }
 
 static cudaError_t run_chunk(Problem& P, SolveCtx& C, int n, bool use_graph) {
@@ -406,6 +420,8 @@ dualip_status dualip_solve(dualip_problem* h, const dualip_solve_opts* o, float*
   {
     Vecs v{C.lam, C.y, C.yp, C.G, C.Gp, C.D};
     solve_init_kernel<<<C.blocks, 256, 0, C.stream>>>(P.J, lambda_io, P.orig_of, v);
+    if ((e = cudaGetLastError())) return cuda_fail(e, "initialising the solver");
+    solve_prep_kernel<<<C.blocks, 256, 0, C.stream>>>(P.J, C.st, v, P.mu_r);
     if ((e = cudaGetLastError())) return cuda_fail(e, "initialising the solver");
   }
   int done = 0;
