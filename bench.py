@@ -128,8 +128,8 @@ def config_dict(inst, name, scale, storage):
 # sources, with the hash of the kernel source it was taken on.  It is scaled to
 # a launch by the edges processed, and reported only while the kernel's code
 # (the source without comments and blank lines) is unchanged.
-PASS_TRAFFIC = {"bytes": 182_644_736 + 3_997_696, "edges": 14_995_720,
-                "pass_cu_code_sha256": "7efa4445a4b6a32a88b1ff9c17b8fbe0be29f72e41060f0f1973e0759500a70e"}
+PASS_TRAFFIC = {"bytes": 182_637_568 + 3_627_008, "edges": 14_995_720,
+                "pass_cu_code_sha256": "6d3ad623d24d65a321bc0f852863f9c52a8f812ad46938e5d133a6f33c512c47"}
 
 
 def kernel_code_hash():
@@ -286,6 +286,13 @@ def time_to_gap(d, torch, base, name, storage):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     P.close()
+    out = {"workload": f"{name} graph and values with greedy-load budgets (App. B rule)",
+           "storage": storage,
+           "seconds": dt, "iters": res["iters"], "converged": res["converged"],
+           "gap_rel": res["gap_rel"], "infeas_rel": res["infeas_rel"],
+           "dual_obj": res["dual_obj"]}
+    if name != "c2":
+        return out
     # a recurring solve: costs moved by about 1%, started from this optimum at
     # the final gamma
     rng = np.random.default_rng(17)
@@ -301,15 +308,10 @@ def time_to_gap(d, torch, base, name, storage):
     torch.cuda.synchronize()
     wdt = time.perf_counter() - t0
     Q.close()
-    return {"workload": f"{name} graph and values with greedy-load budgets (App. B rule)",
-            "storage": storage,
-            "seconds": dt, "iters": res["iters"], "converged": res["converged"],
-            "gap_rel": res["gap_rel"], "infeas_rel": res["infeas_rel"],
-            "dual_obj": res["dual_obj"],
-            "warm_recurring": {"seconds": wdt, "iters": wres["iters"],
-                               "converged": wres["converged"],
-                               "change": "c * (1 + 0.01 N(0,1)), from the previous optimum "
-                                         "at gamma 1e-3"}}
+    out["warm_recurring"] = {"seconds": wdt, "iters": wres["iters"], "converged": wres["converged"],
+                             "change": "c * (1 + 0.01 N(0,1)), from the previous optimum at "
+                                       "gamma 1e-3"}
+    return out
 
 
 def batch_time_to_gap(d, torch, probs, B):
