@@ -245,16 +245,18 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   const int32_t* dst_raw = d->dst;
   int32_t* dst_tmp = nullptr;
   unsigned* counts = nullptr;
-  if ((e = cudaMalloc(&counts, sizeof(unsigned) * J))) return bail(cuda_fail(e, "allocating"));
+  // temporaries are stream-ordered (cudaMallocAsync / cudaFreeAsync on s): no
+  // device-wide synchronisation, so a build overlaps other streams' kernels
+  if ((e = cudaMallocAsync(&counts, sizeof(unsigned) * J, s)))
+    return bail(cuda_fail(e, "allocating"));
   auto free_tmp = [&]() {
-    cudaStreamSynchronize(s);
-    if (dst_tmp) cudaFree(dst_tmp);
-    if (counts) cudaFree(counts);
+    if (dst_tmp) cudaFreeAsync(dst_tmp, s);
+    if (counts) cudaFreeAsync(counts, s);
     dst_tmp = nullptr;
     counts = nullptr;
   };
   if (!d->inputs_on_device && E > 0) {
-    if ((e = cudaMalloc(&dst_tmp, sizeof(int32_t) * E)) ||
+    if ((e = cudaMallocAsync(&dst_tmp, sizeof(int32_t) * E, s)) ||
         (e = cudaMemcpyAsync(dst_tmp, d->dst, sizeof(int32_t) * E, cudaMemcpyHostToDevice, s))) {
       free_tmp();
       return bail(cuda_fail(e, "uploading dst"));
@@ -306,17 +308,18 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   // edge values
   unsigned absmax[2] = {0u, 0u};  // bit patterns of max |c|, max |a|
   unsigned* counts_max = nullptr;
-  if ((e = cudaMalloc(&counts_max, 2 * sizeof(unsigned)))) return bail(cuda_fail(e, "allocating"));
+  if ((e = cudaMallocAsync(&counts_max, 2 * sizeof(unsigned), s)))
+    return bail(cuda_fail(e, "allocating"));
   if (E > 0) {
     float *c_tmp = nullptr, *a_tmp = nullptr;
     const float *c_src = d->c, *a_src = d->a;
     if (!d->inputs_on_device) {
-      if ((e = cudaMalloc(&c_tmp, 4 * (size_t)E)) || (e = cudaMalloc(&a_tmp, 4 * (size_t)E)) ||
+      if ((e = cudaMallocAsync(&c_tmp, 4 * (size_t)E, s)) ||
+          (e = cudaMallocAsync(&a_tmp, 4 * (size_t)E, s)) ||
           (e = cudaMemcpyAsync(c_tmp, d->c, 4 * (size_t)E, h2d, s)) ||
           (e = cudaMemcpyAsync(a_tmp, d->a, 4 * (size_t)E, h2d, s))) {
-        cudaStreamSynchronize(s);
-        cudaFree(c_tmp);
-        cudaFree(a_tmp);
+        if (c_tmp) cudaFreeAsync(c_tmp, s);
+        if (a_tmp) cudaFreeAsync(a_tmp, s);
         return bail(cuda_fail(e, "uploading c and a"));
       }
       c_src = c_tmp;
@@ -331,17 +334,15 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
                              s)) ||
         (P.storage == DUALIP_EDGE_BF16 && (e = launch_pack_bf16(c_src, a_src, P.ca, E, s))) ||
         (P.storage == DUALIP_EDGE_F32 && (e = launch_pack_f32(c_src, a_src, P.ca2, E, s)))) {
-      cudaStreamSynchronize(s);
-      cudaFree(c_tmp);
-      cudaFree(a_tmp);
+      if (c_tmp) cudaFreeAsync(c_tmp, s);
+      if (a_tmp) cudaFreeAsync(a_tmp, s);
       return bail(cuda_fail(e, "checking edge values"));
     }
-    cudaStreamSynchronize(s);
-    cudaFree(c_tmp);
-    cudaFree(a_tmp);
+    if (c_tmp) cudaFreeAsync(c_tmp, s);
+    if (a_tmp) cudaFreeAsync(a_tmp, s);
   }
+  cudaFreeAsync(counts_max, s);
   e = cudaStreamSynchronize(s);
-  cudaFree(counts_max);
   if (e) return bail(cuda_fail(e, "building the problem"));
   // Fixed-point scale 2^exp_y of A x: |(A x)_j| <= max in-degree * max |a|
   // (x <= 1), kept below 2^61 so no sum can overflow.

@@ -600,7 +600,8 @@ int batch_attach(Batch& B, Problem* P, const dualip_solve_opts& o, cudaError_t* 
   cudaError_t e;
   float* v = nullptr;
   const int32_t J = P->J;
-  if ((e = cudaMalloc(&v, sizeof(float) * 6 * std::max<int32_t>(J, 1)))) {
+  // stream-ordered: no device-wide synchronisation while other work runs
+  if ((e = cudaMallocAsync(&v, sizeof(float) * 6 * std::max<int32_t>(J, 1), B.stream))) {
     *err = e;
     return -1;
   }
@@ -656,8 +657,8 @@ cudaError_t batch_write_lambda(Batch& B, int slot, float* lam_out) {
 }
 
 void batch_detach(Batch& B, int slot) {
+  if (B.vecs[slot]) cudaFreeAsync(B.vecs[slot], B.stream);
   cudaStreamSynchronize(B.stream);
-  if (B.vecs[slot]) cudaFree(B.vecs[slot]);
   B.vecs[slot] = nullptr;
   B.prob[slot] = nullptr;
   B.desc[slot] = SlotDesc{};

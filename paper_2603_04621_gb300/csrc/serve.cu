@@ -187,14 +187,16 @@ void Server::run_chunks() {
       std::vector<float> lam;
       dualip_status rst = st ? st : (cancelled ? DUALIP_ECANCELED : DUALIP_OK);
       if (!rst) {
-        float* lam_dev = nullptr;
-        e = cudaMalloc(&lam_dev, sizeof(float) * std::max<int32_t>(r.desc.num_dests, 1));
+        float* lam_dev = nullptr;  // stream-ordered, like the copy below
+        e = cudaMallocAsync(&lam_dev, sizeof(float) * std::max<int32_t>(r.desc.num_dests, 1),
+                            B.stream);
         if (!e) e = batch_write_lambda(B, s, lam_dev);
         lam.resize(r.desc.num_dests);
         if (!e)
-          e = cudaMemcpy(lam.data(), lam_dev, sizeof(float) * r.desc.num_dests,
-                         cudaMemcpyDeviceToHost);
-        if (lam_dev) cudaFree(lam_dev);
+          e = cudaMemcpyAsync(lam.data(), lam_dev, sizeof(float) * r.desc.num_dests,
+                              cudaMemcpyDeviceToHost, B.stream);
+        if (lam_dev) cudaFreeAsync(lam_dev, B.stream);
+        if (!e) e = cudaStreamSynchronize(B.stream);
         if (e) rst = cuda_fail(e, "reading a finished request's lambda");
       }
       dualip_solve_result res{};
