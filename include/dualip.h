@@ -249,8 +249,9 @@ dualip_status dualip_dual_grad_noalloc(int64_t num_sources, int32_t num_dests,
  */
 typedef struct dualip_batch dualip_batch;
 
-/* n >= 1 problems (host array of handles).  Tiles use the default shape
- * (3200 edges, 256 sources) until dualip_batch_autotune picks another. */
+/* n >= 1 problems (host array of handles).  Tiles use the default shape (the
+ * stage capacity: 3200 edges with FP32 storage, 4800 with BF16; 256 sources)
+ * until dualip_batch_autotune picks another. */
 dualip_status dualip_batch_create(int32_t n, dualip_problem* const* problems,
                                   dualip_batch** out);
 void dualip_batch_destroy(dualip_batch* b);
@@ -303,7 +304,8 @@ dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* res
 dualip_status dualip_batch_profile_enable(dualip_batch* b, int32_t max_evals);
 dualip_status dualip_batch_profile_collect(dualip_batch* b, double* ms_prologue, double* ms_pass,
                                            double* ms_epilogue, int32_t* count);
-/* Explicit tile shape: 1 <= edges <= 3200, 1 <= sources <= 256. */
+/* Explicit tile shape: 1 <= edges <= the stage capacity (3200 edges with
+ * FP32 storage, 4800 with BF16), 1 <= sources <= 256. */
 dualip_status dualip_batch_set_tile_shape(dualip_batch* b, int32_t edges, int32_t sources);
 dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* total_J,
                                     int64_t* total_E, int64_t* ntiles, int32_t* tile_edges,

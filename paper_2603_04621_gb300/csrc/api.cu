@@ -198,7 +198,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   }
 
   std::vector<int64_t> tiles, tile_e;
-  build_tiles(off, tiles, tile_e);
+  build_tiles(off, tiles, tile_e, tile_edges_for(P.storage));
   P.ntiles = (int64_t)tiles.size() - 1;
   P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P.num_sms, P.ntiles));
   P.h_mu = std::min(J, kMaxCachedDests);

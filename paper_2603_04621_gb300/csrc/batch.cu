@@ -505,6 +505,7 @@ dualip_status batch_status(Batch& B) {
 
 cudaError_t batch_alloc(Batch& B, int capacity, int storage, int weighted, int num_sms) {
   const int n = capacity;
+  B.tile_edges = tile_edges_for(storage);
   B.n = n;
   B.storage = storage;
   B.weighted = weighted;
@@ -818,7 +819,7 @@ dualip_status dualip_batch_dual_grad(dualip_batch* b, const float* lambda, const
 
 dualip_status dualip_batch_set_tile_shape(dualip_batch* b, int32_t edges, int32_t sources) {
   if (!b) return fail(DUALIP_EINVAL, "batch is NULL");
-  if (edges < 1 || edges > kTileEdges || sources < 1 || sources > kTileSources)
+  if (edges < 1 || edges > tile_edges_for(b->b.storage) || sources < 1 || sources > kTileSources)
     return fail(DUALIP_EINVAL, "tile shape out of range");
   Batch& B = b->b;
   B.tile_edges = edges;
@@ -1015,7 +1016,8 @@ dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* res
   // candidates: a shape is dropped when most of its tiles would hold a single
   // source (p99 degree above half the edge budget) or when its source cap
   // would stop tiles at under a quarter of the edge budget
-  const int32_t cand[][2] = {{kTileEdges, 256}, {kTileEdges, 128}, {2048, 256}, {2048, 128},
+  const int32_t emax = tile_edges_for(B.storage);
+  const int32_t cand[][2] = {{emax, 256}, {emax, 128}, {2048, 256}, {2048, 128},
                              {1536, 128}, {1024, 128}, {1024, 64},   {512, 64}};
   std::vector<int> keep;
   for (int c = 0; c < 8; ++c) {

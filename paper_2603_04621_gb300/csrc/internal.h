@@ -27,6 +27,14 @@ namespace dualip {
 #define DUALIP_PRIV_DESTS 1024
 #endif
 constexpr int kTileEdges = DUALIP_TILE_EDGES;       // edge capacity of a stage
+#ifndef DUALIP_TILE_EDGES_BF16
+#define DUALIP_TILE_EDGES_BF16 4800
+#endif
+// edge capacity of a stage with BF16 (c, a): 8 bytes per edge instead of 12
+constexpr int kTileEdgesBF16 = DUALIP_TILE_EDGES_BF16;
+constexpr int tile_edges_for(int storage) {
+  return storage == DUALIP_EDGE_BF16 ? kTileEdgesBF16 : kTileEdges;
+}
 #ifndef DUALIP_TILE_SOURCES
 #define DUALIP_TILE_SOURCES 256
 #endif
@@ -54,7 +62,7 @@ constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
 constexpr int kMaxCachedDests = 10240; // hot destinations whose mu lives in smem
 constexpr int kMaxPrivDests = DUALIP_PRIV_DESTS;  // hot destinations accumulated in smem
 constexpr int kRegMaxDeg = 128;        // degrees held in registers (4 per lane)
-constexpr int kStageEdgeSlots = kTileEdges + 8;      // + 16-byte alignment slack
+constexpr int kStageSlack = 8;                      // 16-byte alignment slack of a stage
 constexpr int kDstPad = 512;                         // widest group window (32 lanes x 16)
 constexpr int kStageOffSlots = kTileSources + 4;
 

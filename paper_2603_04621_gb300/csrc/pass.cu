@@ -224,12 +224,14 @@ struct alignas(16) StageInfo {
 template <bool BF16>
 struct Layout {
   static constexpr size_t kOffBytes = sizeof(int64_t) * kStageOffSlots;
-  static constexpr size_t kEdgeArr = sizeof(uint32_t) * kStageEdgeSlots;
+  static constexpr int kTile = BF16 ? kTileEdgesBF16 : kTileEdges;  // edges of a tile
+  static constexpr int kSlots = kTile + kStageSlack;
+  static constexpr size_t kEdgeArr = sizeof(uint32_t) * kSlots;
   // dst carries kDstPad extra slots: a group's aligned window (at most 512
   // slots) never leaves it, and every slot holds a valid destination id
   // (zeroed at start, then earlier tiles' ids), so window slots outside the
   // source need no index masking
-  static constexpr size_t kDstArr = sizeof(uint32_t) * (kStageEdgeSlots + kDstPad);
+  static constexpr size_t kDstArr = sizeof(uint32_t) * (kSlots + kDstPad);
   static constexpr size_t kStageBytes = kOffBytes + kDstArr + kEdgeArr * (BF16 ? 1 : 2);
   static constexpr size_t kMu = kStages * kStageBytes;
   static constexpr size_t kY = kMu + sizeof(float) * kMaxCachedDests;
@@ -874,12 +876,12 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       si.e0 = e0;
       si.e1 = e1;
       const bool bad = !done && (s1 - s0 > kTileSources || s1 < s0 || e1 < e0 ||
-                                 (e1 - e0 > kTileEdges && s1 - s0 != 1));
+                                 (e1 - e0 > L::kTile && s1 - s0 != 1));
       if (bad) {
         atomicOr(&p.status->err, kErrBounds);
         si.s1 = s0;  // skip the tile; results are flagged invalid
       }
-      si.big = done ? 2 : ((!bad && e1 - e0 > kTileEdges) ? 1 : 0);
+      si.big = done ? 2 : ((!bad && e1 - e0 > L::kTile) ? 1 : 0);
       si.slot = slot;
       si.a0 = e0 & ~int64_t(3);
       si.o0 = s0 & ~int64_t(1);
