@@ -9,14 +9,16 @@
 // grad = A x - b, g(mu) (Eq. 2) and ||(A x - b)_+|| (Appendix A).
 //
 // Kernel design (GB300-first, not the paper's bucketed padded slabs):
-//  * one persistent CTA per SM walks a contiguous range of "tiles" (runs of
-//    whole sources holding <= kTileEdges edges and <= kTileSources sources);
-//    warp 0 streams each tile's offsets, destinations and (c, a) into a
+//  * one persistent CTA per SM walks "tiles" (runs of whole sources holding
+//    at most a stage's edges and kTileSources sources): a single problem's
+//    tiles are taken in grabs of DUALIP_GRAB from a counter shared by all
+//    CTAs (balanced ends), a batched pass's in a contiguous range.  Warp 0
+//    streams each tile's offsets, destinations and (c, a) into a
 //    kStages-deep shared-memory ring with cp.async.bulk + mbarrier
-//    transaction counts; 16 consumer warps project;
+//    transaction counts; the other warps project;
 //  * consumer warps claim batches of eight sources of a staged tile through a
 //    per-stage shared counter; the span of a source picks how many lanes
-//    share it (4, 8, 16 or 32, up to 16 edges per lane in registers);
+//    share it (4, 8, 16 or 32, up to 16 or 20 edges per lane in registers);
 //  * the common case at small gamma is a saturated source with a single
 //    candidate (its second score is more than gamma below the first): it gets
 //    x = 1 exactly.  Everything else (unsaturated sources, near-ties, spans
@@ -25,8 +27,8 @@
 //    (hi + lo = -(c + a mu) to about 2^-48 relative) shifted by the block
 //    maximum (exact by Sterbenz's lemma near the top), so the threshold and x
 //    keep FP32 accuracy relative to gamma; Michelot's finite iteration starts
-//    from {d_e > max_e(d_e - gamma w_e)}, which contains the active set.  A
-//    source larger than a tile is projected by one warp from global memory;
+//    from a set that contains the active set.  A source larger than a tile is
+//    projected by one warp from global memory;
 //  * y = A x accumulates in 64-bit two's-complement fixed point (scale
 //    2^exp_y chosen at create so that no sum can overflow): every add is
 //    exact, so A x does not depend on the order of the adds.  Hot
@@ -34,7 +36,12 @@
 //    and are flushed once per CTA; the rest go to global atomics;
 //  * objective partials are per-lane FP32 TwoSum accumulators and FP32
 //    double-float pairs through the warp and CTA trees; batches go to warps
-//    dynamically, so their last bits may differ from run to run.
+//    dynamically, so their last bits may differ from run to run;
+//  * the pass may be launched before the preceding kernel of its stream has
+//    finished (programmatic dependent launch): until the consumers have waited
+//    for that kernel, the producer reads only the problem's immutable arrays
+//    and the schedule counter (rewound by the previous pass, which finished
+//    before that kernel began).
 #include <cuda_bf16.h>
 #include <math_constants.h>
 
