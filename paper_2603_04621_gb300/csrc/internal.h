@@ -61,7 +61,6 @@ constexpr unsigned kWaitHintNs = DUALIP_WAIT_HINT_NS;  // mbarrier suspend hint 
 constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
 constexpr int kMaxCachedDests = 10240; // hot destinations whose mu lives in smem
 constexpr int kMaxPrivDests = DUALIP_PRIV_DESTS;  // hot destinations accumulated in smem
-constexpr int kRegMaxDeg = 128;        // degrees held in registers (4 per lane)
 constexpr int kStageSlack = 8;                      // 16-byte alignment slack of a stage
 constexpr int kDstPad = 512;                         // widest group window (32 lanes x 16)
 constexpr int kStageOffSlots = kTileSources + 4;
