@@ -2,13 +2,18 @@
 //
 // The iteration lives entirely on the device so that check_every iterations
 // can be replayed as one CUDA graph with no host synchronisation:
-//   prep   (J)  gamma_k from k; momentum restart on a gamma change; mu = D y
 //   pass        projection + A x (pass.cu), gamma read from the state
 //   epi    (J)  G = D (A x - b) and the FP64 scalars (pass.cu)
 //   norms  (J)  ||y - y_prev||, ||G - G_prev|| in FP64; the last block picks
 //               the step (secant estimate capped by max_step * gamma / gamma0),
-//               the momentum weight, the stopping scalars and the trace row
-//   step   (J)  lam+ = max(0, y + eta G); y+ = max(0, lam+ + beta (lam+ - lam))
+//               the momentum weight, the stopping scalars and the trace row,
+//               advances k and publishes gamma_{k+1}
+//   step   (J)  lam+ = max(0, y + eta G); y+ = max(0, lam+ + beta (lam+ - lam)),
+//               or y+ = lam+ when gamma changes at k+1 (momentum restart);
+//               mu = D y+ for the next pass
+// A prep kernel forms mu and gamma of the first iteration.  Every kernel but
+// the first of the chain is launched with programmatic stream serialisation
+// and waits for its predecessor before it reads.
 // Vectors are kept in the renumbered destination order and in the
 // normalised coordinates lam' of Section 5.1 (mu = D lam').
 #include <algorithm>
