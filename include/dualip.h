@@ -338,8 +338,8 @@ typedef struct {
 } dualip_server_opts;
 
 typedef enum {
-  DUALIP_REQ_QUEUED = 0,
-  DUALIP_REQ_RUNNING = 1,  /* admitted: being built or iterating */
+  DUALIP_REQ_QUEUED = 0,   /* waiting for admission, or admitted and being built */
+  DUALIP_REQ_RUNNING = 1,  /* built (its inputs copied): waiting to join, or iterating */
   DUALIP_REQ_DONE = 2,
   DUALIP_REQ_FAILED = 3
 } dualip_request_state;
@@ -376,9 +376,10 @@ dualip_status dualip_server_poll(dualip_server* s, int64_t ticket, dualip_reques
 dualip_status dualip_server_wait(dualip_server* s, int64_t ticket, double timeout_s,
                                  dualip_request_info* info, float* lambda_out);
 dualip_status dualip_server_get_stats(dualip_server* s, dualip_server_stats* stats);
-/* Cancels a request: a queued one leaves the queue at once, an admitted one
- * leaves at the next chunk boundary; it ends FAILED with DUALIP_ECANCELED
- * and no lambda.  A request already DONE or FAILED is left as it is. */
+/* Cancels a request: one waiting for admission leaves the queue at once; one
+ * being built or running leaves when its build ends or at the next chunk
+ * boundary.  It ends FAILED with DUALIP_ECANCELED and no lambda.  A request
+ * already DONE or FAILED is left as it is. */
 dualip_status dualip_server_cancel(dualip_server* s, int64_t ticket);
 /* Stops the loop; queued and running requests are dropped. */
 void dualip_server_destroy(dualip_server* s);

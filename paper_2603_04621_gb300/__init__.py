@@ -628,7 +628,8 @@ class Server:
     def wait(self, ticket: int, timeout_s: float = 600.0):
         lam = np.empty(self._J[ticket], dtype=np.float32)
         info = dualip_server_wait(self.h, ticket, timeout_s, lam.ctypes.data)
-        self._keep.pop(ticket, None)
+        if info["state"] != DUALIP_REQ_QUEUED:  # the build has copied the arrays
+            self._keep.pop(ticket, None)
         return info, (lam if info["state"] == DUALIP_REQ_DONE else None)
 
     def stats(self) -> dict:

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -53,6 +54,20 @@ void free_all(Problem& P) {
   P.allocations.clear();
   if (P.eval_host) cudaFreeHost(P.eval_host);
   P.eval_host = nullptr;
+}
+
+// The pass kernels' shared-memory limits are set once per device (a function
+// attribute is set on the current device), under a lock: problems may be
+// created from several host threads at once.
+cudaError_t configure_device_once(int device) {
+  static std::mutex m;
+  static std::vector<char> done;
+  std::lock_guard<std::mutex> lk(m);
+  if (device >= (int)done.size()) done.resize((size_t)device + 1, 0);
+  if (done[device]) return cudaSuccess;
+  const cudaError_t e = configure_pass_kernels();
+  if (e == cudaSuccess) done[device] = 1;
+  return e;
 }
 
 }  // namespace
@@ -191,11 +206,8 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   if ((e = cudaGetDevice(&P.device))) return bail(cuda_fail(e, "cudaGetDevice"));
   if ((e = cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, P.device)))
     return bail(cuda_fail(e, "querying the SM count"));
-  static bool configured = false;
-  if (!configured) {
-    if ((e = configure_pass_kernels())) return bail(cuda_fail(e, "configuring the pass kernel"));
-    configured = true;
-  }
+  if ((e = configure_device_once(P.device)))
+    return bail(cuda_fail(e, "configuring the pass kernel"));
 
   std::vector<int64_t> tiles, tile_e;
   build_tiles(off, tiles, tile_e, tile_edges_for(P.storage));
@@ -355,7 +367,8 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     P.exp_y = std::max(-100, std::min(100, 61 - ex));
   }
   DeviceStatus st{};
-  if ((e = cudaMemcpy(&st, P.status, sizeof(st), cudaMemcpyDeviceToHost)))
+  if ((e = cudaMemcpyAsync(&st, P.status, sizeof(st), cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
     return bail(cuda_fail(e, "reading the device status"));
   if (st.err) return bail(fail(DUALIP_EINVAL, "dst out of [0, J) or non-finite c / a"));
   P.off_host = std::move(off);

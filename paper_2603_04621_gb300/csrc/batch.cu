@@ -503,7 +503,8 @@ dualip_status batch_status(Batch& B) {
   return DUALIP_OK;
 }
 
-cudaError_t batch_alloc(Batch& B, int capacity, int storage, int weighted, int num_sms) {
+static cudaError_t batch_alloc_parts(Batch& B, int capacity, int storage, int weighted,
+                                     int num_sms) {
   const int n = capacity;
   B.tile_edges = tile_edges_for(storage);
   B.n = n;
@@ -545,6 +546,16 @@ cudaError_t batch_alloc(Batch& B, int capacity, int storage, int weighted, int n
       (e = cudaStreamSynchronize(B.stream)))
     return e;
   return cudaSuccess;
+}
+
+// On failure, everything allocated so far is released and B is left empty.
+cudaError_t batch_alloc(Batch& B, int capacity, int storage, int weighted, int num_sms) {
+  const cudaError_t e = batch_alloc_parts(B, capacity, storage, weighted, num_sms);
+  if (e) {
+    batch_free(B);
+    B = Batch{};
+  }
+  return e;
 }
 
 SlotDesc slot_desc(Problem& P, int64_t joff) {

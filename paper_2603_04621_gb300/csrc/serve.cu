@@ -5,7 +5,8 @@
 // requests in arrival order while a slot is free and the request's estimated
 // footprint fits the HBM budget, and builds each on the device with
 // dualip_create on its own stream (so the upload overlaps the iterations of
-// the resident requests).  The scheduler thread attaches built requests to
+// the resident requests).  A request stays QUEUED while it is built, since the
+// build reads the caller's arrays; it turns RUNNING once they are copied.  The scheduler thread attaches built requests to
 // the batch of their storage kind at a chunk boundary, runs every non-empty
 // batch for check_every iterations (one CUDA graph per batch membership),
 // reads the per-request stopping quantities, and retires requests that have
@@ -40,7 +41,8 @@ struct Request {
   dualip_problem* h = nullptr;  // built, waiting for a slot, or resident
   int kind = 0, slot = -1;
   int32_t iters = 0;
-  bool cancel = false;  // leaves at the next chunk boundary
+  bool building = false;  // admitted; dualip_create is reading the caller's arrays
+  bool cancel = false;    // leaves when its build ends or at the next chunk boundary
   dualip_solve_result result{};
   std::vector<float> lam;
 };
@@ -124,7 +126,7 @@ void Server::admit_loop() {
       t = queue.front();
       queue.pop_front();
       Request& r = reqs[t];
-      r.state = DUALIP_REQ_RUNNING;
+      r.building = true;
       r.t_admit = now();
       resident += r.footprint;
       peak = std::max(peak, resident + r.transient);
@@ -136,12 +138,14 @@ void Server::admit_loop() {
     std::string msg = st ? dualip_last_error() : "";
     std::lock_guard<std::mutex> lk(mu);
     Request& r = reqs[t];
+    r.building = false;
     if (st) {
       r.status = st;
       r.error = msg;
       finish_locked(r, DUALIP_REQ_FAILED);
     } else {
       r.h = h;
+      r.state = DUALIP_REQ_RUNNING;  // a cancel taken during the build is honoured at attach
       built.push_back(t);
       cv.notify_all();
     }
@@ -162,8 +166,11 @@ void Server::run_chunks() {
     if (!e) e = run_batch_chunk(B, o.check_every, true);
     if (!e) e = batch_read_state(B);
     dualip_status st = e ? cuda_fail(e, "running a serving chunk") : batch_status(B);
-    busy += now() - c0;
-    ++chunks;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      busy += now() - c0;
+      ++chunks;
+    }
     for (int s = 0; s < B.n; ++s) {
       if (!B.active[s]) continue;
       const int64_t t = slot_ticket[k][s];
@@ -446,7 +453,7 @@ dualip_status dualip_server_cancel(dualip_server* h, int64_t ticket) {
   auto it = S.reqs.find(ticket);
   if (it == S.reqs.end()) return fail(DUALIP_EINVAL, "unknown ticket");
   Request& r = it->second;
-  if (r.state == DUALIP_REQ_QUEUED) {
+  if (r.state == DUALIP_REQ_QUEUED && !r.building) {
     for (auto q = S.queue.begin(); q != S.queue.end(); ++q)
       if (*q == ticket) {
         S.queue.erase(q);
@@ -458,8 +465,8 @@ dualip_status dualip_server_cancel(dualip_server* h, int64_t ticket) {
     r.t_done = S.now();
     ++S.n_failed;
     S.cv.notify_all();
-  } else if (r.state == DUALIP_REQ_RUNNING) {
-    r.cancel = true;
+  } else if (r.state == DUALIP_REQ_QUEUED || r.state == DUALIP_REQ_RUNNING) {
+    r.cancel = true;  // being built or resident: leaves at the next chunk boundary
   }
   return DUALIP_OK;
 }

@@ -7,6 +7,7 @@
   then run one after another), and a request that can never fit fails.
 * FP32 and BF16 requests run side by side, each matching the oracle on the
   values it stores.
+* A request's input arrays may be overwritten once it reports RUNNING.
 """
 import time
 
@@ -124,3 +125,26 @@ def test_mixed_storage_matches_oracle(dl):
         eo = oracle.Problem(ref).eval(lam.astype(np.float64), gamma)
         # the returned lambda is the point of the last evaluation
         assert abs(info["dual_obj"] - eo.dual) <= 1e-6 * max(1.0, abs(eo.dual))
+
+
+def test_inputs_may_change_once_running(dl):
+    """A request's host arrays have been copied by the time it reports RUNNING:
+    overwriting them from then on leaves its result as it was."""
+    kw = dict(max_iters=200, stop_on_tol=0)
+    x_ref = requests(1, seed=99)[0][0]
+    x = requests(1, seed=99)[0][0]  # the same instance, in arrays of its own
+    srv = dl.Server(64 * GIB, max_slots=4)
+    ref_info, ref_lam = srv.wait(srv.submit(x_ref, **kw))
+    t = srv.submit(x, **kw)
+    assert np.shares_memory(srv._keep[t][2], x.c)  # the server reads x's own buffers
+    deadline = time.time() + 60
+    while srv.poll(t)["state"] == dl.DUALIP_REQ_QUEUED and time.time() < deadline:
+        time.sleep(0.001)
+    for arr in (x.c, x.a, x.b):
+        arr[:] = 7.0
+    x.dst[:] = 0
+    info, lam = srv.wait(t)
+    srv.close()
+    assert ref_info["state"] == info["state"] == dl.DUALIP_REQ_DONE
+    assert info["iters"] == ref_info["iters"] == 200
+    assert np.array_equal(lam, ref_lam)
