@@ -273,17 +273,18 @@ static cudaError_t solve_ctx_get(Problem& P, SolveCtx** out) {
   SolveCtx* C = new SolveCtx();
   P.solve_ctx = C;
   const size_t n = (size_t)P.J * sizeof(float);
+  C->blocks = (int)std::max<int64_t>(1, std::min<int64_t>((P.J + 255) / 256, 2 * P.num_sms));
   cudaError_t e;
   if ((e = cudaMalloc(&C->lam, n)) || (e = cudaMalloc(&C->y, n)) || (e = cudaMalloc(&C->yp, n)) ||
-      (e = cudaMalloc(&C->G, n)) || (e = cudaMalloc(&C->Gp, n)) || (e = cudaMalloc(&C->D, n)))
-    return e;
-  C->blocks = (int)std::max<int64_t>(1, std::min<int64_t>((P.J + 255) / 256, 2 * P.num_sms));
-  if ((e = cudaMalloc(&C->part, sizeof(double) * 2 * C->blocks)) ||
+      (e = cudaMalloc(&C->G, n)) || (e = cudaMalloc(&C->Gp, n)) || (e = cudaMalloc(&C->D, n)) ||
+      (e = cudaMalloc(&C->part, sizeof(double) * 2 * C->blocks)) ||
       (e = cudaMalloc(&C->st, sizeof(SolveState))) ||
       (e = cudaMallocHost(&C->st_host, sizeof(SolveState))) ||
       (e = cudaStreamCreateWithFlags(&C->stream, cudaStreamNonBlocking)) ||
-      (e = cudaEventCreateWithFlags(&C->ev, cudaEventDisableTiming)))
+      (e = cudaEventCreateWithFlags(&C->ev, cudaEventDisableTiming))) {
+    solve_ctx_free(P);  // a later call starts again from nothing
     return e;
+  }
   *out = C;
   return cudaSuccess;
 }
