@@ -100,7 +100,12 @@ typedef struct dualip_problem dualip_problem;
  * finiteness).  Work is queued on `stream` and finished before return.
  * Errors: DUALIP_EINVAL (bad desc or data), DUALIP_ENOMEM, DUALIP_ECUDA.
  * On success *out owns device memory of about E * (4 + bytes of c and a)
- * + 8 I + 40 J bytes; free it with dualip_destroy. */
+ * + 8 I + 40 J bytes; free it with dualip_destroy.
+ * Degree order: when the source degrees spread widely (standard deviation
+ * above 0.3 of the mean), the sources are stored in order of increasing
+ * degree.  Results do not depend on it beyond rounding: gradients are exact
+ * sums either way, the scalars' partial sums come in another order, and
+ * dualip_get_primal returns x in the caller's edge order. */
 dualip_status dualip_create(const dualip_problem_desc* desc, void* stream, dualip_problem** out);
 
 /* Release a handle (NULL is ignored).  Synchronises the handle's last stream. */
@@ -133,8 +138,11 @@ dualip_status dualip_dual_grad_async(dualip_problem* p, const float* lambda, dou
 dualip_status dualip_dual_grad_host(dualip_problem* p, const float* lambda_host, double gamma,
                                     float* grad_host, dualip_eval* out, void* stream);
 
-/* The primal minimiser x*(lambda) of Section 3.1 for every edge, in edge order:
- *   x  [E] float, device, written.  Other arguments as dualip_dual_grad. */
+/* The primal minimiser x*(lambda) of Section 3.1 for every edge, in the
+ * caller's edge order:
+ *   x  [E] float, device, written.  Other arguments as dualip_dual_grad.
+ * For a problem stored in degree order it takes a stream-ordered temporary of
+ * E floats and 16 bytes per source. */
 dualip_status dualip_get_primal(dualip_problem* p, const float* lambda, double gamma, float* x,
                                 void* stream);
 

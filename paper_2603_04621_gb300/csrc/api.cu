@@ -101,6 +101,21 @@ void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
+// Degrees spread widely when their standard deviation exceeds 0.3 of their
+// mean.  Such problems are stored in degree order (dualip_create).
+bool degrees_spread_widely(const std::vector<int64_t>& off) {
+  const int64_t I = (int64_t)off.size() - 1;
+  if (I < 2) return false;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = 0; i < I; ++i) {
+    const double d = (double)(off[i + 1] - off[i]);
+    s1 += d;
+    s2 += d * d;
+  }
+  const double mean = s1 / (double)I, var = s2 / (double)I - mean * mean;
+  return mean > 0.0 && var > 0.09 * mean * mean;
+}
+
 namespace {
 
 dualip_status read_status(Problem& P, cudaStream_t s) {
@@ -188,6 +203,26 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     if (off[i + 1] < off[i]) return fail(DUALIP_EINVAL, "src_offsets must be nondecreasing");
   if (off[I] != E) return fail(DUALIP_EINVAL, "src_offsets[I] must equal num_edges");
 
+  // Degree order: when the degrees spread widely, sources are stored by
+  // increasing degree (ties in the caller's order), so that the pass's
+  // batches of eight consecutive sources have similar spans and one window
+  // width serves all eight.  Sources are independent blocks of the problem:
+  // only the order of the objective's partial sums changes, and
+  // dualip_get_primal maps x back to the caller's order.
+  std::vector<int64_t> src_of, off_st;
+  if (degrees_spread_widely(off)) {
+    src_of.resize((size_t)I);
+    std::iota(src_of.begin(), src_of.end(), int64_t(0));
+    std::stable_sort(src_of.begin(), src_of.end(), [&](int64_t x, int64_t y) {
+      return off[x + 1] - off[x] < off[y + 1] - off[y];
+    });
+    off_st.resize((size_t)I + 1);
+    off_st[0] = 0;
+    for (int64_t i = 0; i < I; ++i) off_st[i + 1] = off_st[i] + (off[src_of[i] + 1] - off[src_of[i]]);
+  }
+  const bool seg = !src_of.empty();
+  const std::vector<int64_t>& off_s = seg ? off_st : off;  // offsets as stored
+
   auto* h = new (std::nothrow) dualip_problem();
   if (!h) return fail(DUALIP_ENOMEM, "host allocation failed");
   Problem& P = h->p;
@@ -210,7 +245,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     return bail(cuda_fail(e, "configuring the pass kernel"));
 
   std::vector<int64_t> tiles, tile_e;
-  build_tiles(off, tiles, tile_e, tile_edges_for(P.storage));
+  build_tiles(off_s, tiles, tile_e, tile_edges_for(P.storage));
   P.ntiles = (int64_t)tiles.size() - 1;
   P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P.num_sms, P.ntiles));
   P.h_mu = std::min(J, kMaxCachedDests);
@@ -220,7 +255,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   const size_t e_pad = (size_t)((E + 3) & ~int64_t(3)) + 4;
   const size_t i_pad = (size_t)I + 4;
   std::vector<int64_t> off_pad(i_pad, E);
-  std::copy(off.begin(), off.end(), off_pad.begin());
+  std::copy(off_s.begin(), off_s.end(), off_pad.begin());
 
   if ((e = dev_alloc(P, &P.off, i_pad)) || (e = dev_alloc(P, &P.dst, e_pad)) ||
       (e = dev_alloc(P, &P.tiles, tiles.size())) || (e = dev_alloc(P, &P.tile_e, tiles.size())) ||
@@ -257,15 +292,34 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   const int32_t* dst_raw = d->dst;
   int32_t* dst_tmp = nullptr;
   unsigned* counts = nullptr;
+  int64_t *seg_src = nullptr, *seg_orig = nullptr;  // degree order: device copies of the map
   // temporaries are stream-ordered (cudaMallocAsync / cudaFreeAsync on s): no
   // device-wide synchronisation, so a build overlaps other streams' kernels
-  if ((e = cudaMallocAsync(&counts, sizeof(unsigned) * J, s)))
+  auto free_seg = [&]() {
+    if (seg_src) cudaFreeAsync(seg_src, s);
+    if (seg_orig) cudaFreeAsync(seg_orig, s);
+    seg_src = seg_orig = nullptr;
+  };
+  if (seg && ((e = cudaMallocAsync(&seg_src, sizeof(int64_t) * I, s)) ||
+              (e = cudaMallocAsync(&seg_orig, sizeof(int64_t) * (I + 1), s)) ||
+              (e = cudaMemcpyAsync(seg_src, src_of.data(), sizeof(int64_t) * I,
+                                   cudaMemcpyHostToDevice, s)) ||
+              (e = cudaMemcpyAsync(seg_orig, off.data(), sizeof(int64_t) * (I + 1),
+                                   cudaMemcpyHostToDevice, s)))) {
+    free_seg();
+    return bail(cuda_fail(e, "uploading the source order"));
+  }
+  const SegMap segmap{P.off, seg_src, seg_orig, I};
+  if ((e = cudaMallocAsync(&counts, sizeof(unsigned) * J, s))) {
+    free_seg();
     return bail(cuda_fail(e, "allocating"));
+  }
   auto free_tmp = [&]() {
     if (dst_tmp) cudaFreeAsync(dst_tmp, s);
     if (counts) cudaFreeAsync(counts, s);
     dst_tmp = nullptr;
     counts = nullptr;
+    free_seg();
   };
   if (!d->inputs_on_device && E > 0) {
     if ((e = cudaMallocAsync(&dst_tmp, sizeof(int32_t) * E, s)) ||
@@ -311,17 +365,24 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   if ((e = cudaMemcpyAsync(P.orig_of, orig_of.data(), 4 * (size_t)J, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(P.new_of, new_of.data(), 4 * (size_t)J, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(P.b_r, b_r.data(), 4 * (size_t)J, cudaMemcpyHostToDevice, s)) ||
-      (E > 0 && (e = launch_renumber(dst_raw, P.dst, P.new_of, E, J, P.status, s)))) {
+      (E > 0 && !seg && (e = launch_renumber(dst_raw, P.dst, P.new_of, E, J, P.status, s))) ||
+      (E > 0 && seg &&
+       (e = launch_renumber_seg(dst_raw, P.dst, P.new_of, segmap, J, P.status, s)))) {
     free_tmp();
     return bail(cuda_fail(e, "renumbering destinations"));
   }
-  free_tmp();
+  if (dst_tmp) cudaFreeAsync(dst_tmp, s);
+  if (counts) cudaFreeAsync(counts, s);
+  dst_tmp = nullptr;
+  counts = nullptr;
 
   // edge values
   unsigned absmax[2] = {0u, 0u};  // bit patterns of max |c|, max |a|
   unsigned* counts_max = nullptr;
-  if ((e = cudaMallocAsync(&counts_max, 2 * sizeof(unsigned), s)))
+  if ((e = cudaMallocAsync(&counts_max, 2 * sizeof(unsigned), s))) {
+    free_seg();
     return bail(cuda_fail(e, "allocating"));
+  }
   if (E > 0) {
     float *c_tmp = nullptr, *a_tmp = nullptr;
     const float *c_src = d->c, *a_src = d->a;
@@ -332,6 +393,8 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
           (e = cudaMemcpyAsync(a_tmp, d->a, 4 * (size_t)E, h2d, s))) {
         if (c_tmp) cudaFreeAsync(c_tmp, s);
         if (a_tmp) cudaFreeAsync(a_tmp, s);
+        cudaFreeAsync(counts_max, s);
+        free_seg();
         return bail(cuda_fail(e, "uploading c and a"));
       }
       c_src = c_tmp;
@@ -344,16 +407,24 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
         (e = launch_absmax(a_src, E, counts_max + 1, s)) ||
         (e = cudaMemcpyAsync(absmax, counts_max, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost,
                              s)) ||
-        (P.storage == DUALIP_EDGE_BF16 && (e = launch_pack_bf16(c_src, a_src, P.ca, E, s))) ||
-        (P.storage == DUALIP_EDGE_F32 && (e = launch_pack_f32(c_src, a_src, P.ca2, E, s)))) {
+        (!seg && P.storage == DUALIP_EDGE_BF16 &&
+         (e = launch_pack_bf16(c_src, a_src, P.ca, E, s))) ||
+        (!seg && P.storage == DUALIP_EDGE_F32 &&
+         (e = launch_pack_f32(c_src, a_src, P.ca2, E, s))) ||
+        (seg && (e = launch_pack_seg(c_src, a_src, P.storage,
+                                     P.storage == DUALIP_EDGE_BF16 ? (void*)P.ca : (void*)P.ca2,
+                                     segmap, s)))) {
       if (c_tmp) cudaFreeAsync(c_tmp, s);
       if (a_tmp) cudaFreeAsync(a_tmp, s);
+      cudaFreeAsync(counts_max, s);
+      free_seg();
       return bail(cuda_fail(e, "checking edge values"));
     }
     if (c_tmp) cudaFreeAsync(c_tmp, s);
     if (a_tmp) cudaFreeAsync(a_tmp, s);
   }
   cudaFreeAsync(counts_max, s);
+  free_seg();
   e = cudaStreamSynchronize(s);
   if (e) return bail(cuda_fail(e, "building the problem"));
   // Fixed-point scale 2^exp_y of A x: |(A x)_j| <= max in-degree * max |a|
@@ -371,7 +442,13 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
       (e = cudaStreamSynchronize(s)))
     return bail(cuda_fail(e, "reading the device status"));
   if (st.err) return bail(fail(DUALIP_EINVAL, "dst out of [0, J) or non-finite c / a"));
-  P.off_host = std::move(off);
+  if (seg) {
+    P.off_host = std::move(off_st);
+    P.orig_off_host = std::move(off);
+    P.src_of_host = std::move(src_of);
+  } else {
+    P.off_host = std::move(off);
+  }
   *out = h;
   return DUALIP_OK;
 }
@@ -451,7 +528,28 @@ dualip_status dualip_get_primal(dualip_problem* h, const float* lambda, double g
   Problem& P = h->p;
   cudaStream_t s = as_stream(stream);
   P.last_stream = s;
-  cudaError_t e = enqueue_eval(P, lambda, gamma, P.grad_stage, P.eval_dev, x, s);
+  cudaError_t e;
+  if (P.src_of_host.empty()) {
+    e = enqueue_eval(P, lambda, gamma, P.grad_stage, P.eval_dev, x, s);
+    return e ? cuda_fail(e, "launching the primal evaluation") : DUALIP_OK;
+  }
+  // degree order: x in stored order, then each source's segment back to the
+  // caller's place (stream-ordered temporaries)
+  float* xs = nullptr;
+  int64_t *src = nullptr, *orig = nullptr;
+  const int64_t I = P.I;
+  if (!(e = cudaMallocAsync(&xs, sizeof(float) * std::max<int64_t>(P.E, 1), s)) &&
+      !(e = cudaMallocAsync(&src, sizeof(int64_t) * I, s)) &&
+      !(e = cudaMallocAsync(&orig, sizeof(int64_t) * (I + 1), s)) &&
+      !(e = cudaMemcpyAsync(src, P.src_of_host.data(), sizeof(int64_t) * I,
+                            cudaMemcpyHostToDevice, s)) &&
+      !(e = cudaMemcpyAsync(orig, P.orig_off_host.data(), sizeof(int64_t) * (I + 1),
+                            cudaMemcpyHostToDevice, s)) &&
+      !(e = enqueue_eval(P, lambda, gamma, P.grad_stage, P.eval_dev, xs, s)))
+    e = launch_unpermute_seg(xs, x, SegMap{P.off, src, orig, I}, s);
+  if (xs) cudaFreeAsync(xs, s);
+  if (src) cudaFreeAsync(src, s);
+  if (orig) cudaFreeAsync(orig, s);
   return e ? cuda_fail(e, "launching the primal evaluation") : DUALIP_OK;
 }
 

@@ -214,7 +214,11 @@ struct Problem {
   double bnorm = 0.0;           // ||b||_2
   void* solve_ctx = nullptr;    // solver state, created by the first dualip_solve
   std::vector<cudaEvent_t> prof_ev;  // 4 per recorded evaluation
-  std::vector<int64_t> off_host;     // source offsets (tiling of batched passes)
+  std::vector<int64_t> off_host;     // source offsets as stored (tiling of batched passes)
+  // degree order (empty: sources are stored in the caller's order): stored
+  // source i is the caller's source src_of_host[i]; orig_off_host holds the
+  // caller's offsets
+  std::vector<int64_t> src_of_host, orig_off_host;
   int prof_max = 0, prof_used = 0;
   std::vector<void*> allocations;
 };
@@ -274,6 +278,20 @@ cudaError_t launch_pack_f32(const float* c, const float* a, float2* ca2, int64_t
 cudaError_t launch_pack_bf16(const float* c, const float* a, uint32_t* ca, int64_t E,
                              cudaStream_t s);
 cudaError_t launch_check_finite(const float* v, int64_t n, DeviceStatus* st, cudaStream_t s);
+// Degree order: stored source i is the caller's source src_of[i]; its edges
+// sit at off[i] .. off[i+1]-1 in storage and start at orig_off[src_of[i]] in
+// the caller's arrays (all three are device arrays).
+struct SegMap {
+  const int64_t* off;
+  const int64_t* src_of;
+  const int64_t* orig_off;
+  int64_t I;
+};
+cudaError_t launch_renumber_seg(const int32_t* dst_in, int32_t* dst_out, const int32_t* new_of,
+                                const SegMap& m, int32_t J, DeviceStatus* st, cudaStream_t s);
+cudaError_t launch_pack_seg(const float* c, const float* a, int storage, void* out,
+                            const SegMap& m, cudaStream_t s);
+cudaError_t launch_unpermute_seg(const float* in, float* out, const SegMap& m, cudaStream_t s);
 cudaError_t launch_absmax(const float* v, int64_t n, unsigned* out, cudaStream_t s);
 
 // solve.cu

@@ -165,6 +165,42 @@ def test_primal_matches_oracle(dl):
         assert sums.max() <= 1 + 1e-5
 
 
+def degree_cv(inst):
+    deg = np.diff(inst.off).astype(np.float64)
+    return deg.std() / deg.mean()
+
+
+@pytest.mark.parametrize("storage,weighted", [("f32", False), ("bf16", True)])
+def test_degree_order_storage(dl, storage, weighted):
+    """Degrees Uniform[5,100] (the batched recipe) spread widely, so the problem
+    is stored in degree order: evaluations, the primal in the caller's edge
+    order, device inputs and the range check all hold on that path."""
+    import torch
+
+    inst = synth.matching(20_000, 3_000, 17, ("uniform", 5, 100), "zipf")
+    assert degree_cv(inst) > 0.3  # the documented threshold for degree order
+    rng = np.random.default_rng(9)
+    P = Po = None
+    for gamma in (0.1, 1e-3):
+        P, Po, _, _ = check_eval(dl, inst, rng.uniform(0, 2, inst.J), gamma, weighted,
+                                 storage=storage, P=P, Po=Po)
+    lam = rng.uniform(0, 2, inst.J).astype(np.float32)
+    ref = decoded(inst) if storage == "bf16" else inst
+    xo = oracle.Problem(ref, weighted=weighted).eval(lam.astype(np.float64), 1e-2,
+                                                     want_x=True).x
+    x = P.primal(torch.from_numpy(lam).cuda(), 1e-2).cpu().numpy()
+    assert np.abs(x - xo).max() <= 2e-5, np.abs(x - xo).max()
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()  # noqa: E731
+    Pd = dl.Problem(t(inst.off), t(inst.dst), t(inst.c), t(inst.a), t(inst.b), inst.J,
+                    storage=storage, primal_scaling=weighted)
+    check_eval(dl, inst, lam, 1e-2, weighted, storage=storage, P=Pd)
+    bad = synth.Instance(inst.off, inst.dst.copy(), inst.c, inst.a, inst.b, inst.J)
+    bad.dst[inst.E // 2] = -1
+    with pytest.raises(dl.DualipError) as ei:
+        dl.Problem.from_instance(bad, storage=storage)
+    assert ei.value.status == dl.DUALIP_EINVAL
+
+
 def test_host_buffer_entry_point(dl):
     inst = synth.config("c2", scale=0.005)
     P = dl.Problem.from_instance(inst)
