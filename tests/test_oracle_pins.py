@@ -127,6 +127,35 @@ def _dense_A(inst):
 
 
 @pytest.mark.parametrize("weighted", [False, True])
+def test_sources_are_independent_blocks(weighted):
+    """Section 3.1: C is a product of one simplex per source, so the minimiser
+    splits by source.  Reordering the sources, and the edges inside each
+    source, reorders x the same way and leaves A x, the gradient and every
+    scalar as they were (up to the order of FP64 sums)."""
+    inst = _tiny(I=300, J=12, seed=51, deg=("uniform", 1, 12))
+    rng = np.random.default_rng(52)
+    perm = rng.permutation(inst.I)
+    edges = []
+    for i in perm:
+        seg = np.arange(inst.off[i], inst.off[i + 1])
+        edges.append(rng.permutation(seg))
+    e_new = np.concatenate(edges).astype(np.int64)
+    deg = np.diff(inst.off)[perm]
+    off2 = np.concatenate([[0], np.cumsum(deg)]).astype(np.int64)
+    moved = synth.Instance(off2, inst.dst[e_new], inst.c[e_new], inst.a[e_new], inst.b, inst.J)
+    lam = rng.uniform(0.0, 1.5, inst.J)
+    for gamma in (0.3, 1e-3):
+        e1 = oracle.Problem(inst, weighted=weighted).eval(lam, gamma, want_x=True)
+        e2 = oracle.Problem(moved, weighted=weighted).eval(lam, gamma, want_x=True)
+        assert np.allclose(e2.x, e1.x[e_new], rtol=0, atol=1e-13)
+        assert np.allclose(e2.ax, e1.ax, rtol=1e-12, atol=1e-13)
+        assert np.allclose(e2.grad, e1.grad, rtol=1e-12, atol=1e-13)
+        for key in ("dual", "primal_lin", "reg", "infeas"):
+            a, b = getattr(e1, key), getattr(e2, key)
+            assert abs(a - b) <= 1e-12 * max(1.0, abs(a)), key
+
+
+@pytest.mark.parametrize("weighted", [False, True])
 def test_gradient_is_central_difference(weighted):
     inst = _tiny()
     P = oracle.Problem(inst, weighted=weighted)
