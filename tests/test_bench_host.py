@@ -1,0 +1,45 @@
+"""Host logic of the benchmark that needs no GPU: the DRAM traffic it reports
+beside the roofline comes from a committed ncu capture.  It is scaled to a
+launch (the per-destination bytes fixed, the rest by the edges processed),
+and it is withheld when the capture no longer describes the kernel, the
+configuration or the tile shape."""
+import pytest
+
+import bench
+
+
+def test_traffic_scaling_keeps_the_destination_bytes_fixed():
+    cap = bench.PASS_TRAFFIC[("c2", "f32")]
+    if bench.kernel_code_hash() != bench.PASS_CODE_SHA256:
+        pytest.skip("the pass kernel changed since the capture: no traffic is reported")
+    # the captured case itself scales to its own bytes
+    assert bench.pass_traffic(cap["edges"], cap["J"], "c2", "f32") == pytest.approx(cap["bytes"])
+    # twice the edges with the same destinations: the per-destination part stays
+    two = bench.pass_traffic(2 * cap["edges"], cap["J"], "c2", "f32")
+    assert two == pytest.approx(2 * cap["bytes"] - 12 * cap["J"])
+    # the c2 launch: within 3 % of the algorithmic bytes (no re-reads)
+    E, I, J = 49_991_549, 1_000_000, 10_000
+    alg = 12 * E + 8 * (I + 1) + 12 * J
+    assert 0.97 < bench.pass_traffic(E, J, "c2", "f32") / alg < 1.03
+
+
+def test_traffic_is_withheld_when_the_capture_does_not_apply(monkeypatch):
+    # no capture for this configuration
+    assert bench.pass_traffic(10**6, 10**4, "c3", "f32") is None
+    # the batched recipe's capture predates its degree-ordered storage
+    assert bench.pass_traffic(10**9, 10**6, "c4", "f32", [3200, 128]) is None
+    # a changed kernel
+    monkeypatch.setattr(bench, "kernel_code_hash", lambda: "0" * 64)
+    assert bench.pass_traffic(10**8, 10**4, "c2", "f32") is None
+
+
+def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
+    src = tmp_path / "paper_2603_04621_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "pass.cu").write_text("int f() { return 1; }  // one\n\n// note\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h1 = bench.kernel_code_hash()
+    (src / "pass.cu").write_text("// header\nint f() { return 1; }  // two\n")
+    assert bench.kernel_code_hash() == h1
+    (src / "pass.cu").write_text("int f() { return 2; }\n")
+    assert bench.kernel_code_hash() != h1
