@@ -335,7 +335,9 @@ dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* 
  * momentum and stopping test use its own quantities only.
  *
  * Footprint estimate (bytes): E (4 + bytes(c, a)) + 8 (I + 4) + 16 tiles
- * + 56 J, plus 12 E while host inputs are staged at creation.
+ * + 56 J, plus 12 E while host inputs are staged at creation.  A request
+ * stored in degree order (see dualip_create) also holds 16 (I + 1) bytes of
+ * source map during its creation; the estimate leaves that out.
  */
 typedef struct dualip_server dualip_server;
 
