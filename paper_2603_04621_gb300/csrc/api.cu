@@ -72,49 +72,7 @@ cudaError_t configure_device_once(int device) {
 
 }  // namespace
 
-// Greedy tiling: consecutive whole sources while the edge count stays within
-// max_edges and the source count within max_sources; a source larger than
-// max_edges forms a tile of its own (projected from global memory).
-void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
-                 std::vector<int64_t>& tile_e, int64_t max_edges, int64_t max_sources) {
-  const int64_t I = (int64_t)off.size() - 1;
-  tiles.clear();
-  tile_e.clear();
-  int64_t s = 0;
-  while (s < I) {
-    tiles.push_back(s);
-    tile_e.push_back(off[s]);
-    int64_t e = 0, n = 0;
-    if (off[s + 1] - off[s] > max_edges) {
-      ++s;
-      continue;
-    }
-    while (s < I && n < max_sources && e + (off[s + 1] - off[s]) <= max_edges) {
-      e += off[s + 1] - off[s];
-      ++n;
-      ++s;
-    }
-  }
-  tiles.push_back(I);
-  tile_e.push_back(off[I]);
-}
-
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
-
-// Degrees spread widely when their standard deviation exceeds 0.3 of their
-// mean.  Such problems are stored in degree order (dualip_create).
-bool degrees_spread_widely(const std::vector<int64_t>& off) {
-  const int64_t I = (int64_t)off.size() - 1;
-  if (I < 2) return false;
-  double s1 = 0.0, s2 = 0.0;
-  for (int64_t i = 0; i < I; ++i) {
-    const double d = (double)(off[i + 1] - off[i]);
-    s1 += d;
-    s2 += d * d;
-  }
-  const double mean = s1 / (double)I, var = s2 / (double)I - mean * mean;
-  return mean > 0.0 && var > 0.09 * mean * mean;
-}
 
 namespace {
 
@@ -210,16 +168,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   // only the order of the objective's partial sums changes, and
   // dualip_get_primal maps x back to the caller's order.
   std::vector<int64_t> src_of, off_st;
-  if (degrees_spread_widely(off)) {
-    src_of.resize((size_t)I);
-    std::iota(src_of.begin(), src_of.end(), int64_t(0));
-    std::stable_sort(src_of.begin(), src_of.end(), [&](int64_t x, int64_t y) {
-      return off[x + 1] - off[x] < off[y + 1] - off[y];
-    });
-    off_st.resize((size_t)I + 1);
-    off_st[0] = 0;
-    for (int64_t i = 0; i < I; ++i) off_st[i + 1] = off_st[i] + (off[src_of[i] + 1] - off[src_of[i]]);
-  }
+  if (degrees_spread_widely(off)) degree_order(off, src_of, off_st);
   const bool seg = !src_of.empty();
   const std::vector<int64_t>& off_s = seg ? off_st : off;  // offsets as stored
 
@@ -245,7 +194,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     return bail(cuda_fail(e, "configuring the pass kernel"));
 
   std::vector<int64_t> tiles, tile_e;
-  build_tiles(off_s, tiles, tile_e, tile_edges_for(P.storage));
+  build_tiles(off_s, tiles, tile_e, tile_edges_for(P.storage), kTileSources);
   P.ntiles = (int64_t)tiles.size() - 1;
   P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P.num_sms, P.ntiles));
   P.h_mu = std::min(J, kMaxCachedDests);

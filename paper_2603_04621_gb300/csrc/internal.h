@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/dualip.h"
+#include "plan.h"
 #include <nvtx3/nvToolsExt.h>
 
 namespace dualip {
@@ -297,12 +298,7 @@ cudaError_t launch_absmax(const float* v, int64_t n, unsigned* out, cudaStream_t
 // solve.cu
 void solve_ctx_free(Problem& P);
 
-// api.cu helpers
-// Tiles of whole sources: runs with at most max_edges edges and max_sources
-// sources; a source larger than max_edges forms a tile of its own.
-void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
-                 std::vector<int64_t>& tile_e, int64_t max_edges = kTileEdges,
-                 int64_t max_sources = kTileSources);
+// api.cu helpers (the tiling and the degree order are in plan.h)
 cudaStream_t as_stream(void* s);
 // NVTX range for the lifetime of a scope (shown by profilers; nothing
 // happens without one attached).

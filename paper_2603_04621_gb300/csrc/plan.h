@@ -1,0 +1,75 @@
+// Host-side planning of a problem's stored layout (plain C++, no CUDA): the
+// degree order of the sources and the tiling of the source-major edge list.
+// dualip_create and the batched form use these; a CPU test compiles this
+// header on its own and checks the invariants stated below.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <numeric>
+#include <vector>
+
+namespace dualip {
+
+// Greedy tiling: consecutive whole sources while the edge count stays within
+// max_edges and the source count within max_sources; a source larger than
+// max_edges forms a tile of its own (projected from global memory).  On
+// return tiles[t] .. tiles[t+1]-1 are the sources of tile t and tile_e[t] its
+// first edge; tiles.back() = I and tile_e.back() = E.
+inline void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& tiles,
+                        std::vector<int64_t>& tile_e, int64_t max_edges, int64_t max_sources) {
+  const int64_t I = (int64_t)off.size() - 1;
+  tiles.clear();
+  tile_e.clear();
+  int64_t s = 0;
+  while (s < I) {
+    tiles.push_back(s);
+    tile_e.push_back(off[s]);
+    int64_t e = 0, n = 0;
+    if (off[s + 1] - off[s] > max_edges) {
+      ++s;
+      continue;
+    }
+    while (s < I && n < max_sources && e + (off[s + 1] - off[s]) <= max_edges) {
+      e += off[s + 1] - off[s];
+      ++n;
+      ++s;
+    }
+  }
+  tiles.push_back(I);
+  tile_e.push_back(off[I]);
+}
+
+// Degrees spread widely when their standard deviation exceeds 0.3 of their
+// mean.  Such problems are stored in degree order (dualip_create).
+inline bool degrees_spread_widely(const std::vector<int64_t>& off) {
+  const int64_t I = (int64_t)off.size() - 1;
+  if (I < 2) return false;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = 0; i < I; ++i) {
+    const double d = (double)(off[i + 1] - off[i]);
+    s1 += d;
+    s2 += d * d;
+  }
+  const double mean = s1 / (double)I, var = s2 / (double)I - mean * mean;
+  return mean > 0.0 && var > 0.09 * mean * mean;
+}
+
+// Degree order: src_of[i] is the caller's source stored at position i, by
+// increasing degree with ties in the caller's order; off_st are the stored
+// offsets (off_st[i+1] - off_st[i] = the degree of src_of[i]).
+inline void degree_order(const std::vector<int64_t>& off, std::vector<int64_t>& src_of,
+                         std::vector<int64_t>& off_st) {
+  const int64_t I = (int64_t)off.size() - 1;
+  src_of.resize((size_t)I);
+  std::iota(src_of.begin(), src_of.end(), int64_t(0));
+  std::stable_sort(src_of.begin(), src_of.end(), [&](int64_t x, int64_t y) {
+    return off[x + 1] - off[x] < off[y + 1] - off[y];
+  });
+  off_st.resize((size_t)I + 1);
+  off_st[0] = 0;
+  for (int64_t i = 0; i < I; ++i)
+    off_st[i + 1] = off_st[i] + (off[src_of[i] + 1] - off[src_of[i]]);
+}
+
+}  // namespace dualip

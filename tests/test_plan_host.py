@@ -1,0 +1,150 @@
+"""Host planning of the stored layout (paper_2603_04621_gb300/csrc/plan.h),
+compiled on its own with g++ (no CUDA): the greedy tiling of the
+source-major edge list, the degree-spread rule and the degree order.
+
+* Tiles cover the sources in order.  Each tile is a single oversized source,
+  or holds at most max_edges edges and max_sources sources.  It is greedy:
+  the next source would break a limit.
+* The spread rule is "standard deviation above 0.3 of the mean".
+* The degree order is a stable permutation by degree, and its offsets move
+  each source's edges as one segment.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2603_04621_gb300", "csrc")
+
+SHIM = r"""
+#include "plan.h"
+extern "C" {
+int64_t plan_tiles(const int64_t* off, int64_t I, int64_t max_e, int64_t max_s,
+                   int64_t* tiles, int64_t* tile_e, int64_t cap) {
+  std::vector<int64_t> o(off, off + I + 1), t, te;
+  dualip::build_tiles(o, t, te, max_e, max_s);
+  for (size_t k = 0; k < t.size() && (int64_t)k < cap; ++k) { tiles[k] = t[k]; tile_e[k] = te[k]; }
+  return (int64_t)t.size();
+}
+int plan_spread(const int64_t* off, int64_t I) {
+  return dualip::degrees_spread_widely(std::vector<int64_t>(off, off + I + 1)) ? 1 : 0;
+}
+void plan_degree_order(const int64_t* off, int64_t I, int64_t* src_of, int64_t* off_st) {
+  std::vector<int64_t> s, os;
+  dualip::degree_order(std::vector<int64_t>(off, off + I + 1), s, os);
+  for (int64_t i = 0; i < I; ++i) src_of[i] = s[i];
+  for (int64_t i = 0; i <= I; ++i) off_st[i] = os[i];
+}
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def plan(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ is not available")
+    d = tmp_path_factory.mktemp("plan")
+    src = d / "shim.cpp"
+    src.write_text(SHIM)
+    lib = d / "libplan.so"
+    subprocess.run([gxx, "-std=c++17", "-O2", "-shared", "-fPIC", "-I", CSRC, str(src), "-o",
+                    str(lib)], check=True)
+    L = ctypes.CDLL(str(lib))
+    p64 = ctypes.POINTER(ctypes.c_int64)
+    L.plan_tiles.argtypes = [p64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, p64, p64,
+                             ctypes.c_int64]
+    L.plan_tiles.restype = ctypes.c_int64
+    L.plan_spread.argtypes = [p64, ctypes.c_int64]
+    L.plan_spread.restype = ctypes.c_int
+    L.plan_degree_order.argtypes = [p64, ctypes.c_int64, p64, p64]
+    L.plan_degree_order.restype = None
+    return L
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def offsets(deg):
+    return np.concatenate([[0], np.cumsum(deg)]).astype(np.int64)
+
+
+def tiles_of(plan, off, max_e, max_s):
+    I = len(off) - 1
+    cap = I + 2
+    t = np.zeros(cap, np.int64)
+    te = np.zeros(cap, np.int64)
+    n = plan.plan_tiles(_p(off), I, max_e, max_s, _p(t), _p(te), cap)
+    assert n <= cap
+    return t[:n], te[:n]
+
+
+@pytest.mark.parametrize("law", ["poisson", "uniform", "with_giants", "zeros_and_ones"])
+def test_tiles_cover_in_order_within_limits_and_greedily(plan, law):
+    rng = np.random.default_rng({"poisson": 1, "uniform": 2, "with_giants": 3,
+                                 "zeros_and_ones": 4}[law])
+    if law == "poisson":
+        deg = rng.poisson(50, 20_000)
+    elif law == "uniform":
+        deg = rng.integers(5, 101, 20_000)
+    elif law == "with_giants":
+        deg = rng.poisson(80, 5_000)
+        deg[rng.choice(5_000, 40, replace=False)] = rng.integers(3_201, 20_000, 40)
+    else:
+        deg = rng.integers(0, 2, 30_000)
+    off = offsets(deg)
+    max_e, max_s = 3_200, 256
+    t, te = tiles_of(plan, off, max_e, max_s)
+    I = len(deg)
+    assert t[0] == 0 and t[-1] == I and np.all(np.diff(t) >= 1)
+    assert np.array_equal(te, off[t])
+    for a, b in zip(t[:-1], t[1:]):
+        e = off[b] - off[a]
+        if b - a == 1 and deg[a] > max_e:
+            continue  # an oversized source alone
+        assert e <= max_e and b - a <= max_s
+        assert np.all(deg[a:b] <= max_e)
+        if b < I:  # greedy: the next source would break a limit, or is oversized
+            assert b - a == max_s or e + deg[b] > max_e
+
+
+def test_spread_rule_is_a_coefficient_of_variation_above_0_3(plan):
+    rng = np.random.default_rng(5)
+    cases = {
+        "poisson50": rng.poisson(50, 50_000),
+        "uniform5_100": rng.integers(5, 101, 50_000),
+        "constant": np.full(1_000, 10),
+        "one_source": np.array([7]),
+        "all_empty": np.zeros(100, np.int64),
+        "two_levels": np.repeat([10, 20], 500),
+    }
+    for name, deg in cases.items():
+        off = offsets(deg)
+        d = deg.astype(np.float64)
+        expect = len(d) >= 2 and d.mean() > 0 and d.var() > 0.09 * d.mean() ** 2
+        assert plan.plan_spread(_p(off), len(deg)) == int(expect), name
+    # the workload laws on either side of the rule
+    assert plan.plan_spread(_p(offsets(cases["poisson50"])), 50_000) == 0
+    assert plan.plan_spread(_p(offsets(cases["uniform5_100"])), 50_000) == 1
+
+
+def test_degree_order_is_a_stable_permutation_with_consistent_offsets(plan):
+    rng = np.random.default_rng(6)
+    deg = rng.integers(0, 12, 5_000)
+    off = offsets(deg)
+    I = len(deg)
+    src = np.zeros(I, np.int64)
+    off_st = np.zeros(I + 1, np.int64)
+    plan.plan_degree_order(_p(off), I, _p(src), _p(off_st))
+    assert np.array_equal(np.sort(src), np.arange(I))
+    assert np.array_equal(src, np.argsort(deg, kind="stable"))  # ties keep the caller's order
+    assert np.all(np.diff(deg[src]) >= 0)
+    assert np.array_equal(np.diff(off_st), deg[src]) and off_st[-1] == off[-1]
+    # moving each source's segment to its stored place is a bijection of the edges
+    edge_of = np.concatenate([np.arange(off[s], off[s + 1]) for s in src])
+    assert np.array_equal(np.sort(edge_of), np.arange(off[-1]))
