@@ -42,6 +42,27 @@ def test_binding_lists_every_declared_symbol():
     assert sorted(d.EXPORTS) == _declared()
 
 
+def _prototypes():
+    """name -> parameter count of every function declared in the header."""
+    src = open(os.path.join(ROOT, "include", "dualip.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(dualip_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argtypes_match_the_prototypes():
+    import paper_2603_04621_gb300 as d
+
+    L = d.lib()
+    protos = _prototypes()
+    assert sorted(protos) == _declared()
+    for name, n in protos.items():
+        assert len(getattr(L, name).argtypes) == n, name
+
+
 def test_last_error_is_empty_string_initially(libdualip):
     libdualip.dualip_last_error.restype = ctypes.c_char_p
     assert libdualip.dualip_last_error() == b""
