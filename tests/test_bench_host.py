@@ -43,3 +43,33 @@ def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
     assert bench.kernel_code_hash() == h1
     (src / "pass.cu").write_text("int f() { return 2; }\n")
     assert bench.kernel_code_hash() != h1
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` times the oracle on the host cores and prints
+    one JSON line with the main arm's metric, unit and direction."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3", "--scale", "0.01"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference"
+    assert out["metric"] == bench.METRIC and out["unit"] == bench.UNIT
+    assert out["higher_is_better"] is True and out["vs_baseline"] is None
+    assert out["n_gpus"] == 1 and out["steps"] == 1 and out["warmup"] == 3
+    assert out["value"] > 0 and out["ms_per_step"] > 0
+    assert out["data"] == "synthetic" and "workload" in out["config"]
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == out["value"]
+    assert cb["unit"] == out["unit"] and cb["sample"]
+    e2e = out["e2e"]
+    assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
