@@ -57,15 +57,26 @@ inline bool degrees_spread_widely(const std::vector<int64_t>& off) {
 
 // Degree order: src_of[i] is the caller's source stored at position i, by
 // increasing degree with ties in the caller's order; off_st are the stored
-// offsets (off_st[i+1] - off_st[i] = the degree of src_of[i]).
+// offsets (off_st[i+1] - off_st[i] = the degree of src_of[i]).  A counting
+// sort by degree (stable, O(I + max degree)) gives the order; when the
+// largest degree exceeds 4 I + 1024 a comparison sort gives the same one.
 inline void degree_order(const std::vector<int64_t>& off, std::vector<int64_t>& src_of,
                          std::vector<int64_t>& off_st) {
   const int64_t I = (int64_t)off.size() - 1;
   src_of.resize((size_t)I);
-  std::iota(src_of.begin(), src_of.end(), int64_t(0));
-  std::stable_sort(src_of.begin(), src_of.end(), [&](int64_t x, int64_t y) {
-    return off[x + 1] - off[x] < off[y + 1] - off[y];
-  });
+  int64_t dmax = 0;
+  for (int64_t i = 0; i < I; ++i) dmax = std::max(dmax, off[i + 1] - off[i]);
+  if (dmax <= 4 * I + 1024) {
+    std::vector<int64_t> start((size_t)dmax + 2, 0);  // start[d + 1]: sources of degree d
+    for (int64_t i = 0; i < I; ++i) ++start[(size_t)(off[i + 1] - off[i]) + 1];
+    for (int64_t d = 0; d <= dmax; ++d) start[(size_t)d + 1] += start[(size_t)d];
+    for (int64_t i = 0; i < I; ++i) src_of[(size_t)start[(size_t)(off[i + 1] - off[i])]++] = i;
+  } else {
+    std::iota(src_of.begin(), src_of.end(), int64_t(0));
+    std::stable_sort(src_of.begin(), src_of.end(), [&](int64_t x, int64_t y) {
+      return off[x + 1] - off[x] < off[y + 1] - off[y];
+    });
+  }
   off_st.resize((size_t)I + 1);
   off_st[0] = 0;
   for (int64_t i = 0; i < I; ++i)

@@ -133,9 +133,13 @@ def test_spread_rule_is_a_coefficient_of_variation_above_0_3(plan):
     assert plan.plan_spread(_p(offsets(cases["uniform5_100"])), 50_000) == 1
 
 
-def test_degree_order_is_a_stable_permutation_with_consistent_offsets(plan):
+@pytest.mark.parametrize("case", ["counting", "comparison"])
+def test_degree_order_is_a_stable_permutation_with_consistent_offsets(plan, case):
     rng = np.random.default_rng(6)
     deg = rng.integers(0, 12, 5_000)
+    if case == "comparison":  # a degree above 4 I + 1024 takes the comparison sort
+        deg[17] = 4 * len(deg) + 5_000
+        deg[4_000] = deg[17]  # a tie among the giants keeps the caller's order
     off = offsets(deg)
     I = len(deg)
     src = np.zeros(I, np.int64)
