@@ -1005,38 +1005,15 @@ dualip_status dualip_batch_autotune(dualip_batch* b, dualip_autotune_result* res
   int64_t nsrc = 0, nedge = 0;
   for (int k = 0; k < B.n; ++k) {
     const std::vector<int64_t>& off = B.prob[k]->off_host;
-    for (size_t i = 0; i + 1 < off.size(); ++i) {
-      const int64_t d = off[i + 1] - off[i];
-      int bk = 0;
-      while (bk < 31 && (int64_t(2) << bk) <= d) ++bk;
-      ++r.degree_hist[bk];
-    }
+    for (size_t i = 0; i + 1 < off.size(); ++i) ++r.degree_hist[degree_bucket(off[i + 1] - off[i])];
     nsrc += (int64_t)off.size() - 1;
     nedge += off.empty() ? 0 : off.back();
   }
-  // the degree below which 99% of the sources lie (bucket upper bound)
-  int64_t p99 = 1, acc = 0;
-  for (int bk = 0; bk < 32; ++bk) {
-    acc += r.degree_hist[bk];
-    if (acc >= nsrc - nsrc / 100) {
-      p99 = int64_t(2) << bk;
-      break;
-    }
-  }
-  const double mean = nsrc ? (double)nedge / (double)nsrc : 1.0;
-  // candidates: a shape is dropped when most of its tiles would hold a single
-  // source (p99 degree above half the edge budget) or when its source cap
-  // would stop tiles at under a quarter of the edge budget
+  // candidate shapes, pruned by the degree histogram (plan.h)
   const int32_t emax = tile_edges_for(B.storage);
   const int32_t cand[][2] = {{emax, 256}, {emax, 128}, {2048, 256}, {2048, 128},
                              {1536, 128}, {1024, 128}, {1024, 64},   {512, 64}};
-  std::vector<int> keep;
-  for (int c = 0; c < 8; ++c) {
-    const double e = cand[c][0], src = cand[c][1];
-    if (p99 > e / 2 && c != 0) continue;
-    if (src * mean < e / 4 && c != 0) continue;
-    keep.push_back(c);
-  }
+  const std::vector<int> keep = prune_shapes(r.degree_hist, nsrc, nedge, cand, 8);
   dualip_status st = DUALIP_OK;
   std::vector<float*> bufs(2, nullptr);
   int64_t Jt = 0;

@@ -83,4 +83,42 @@ inline void degree_order(const std::vector<int64_t>& off, std::vector<int64_t>& 
     off_st[i + 1] = off_st[i] + (off[src_of[i] + 1] - off[src_of[i]]);
 }
 
+// Autotuner histogram bucket of a degree: 0 for degrees 0 and 1, else k for
+// [2^k, 2^(k+1)), at most 31.
+inline int degree_bucket(int64_t d) {
+  int bk = 0;
+  while (bk < 31 && (int64_t(2) << bk) <= d) ++bk;
+  return bk;
+}
+
+// The degree below which 99% of the sources lie, as the upper bound of its
+// histogram bucket (with no sources, bucket 0's bound: 2).
+inline int64_t degree_p99(const int64_t hist[32], int64_t nsrc) {
+  int64_t acc = 0;
+  for (int bk = 0; bk < 32; ++bk) {
+    acc += hist[bk];
+    if (acc >= nsrc - nsrc / 100) return int64_t(2) << bk;
+  }
+  return 1;
+}
+
+// Tile shapes worth timing: candidate c = (edges, sources) is dropped when
+// most of its tiles would hold a single source (p99 degree above half the
+// edge budget), or when its source cap would stop tiles at under a quarter
+// of the edge budget (sources x mean degree).  The first candidate is always
+// kept.  Returns the indices kept, in order.
+inline std::vector<int> prune_shapes(const int64_t hist[32], int64_t nsrc, int64_t nedge,
+                                     const int32_t (*cand)[2], int ncand) {
+  const int64_t p99 = degree_p99(hist, nsrc);
+  const double mean = nsrc ? (double)nedge / (double)nsrc : 1.0;
+  std::vector<int> keep;
+  for (int c = 0; c < ncand; ++c) {
+    const double e = cand[c][0], src = cand[c][1];
+    if (p99 > e / 2 && c != 0) continue;
+    if (src * mean < e / 4 && c != 0) continue;
+    keep.push_back(c);
+  }
+  return keep;
+}
+
 }  // namespace dualip

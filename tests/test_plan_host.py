@@ -8,6 +8,10 @@ source-major edge list, the degree-spread rule and the degree order.
 * The spread rule is "standard deviation above 0.3 of the mean".
 * The degree order is a stable permutation by degree, and its offsets move
   each source's edges as one segment.
+* The autotuner's histogram buckets are [2^k, 2^(k+1)) (0 and 1 in bucket 0);
+  its 99th-percentile degree is a bucket's upper bound; and it times only the
+  shapes that neither make most tiles single-source nor cap tiles at under a
+  quarter of their edge budget.
 """
 import ctypes
 import os
@@ -32,6 +36,15 @@ int64_t plan_tiles(const int64_t* off, int64_t I, int64_t max_e, int64_t max_s,
 }
 int plan_spread(const int64_t* off, int64_t I) {
   return dualip::degrees_spread_widely(std::vector<int64_t>(off, off + I + 1)) ? 1 : 0;
+}
+int plan_bucket(int64_t d) { return dualip::degree_bucket(d); }
+int64_t plan_p99(const int64_t* hist, int64_t nsrc) { return dualip::degree_p99(hist, nsrc); }
+int plan_prune(const int64_t* hist, int64_t nsrc, int64_t nedge, const int32_t* cand, int ncand,
+               int* keep) {
+  std::vector<int> k = dualip::prune_shapes(hist, nsrc, nedge,
+                                            reinterpret_cast<const int32_t (*)[2]>(cand), ncand);
+  for (size_t i = 0; i < k.size(); ++i) keep[i] = k[i];
+  return (int)k.size();
 }
 void plan_degree_order(const int64_t* off, int64_t I, int64_t* src_of, int64_t* off_st) {
   std::vector<int64_t> s, os;
@@ -61,6 +74,14 @@ def plan(tmp_path_factory):
     L.plan_tiles.restype = ctypes.c_int64
     L.plan_spread.argtypes = [p64, ctypes.c_int64]
     L.plan_spread.restype = ctypes.c_int
+    L.plan_bucket.argtypes = [ctypes.c_int64]
+    L.plan_bucket.restype = ctypes.c_int
+    L.plan_p99.argtypes = [p64, ctypes.c_int64]
+    L.plan_p99.restype = ctypes.c_int64
+    L.plan_prune.argtypes = [p64, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int)]
+    L.plan_prune.restype = ctypes.c_int
     L.plan_degree_order.argtypes = [p64, ctypes.c_int64, p64, p64]
     L.plan_degree_order.restype = None
     return L
@@ -152,3 +173,46 @@ def test_degree_order_is_a_stable_permutation_with_consistent_offsets(plan, case
     # moving each source's segment to its stored place is a bijection of the edges
     edge_of = np.concatenate([np.arange(off[s], off[s + 1]) for s in src])
     assert np.array_equal(np.sort(edge_of), np.arange(off[-1]))
+
+
+def test_histogram_buckets_and_p99(plan):
+    for d, bk in ((0, 0), (1, 0), (2, 1), (3, 1), (4, 2), (63, 5), (64, 6), (2**31, 31),
+                  (2**40, 31)):
+        assert plan.plan_bucket(d) == bk, d
+    rng = np.random.default_rng(7)
+    deg = rng.integers(5, 101, 100_000)
+    hist = np.bincount([plan.plan_bucket(int(x)) for x in deg], minlength=32).astype(np.int64)
+    p99 = plan.plan_p99(_p(hist), len(deg))
+    q = np.quantile(deg, 0.99)
+    assert p99 // 2 <= q < p99  # the bucket holding the 99th percentile, by its upper bound
+    assert plan.plan_p99(_p(np.zeros(32, np.int64)), 0) == 2  # no sources: bucket 0's bound
+
+
+CANDS = [(3200, 256), (3200, 128), (2048, 256), (2048, 128), (1536, 128), (1024, 128),
+         (1024, 64), (512, 64)]
+
+
+def kept(plan, deg):
+    hist = np.bincount([plan.plan_bucket(int(x)) for x in deg], minlength=32).astype(np.int64)
+    cand = np.array(CANDS, dtype=np.int32).ravel()
+    keep = (ctypes.c_int * 8)()
+    n = plan.plan_prune(_p(hist), len(deg), int(np.sum(deg)),
+                        cand.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 8, keep)
+    return list(keep[:n]), plan.plan_p99(_p(hist), len(deg)), float(np.mean(deg))
+
+
+@pytest.mark.parametrize("law", ["c4", "tiny", "huge"])
+def test_shape_pruning_rule(plan, law):
+    rng = np.random.default_rng(8)
+    deg = {"c4": rng.integers(5, 101, 50_000), "tiny": rng.integers(1, 3, 50_000),
+           "huge": rng.integers(2_000, 5_000, 5_000)}[law]
+    keep, p99, mean = kept(plan, deg)
+    expect = [c for c, (e, s) in enumerate(CANDS)
+              if c == 0 or not (p99 > e / 2 or s * mean < e / 4)]
+    assert keep == expect
+    if law == "c4":  # moderate degrees: every shape is worth timing
+        assert keep == list(range(8))
+    if law == "huge":  # most tiles would hold one source: only the default shape
+        assert keep == [0]
+    if law == "tiny":  # small source caps would stop tiles early: they go
+        assert 1 not in keep and 7 not in keep
