@@ -121,4 +121,27 @@ inline std::vector<int> prune_shapes(const int64_t hist[32], int64_t nsrc, int64
   return keep;
 }
 
+// Serving admission.  Resident footprint of a request (bytes): its edges
+// (4 bytes of dst plus the stored c and a), offsets, tiles and J-length
+// arrays; the transient is the staging of host inputs during creation.
+inline int64_t request_resident_bytes(int64_t I, int64_t E, int64_t J, bool bf16) {
+  const int64_t eb = bf16 ? 8 : 12;
+  return eb * (E + 8) + 8 * (I + 4) + 16 * (E / 1024 + I / 256 + 2) + 56 * J;
+}
+inline int64_t request_transient_bytes(int64_t E, bool inputs_on_device) {
+  return inputs_on_device ? 0 : 12 * E;
+}
+
+// The head of the queue is admitted when a slot of its kind is free and its
+// footprint and transient fit the budget beside what is resident; it is
+// rejected when it cannot fit even with nothing resident; else it waits.
+enum class Admission { kAdmit, kWait, kReject };
+inline Admission admission(int64_t resident, int64_t footprint, int64_t transient, int64_t budget,
+                           bool slot_free) {
+  const bool fits = resident + footprint + transient <= budget;
+  if (slot_free && fits) return Admission::kAdmit;
+  if (!fits && resident == 0) return Admission::kReject;
+  return Admission::kWait;
+}
+
 }  // namespace dualip

@@ -48,12 +48,11 @@ struct Request {
 };
 
 int64_t resident_bytes(const dualip_problem_desc& d) {
-  const int64_t E = d.num_edges, I = d.num_sources, J = d.num_dests;
-  const int64_t eb = d.storage == DUALIP_EDGE_BF16 ? 8 : 12;
-  return eb * (E + 8) + 8 * (I + 4) + 16 * (E / 1024 + I / 256 + 2) + 56 * J;
+  return request_resident_bytes(d.num_sources, d.num_edges, d.num_dests,
+                                d.storage == DUALIP_EDGE_BF16);
 }
 int64_t transient_bytes(const dualip_problem_desc& d) {
-  return d.inputs_on_device ? 0 : 12 * d.num_edges;
+  return request_transient_bytes(d.num_edges, d.inputs_on_device != 0);
 }
 
 }  // namespace
@@ -107,10 +106,10 @@ void Server::admit_loop() {
         if (stop) return;
         if (!queue.empty()) {
           Request& r = reqs[queue.front()];
-          const bool slot_free = slots_used[r.kind] < o.max_slots;
-          const bool fits = resident + r.footprint + r.transient <= o.hbm_budget_bytes;
-          if (slot_free && fits) break;
-          if (!fits && resident == 0) {  // can never fit
+          const Admission a = admission(resident, r.footprint, r.transient, o.hbm_budget_bytes,
+                                        slots_used[r.kind] < o.max_slots);
+          if (a == Admission::kAdmit) break;
+          if (a == Admission::kReject) {  // can never fit
             r.status = DUALIP_ENOMEM;
             r.error = "the request's footprint exceeds the HBM budget";
             r.state = DUALIP_REQ_FAILED;

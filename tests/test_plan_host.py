@@ -12,6 +12,8 @@ source-major edge list, the degree-spread rule and the degree order.
   its 99th-percentile degree is a bucket's upper bound; and it times only the
   shapes that neither make most tiles single-source nor cap tiles at under a
   quarter of their edge budget.
+* Serving admission: the footprint estimate of the header, and the head of
+  the queue admitted, kept waiting or rejected.
 """
 import ctypes
 import os
@@ -45,6 +47,16 @@ int plan_prune(const int64_t* hist, int64_t nsrc, int64_t nedge, const int32_t* 
                                             reinterpret_cast<const int32_t (*)[2]>(cand), ncand);
   for (size_t i = 0; i < k.size(); ++i) keep[i] = k[i];
   return (int)k.size();
+}
+int64_t plan_resident(int64_t I, int64_t E, int64_t J, int bf16) {
+  return dualip::request_resident_bytes(I, E, J, bf16 != 0);
+}
+int64_t plan_transient(int64_t E, int on_device) {
+  return dualip::request_transient_bytes(E, on_device != 0);
+}
+int plan_admission(int64_t resident, int64_t footprint, int64_t transient, int64_t budget,
+                   int slot_free) {
+  return (int)dualip::admission(resident, footprint, transient, budget, slot_free != 0);
 }
 void plan_degree_order(const int64_t* off, int64_t I, int64_t* src_of, int64_t* off_st) {
   std::vector<int64_t> s, os;
@@ -82,6 +94,13 @@ def plan(tmp_path_factory):
                              ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
                              ctypes.POINTER(ctypes.c_int)]
     L.plan_prune.restype = ctypes.c_int
+    i64 = ctypes.c_int64
+    L.plan_resident.argtypes = [i64, i64, i64, ctypes.c_int]
+    L.plan_resident.restype = i64
+    L.plan_transient.argtypes = [i64, ctypes.c_int]
+    L.plan_transient.restype = i64
+    L.plan_admission.argtypes = [i64, i64, i64, i64, ctypes.c_int]
+    L.plan_admission.restype = ctypes.c_int
     L.plan_degree_order.argtypes = [p64, ctypes.c_int64, p64, p64]
     L.plan_degree_order.restype = None
     return L
@@ -216,3 +235,25 @@ def test_shape_pruning_rule(plan, law):
         assert keep == [0]
     if law == "tiny":  # small source caps would stop tiles early: they go
         assert 1 not in keep and 7 not in keep
+
+
+def test_request_footprint_estimate(plan):
+    I, E, J = 800_000, 32_000_000, 26_000
+    tiles = E // 1024 + I // 256 + 2
+    # E (4 + bytes of c and a) + 8 (I + 4) + 16 tiles + 56 J, with 8 edges of padding
+    assert plan.plan_resident(I, E, J, 0) == 12 * (E + 8) + 8 * (I + 4) + 16 * tiles + 56 * J
+    assert plan.plan_resident(I, E, J, 1) == 8 * (E + 8) + 8 * (I + 4) + 16 * tiles + 56 * J
+    assert plan.plan_transient(E, 0) == 12 * E and plan.plan_transient(E, 1) == 0
+
+
+ADMIT, WAIT, REJECT = 0, 1, 2
+
+
+def test_admission_rule(plan):
+    a = plan.plan_admission
+    assert a(0, 60, 30, 100, 1) == ADMIT        # fits with its transient
+    assert a(0, 60, 50, 100, 1) == REJECT       # never fits, even alone
+    assert a(0, 60, 50, 100, 0) == REJECT       # no slot changes that
+    assert a(20, 60, 30, 100, 1) == WAIT        # fits once something leaves
+    assert a(10, 60, 30, 100, 0) == WAIT        # fits, but no slot of its kind is free
+    assert a(10, 60, 30, 100, 1) == ADMIT       # exactly at the budget
