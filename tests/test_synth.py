@@ -89,3 +89,24 @@ def test_subset_sources_picks_exactly_those_sources():
         assert np.array_equal(sub.c[sub.off[k]:sub.off[k + 1]], c)
     empty = inst.subset_sources(np.array([], dtype=np.int64))
     assert empty.I == 0 and empty.E == 0
+
+
+def test_batched_and_request_degree_laws():
+    # c4 instances: degrees UniformInt[5,100] clipped to J
+    inst = synth.batch_instance(40_000, 5_000, 123)
+    deg = np.diff(inst.off)
+    assert deg.min() >= 5 and deg.max() <= 100
+    assert abs(deg.mean() - 52.5) < 0.5
+    counts = np.bincount(deg, minlength=101)[5:101]
+    assert counts.min() > 0.8 * counts.mean()  # flat over 5..100
+    small = synth.batch_instance(2_000, 12, 124)  # J = 12 clips most degrees
+    d = np.diff(small.off)
+    assert d.max() <= 12 and np.mean(d == 12) > 0.9
+    # c5 requests: degrees Poisson(40) clipped to [1, J]
+    req = dict(t=0.0, I=30_000, J=2_000, seed=7_000_001, storage="f32")
+    deg = np.diff(synth.request_instance(req).off).astype(np.float64)
+    assert abs(deg.mean() - 40.0) < 0.3 and abs(deg.var() / 40.0 - 1.0) < 0.06
+    assert deg.min() >= 1 and deg.max() <= 2_000
+    # the degree spread of the two laws: c4's is about 0.53, c5's about 0.16
+    assert 0.5 < np.std(np.diff(inst.off)) / np.mean(np.diff(inst.off)) < 0.56
+    assert 0.14 < deg.std() / deg.mean() < 0.18
