@@ -54,6 +54,30 @@ def _brute_force_projection(r, alpha):
 
 
 @pytest.mark.parametrize("method", ["sort", "michelot"])
+def test_projection_lone_candidate(method):
+    """x = alpha (r - t)_+ with sum x <= 1 (Eqs. 4-5).  If r_1 >= 1/alpha_1 and
+    every other r_e <= r_1 - 1/alpha_1, the threshold t = r_1 - 1/alpha_1 >= 0
+    meets the KKT conditions with x_1 = 1 and x_e = 0 for e > 1.  Once a runner-up
+    passes that bound, it takes mass and x_1 < 1."""
+    rng = np.random.default_rng(17)
+    for _ in range(300):
+        d = int(rng.integers(1, 12))
+        al = rng.uniform(0.2, 5.0, d)
+        t = rng.uniform(0.0, 2.0)
+        r = np.empty(d)
+        r[0] = t + 1.0 / al[0]
+        r[1:] = t - rng.uniform(1e-9, 3.0, d - 1)
+        x, tau = oracle.project(r, al, method)
+        assert x[0] == pytest.approx(1.0, abs=1e-14) and np.all(x[1:] == 0.0)
+        assert tau == pytest.approx(t, abs=1e-12)
+        if d > 1:
+            r2 = r.copy()
+            r2[1] = t + 1e-3
+            x2, _ = oracle.project(r2, al, method)
+            assert x2[1] > 0.0 and x2[0] < 1.0 and x2.sum() == pytest.approx(1.0, abs=1e-13)
+
+
+@pytest.mark.parametrize("method", ["sort", "michelot"])
 def test_projection_closed_forms(method):
     # d = 1: x = clamp(r * alpha, 0, 1)
     for r in (-2.0, 0.0, 0.3, 0.99, 1.0, 7.5):
