@@ -234,7 +234,12 @@ dualip_status dualip_solve(dualip_problem* p, const dualip_solve_opts* opts, flo
  * shares the array (it is cleared at the start of each call), so calls whose
  * work overlaps on the GPU race: serialise them.  Nothing is synchronised;
  * an edge whose destination is outside [0, J) is skipped and turns every
- * scalar in out_dev into NaN.  The offsets are trusted as given.
+ * entry of grad and every scalar in out_dev into NaN.  The offsets are
+ * trusted as given.  A x is summed with FP64 atomics in arrival order, so
+ * repeated calls on the same inputs may differ in the last bits (the handle
+ * path's A x is exact and reproducible).  The scratch address is looked up
+ * once per device and process: do not call this entry point again after a
+ * device reset (cudaDeviceReset or a primary-context reset) in that process.
  */
 dualip_status dualip_dual_grad_noalloc(int64_t num_sources, int32_t num_dests,
                                        const int64_t* src_offsets, const int32_t* dst,

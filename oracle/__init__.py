@@ -165,7 +165,7 @@ class Problem:
         return Eval(float(sc[0]), float(sc[1]), float(sc[2]), float(sc[3]), float(sc[4]), grad,
                     ax, x)
 
-    def solve(self, lam0=None, gamma0=0.1, gamma_final=1e-3, halve_every=25, max_step=0.1,
+    def solve(self, lam0=None, gamma0=0.1, gamma_final=1e-3, halve_every=25, max_step=10.0,
               init_step=1e-5, max_iters=2000, tol_gap=1e-4, tol_infeas=1e-4, check_every=10,
               row_normalize=True, restart=True, stop_on_tol=True, want_trace=False):
         o = SolveOpts(gamma0, gamma_final, halve_every, max_step, init_step, max_iters, tol_gap,

@@ -24,7 +24,13 @@
 //  * results are the same quantities as dualip_dual_grad (Section 3.1, Eq. 2
 //    and Danskin's gradient), computed by a simpler kernel (one warp per
 //    source reading global memory, FP64 atomics for A x), so they agree with
-//    the handle-based path within rounding, not bit for bit.
+//    the handle-based path within rounding, not bit for bit.  The FP64
+//    atomics add in whatever order the warps reach them, so two calls on the
+//    same inputs may differ in the last bits;
+//  * the cached scratch address belongs to the CUDA context it was looked up
+//    in: after a device reset (cudaDeviceReset, or a reset of the primary
+//    context by another component of the process) this entry point must not
+//    be called again in the same process.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -223,10 +229,13 @@ __global__ void __launch_bounds__(kNaThreads) na_pass_kernel(NaParams p) {
 // in a fixed order and writes out[0..4].
 __global__ void __launch_bounds__(kNaThreads) na_epilogue_kernel(NaParams p, int npart) {
   double s_mug = 0.0, s_inf = 0.0;
+  // an edge with a destination outside [0, J) was skipped by the pass: every
+  // output is then marked invalid, the gradient as well as the scalars
+  const bool bad = *reinterpret_cast<volatile unsigned*>(p.bad) != 0u;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < p.J;
        j += (int64_t)gridDim.x * blockDim.x) {
     const double gj = p.y[j] - (double)p.b[j];
-    p.grad[j] = (float)gj;
+    p.grad[j] = bad ? CUDART_NAN_F : (float)gj;
     s_mug += (double)p.lambda[j] * gj;
     if (gj > 0.0) s_inf += gj * gj;
   }

@@ -158,11 +158,22 @@ void Server::run_chunks() {
     Batch& B = batch[k];
     if (!batch_ok[k]) continue;
     bool any = false;
-    for (int s = 0; s < B.n; ++s) any = any || B.active[s];
+    // a chunk runs check_every iterations, or fewer when a request has fewer
+    // left before its max_iters (so that no request runs past it)
+    int n_it = o.check_every;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (int s = 0; s < B.n; ++s) {
+        if (!B.active[s]) continue;
+        any = true;
+        const Request& r = reqs[slot_ticket[k][s]];
+        n_it = std::min(n_it, std::max(1, r.opts.max_iters - r.iters));
+      }
+    }
     if (!any) continue;
     const double c0 = now();
     cudaError_t e = rebuild_lists(B);
-    if (!e) e = run_batch_chunk(B, o.check_every, true);
+    if (!e) e = run_batch_chunk(B, n_it, n_it == o.check_every);
     if (!e) e = batch_read_state(B);
     dualip_status st = e ? cuda_fail(e, "running a serving chunk") : batch_status(B);
     {
@@ -179,10 +190,10 @@ void Server::run_chunks() {
       {
         std::lock_guard<std::mutex> lk(mu);
         rp = &reqs[t];
-        rp->iters += o.check_every;
+        rp->iters += n_it;
         iters = rp->iters;
         cancelled = rp->cancel;
-        slot_iters += o.check_every;
+        slot_iters += n_it;
       }
       Request& r = *rp;  // the fields below are written by this thread only
       const SlotSolve& S = B.h_ss[s];

@@ -321,13 +321,20 @@ static cudaError_t ensure_row_scale(Problem& P, SolveCtx& C, int row_normalize, 
   return cudaSuccess;
 }
 
-static cudaError_t enqueue_iteration(Problem& P, SolveCtx& C, cudaStream_t s) {
+// prof: record the handle's timing events (dualip_profile_enable) around the
+// pass and the epilogue; only outside graph capture.
+static cudaError_t enqueue_iteration(Problem& P, SolveCtx& C, cudaStream_t s, bool prof) {
   Vecs v{C.lam, C.y, C.yp, C.G, C.Gp, C.D};
   cudaError_t e;
+  cudaEvent_t* ev = nullptr;
+  if (prof && P.prof_used < P.prof_max) ev = &P.prof_ev[4 * (size_t)P.prof_used++];
   // mu and gamma of this iteration come from the previous one (or the prep
   // before the first); every kernel waits for its predecessor's writes
+  if (ev && ((e = cudaEventRecord(ev[0], s)) || (e = cudaEventRecord(ev[1], s)))) return e;
   if ((e = launch_pass(P, &C.st->gamma_f, 0.f, nullptr, s))) return e;
+  if (ev && (e = cudaEventRecord(ev[2], s))) return e;
   if ((e = launch_epilogue(P, C.D, C.G, &C.st->gamma_f, 0.0, C.st->eval, s, true))) return e;
+  if (ev && (e = cudaEventRecord(ev[3], s))) return e;
   if ((e = launch_pdl(solve_norms_kernel, dim3(C.blocks), dim3(256), 0, s, P.J, C.st, v,
                       C.part)))
     return e;
@@ -344,7 +351,7 @@ static cudaError_t run_chunk(Problem& P, SolveCtx& C, int n, bool use_graph) {
       cudaGraph_t g = nullptr;
       if ((e = cudaStreamBeginCapture(C.stream, cudaStreamCaptureModeThreadLocal))) return e;
       for (int i = 0; i < n; ++i) {
-        e = enqueue_iteration(P, C, C.stream);
+        e = enqueue_iteration(P, C, C.stream, false);
         if (e) break;
       }
       cudaError_t e2 = cudaStreamEndCapture(C.stream, &g);
@@ -361,7 +368,7 @@ static cudaError_t run_chunk(Problem& P, SolveCtx& C, int n, bool use_graph) {
     return cudaGraphLaunch(C.graph, C.stream);
   }
   for (int i = 0; i < n; ++i)
-    if ((e = enqueue_iteration(P, C, C.stream))) return e;
+    if ((e = enqueue_iteration(P, C, C.stream, true))) return e;
   return cudaSuccess;
 }
 

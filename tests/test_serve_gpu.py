@@ -73,11 +73,28 @@ def test_alone_equals_in_mix(dl):
     assert stats["done"] == len(insts) and stats["failed"] == 0
     # it overlapped with the others: admitted before some of them finished
     assert any(r[0]["t_done"] > mixed["t_admit"] for r in rest)
+    # its step, momentum and stopping test use its own quantities only, and its
+    # gradients are exact, so it stops at the same check with the same lambda
     assert mixed["converged"] == alone["converged"]
-    if mixed["iters"] == alone["iters"]:
-        assert np.array_equal(lam_alone, lam_mixed)
+    assert mixed["iters"] == alone["iters"]
+    assert np.array_equal(lam_alone, lam_mixed)
     for key in ("dual_obj", "primal_obj", "reg", "lambda_dot_grad"):
         assert abs(mixed[key] - alone[key]) <= 1e-6 * max(1.0, abs(alone[key])), key
+
+
+def test_max_iters_not_a_multiple_of_the_chunk(dl):
+    """A request whose max_iters is not a multiple of the server's chunk length
+    stops at exactly max_iters, alone and beside a request with a longer run."""
+    insts, _ = requests(2, seed=55)
+    srv = dl.Server(64 * GIB, max_slots=8, check_every=10)
+    t_long = srv.submit(insts[0], max_iters=200, stop_on_tol=0)
+    t = srv.submit(insts[1], max_iters=55, stop_on_tol=0)
+    info, _ = srv.wait(t)
+    info_long, _ = srv.wait(t_long)
+    srv.close()
+    assert info["state"] == info_long["state"] == dl.DUALIP_REQ_DONE
+    assert info["iters"] == 55
+    assert info_long["iters"] == 200
 
 
 def test_budget_admission_serialises(dl):
