@@ -14,6 +14,17 @@ With N > 1 (torchrun) every rank runs an independent replica (the method is
 run on one GPU; there is no sharded path), value = edges of all ranks / max
 time.  ``--impl reference`` times the FP64 CPU oracle on the host cores on a
 bounded sample of the same workload.
+
+At N = 1 the c2 line also carries
+
+* ``ascent_pass``: the pass timed along the c2 ascent itself (greedy-load
+  budgets, every iteration of the solve to the 1e-4 gap) and at the solved
+  dual point for gamma 1e-3 and 0.1, where near-ties send sources to the
+  multi-pass projection;
+* ``forms``: the BF16 and FP32 forms on c3, the batched form on c4 and the
+  serving form on c5, each with its pass roofline (CUDA events, measured
+  HBM peak), clocks and time to the 1e-4 gap beside the plain FP32 form
+  (``--no-forms`` skips them).
 """
 from __future__ import annotations
 
@@ -56,6 +67,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the c3/c4/c5 forms that the default c2 line carries")
+    ap.add_argument("--form-requests", type=int, default=30,
+                    help="forms: requests of the c5 replay")
     return ap.parse_args()
 
 
@@ -285,6 +300,54 @@ def run_reference(args):
     return 0
 
 
+def load_peak():
+    """Measured HBM copy bandwidth (GB/s) and where it came from."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    peak = peaks.get("hbm_gbs")
+    if peak:
+        return float(peak), "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def roofline(alg_bytes, pass_ms, peak, note, traffic=None, kernel="dualgrad_pass_kernel"):
+    achieved = alg_bytes / (pass_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": kernel, "kernel_ms": pass_ms,
+            "algorithmic_bytes": alg_bytes, "peak_source": note}
+
+
+def profiled(d, h, n, step, batch=False):
+    """Mean kernel durations (ms) of n evaluations, CUDA events around each kernel."""
+    import torch
+
+    (d.dualip_batch_profile_enable if batch else d.dualip_profile_enable)(h, n)
+    for _ in range(n):
+        step()
+    torch.cuda.synchronize()
+    prof = (d.dualip_batch_profile_collect if batch else d.dualip_profile_collect)(h)
+    c = max(prof["count"], 1)
+    return {"prologue": prof["ms_prologue"] / c, "pass": prof["ms_pass"] / c,
+            "epilogue": prof["ms_epilogue"] / c, "count": prof["count"]}
+
+
+def solve_to_gap(d, torch, inst, storage, **kw):
+    """dualip_solve to the 1e-4 relative gap (default options), after a short
+    warm solve (graph capture, row scale)."""
+    P = d.Problem.from_instance(inst, storage=storage)
+    P.solve(max_iters=20, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, res = P.solve(**kw)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return P, lam, {"seconds": dt, "iters": res["iters"], "converged": res["converged"],
+                    "gap_rel": res["gap_rel"], "infeas_rel": res["infeas_rel"],
+                    "dual_obj": res["dual_obj"], "storage": storage}
+
+
 def time_to_gap(d, torch, base, name, storage):
     """dualip_solve to the 1e-4 relative gap on the workload's graph and values with
     the paper's greedy-load budgets (the sum-fraction budgets never bind, so
@@ -292,21 +355,11 @@ def time_to_gap(d, torch, base, name, storage):
     import synth
 
     inst = synth.greedy_budgets(base)
-    P = d.Problem.from_instance(inst, storage=storage)
-    P.solve(max_iters=20)  # warm: graph capture, row scale
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lam, res = P.solve()
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    P, lam, out = solve_to_gap(d, torch, inst, storage)
     P.close()
-    out = {"workload": f"{name} graph and values with greedy-load budgets (App. B rule)",
-           "storage": storage,
-           "seconds": dt, "iters": res["iters"], "converged": res["converged"],
-           "gap_rel": res["gap_rel"], "infeas_rel": res["infeas_rel"],
-           "dual_obj": res["dual_obj"]}
+    out["workload"] = f"{name} graph and values with greedy-load budgets (App. B rule)"
     if name != "c2":
-        return out
+        return out, lam
     # a recurring solve: costs moved by about 1%, started from this optimum at
     # the final gamma
     rng = np.random.default_rng(17)
@@ -325,7 +378,84 @@ def time_to_gap(d, torch, base, name, storage):
     out["warm_recurring"] = {"seconds": wdt, "iters": wres["iters"], "converged": wres["converged"],
                              "change": "c * (1 + 0.01 N(0,1)), from the previous optimum at "
                                        "gamma 1e-3"}
+    return out, lam
+
+
+def ascent_pass(d, torch, base, storage, peak, note):
+    """The pass where the ascent runs: every iteration of the solve to the gap
+    (CUDA events around each pass, solve without graph capture), then at the
+    solved dual point for gamma 1e-3 and 0.1."""
+    import synth
+
+    inst = synth.greedy_budgets(base)
+    alg = algorithmic_bytes(inst, storage)
+    P = d.Problem.from_instance(inst, storage=storage)
+    P.solve(max_iters=20, use_graph=0)  # warm
+    torch.cuda.synchronize()
+    d.dualip_profile_enable(P.h, 5000)
+    lam, res = P.solve(use_graph=0)
+    torch.cuda.synchronize()
+    prof = d.dualip_profile_collect(P.h)
+    ms = prof["ms_pass"] / max(prof["count"], 1)
+    out = {"workload": "c2 graph and values with greedy-load budgets (App. B rule)",
+           "storage": storage, "iters": res["iters"], "converged": res["converged"],
+           "solve": {"pass_ms_mean": ms, "edges_per_s": inst.E / (ms / 1e3),
+                     "roofline": roofline(alg, ms, peak, note),
+                     "epilogue_ms_mean": prof["ms_epilogue"] / max(prof["count"], 1),
+                     "passes_timed": prof["count"]}}
+    grad = torch.empty(inst.J, dtype=torch.float32, device="cuda")
+    out_dev = torch.empty(8, dtype=torch.float64, device="cuda")
+    sp = int(torch.cuda.current_stream().cuda_stream)
+    for gamma in (1e-3, 0.1):
+        def step():
+            d.dualip_dual_grad_async(P.h, lam.data_ptr(), gamma, grad.data_ptr(),
+                                     out_dev.data_ptr(), sp)
+        for _ in range(5):
+            step()
+        k = profiled(d, P.h, 100, step)
+        out[f"lambda_star_gamma_{gamma:g}"] = {
+            "pass_ms": k["pass"], "edges_per_s": inst.E / (k["pass"] / 1e3),
+            "roofline": roofline(alg, k["pass"], peak, note)}
+    d.dualip_check_device_status(P.h, sp)
+    P.close()
     return out
+
+
+def pass_form(d, torch, inst, name, storage, steps, warmup, peak, note):
+    """One workload's pass on a lone problem: step time and per-kernel CUDA-event
+    durations with clocks sampled meanwhile."""
+    P = d.Problem.from_instance(inst, storage=storage)
+    lam = torch.from_numpy(lam_for(inst)).cuda()
+    grad = torch.empty(inst.J, dtype=torch.float32, device="cuda")
+    out_dev = torch.empty(8, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+
+    def step():
+        d.dualip_dual_grad_async(P.h, lam.data_ptr(), GAMMA, grad.data_ptr(), out_dev.data_ptr(),
+                                 sp)
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        k = profiled(d, P.h, steps, step)
+    d.dualip_check_device_status(P.h, sp)
+    P.close()
+    alg = algorithmic_bytes(inst, storage)
+    return {"storage": storage, "I": inst.I, "J": inst.J, "E": inst.E, "gamma": GAMMA,
+            "ms_per_step": ms, "edges_per_s": inst.E / (ms / 1e3), "kernel_ms": k,
+            "roofline": roofline(alg, k["pass"], peak, note,
+                                 pass_traffic(inst.E, inst.J, name, storage)),
+            "clocks": clk.summary()}
 
 
 def batch_time_to_gap(d, torch, probs, B):
@@ -348,31 +478,25 @@ def batch_time_to_gap(d, torch, probs, B):
             "speedup_batched_vs_lone": tl / tb}
 
 
-def run_batch(args):
+def batch_form(d, torch, steps, warmup, scale, storage, solve, peak, note):
     """c4: every problem of the batch in one batched pass per step."""
-    import torch
     import synth
 
-    torch.cuda.set_device(0)
-    from paper_2603_04621_gb300 import build
-
-    build.build()
-    import paper_2603_04621_gb300 as d
-
     shapes = synth.batch_shapes(256)
-    if args.scale != 1.0:
-        shapes = [(max(1, int(I * args.scale)), J, sd) for I, J, sd in shapes]
+    if scale != 1.0:
+        shapes = [(max(1, int(I * scale)), J, sd) for I, J, sd in shapes]
     probs, sample = [], None
     I_t = J_t = E_t = 0
     for I, J, sd in shapes:
         inst = synth.greedy_budgets(synth.batch_instance(I, J, sd))
-        probs.append(d.Problem.from_instance(inst, storage=args.storage))
+        probs.append(d.Problem.from_instance(inst, storage=storage))
         I_t, J_t, E_t = I_t + inst.I, J_t + inst.J, E_t + inst.E
         if sample is None and inst.I >= 100_000:
             sample = inst
         del inst
     B = d.Batch(probs)
     tune = B.autotune()
+    shape = [tune["tile_edges"][tune["chosen"]], tune["tile_sources"][tune["chosen"]]]
     lam_h = np.random.default_rng(LAM_SEED).uniform(0.0, 1.0, J_t).astype(np.float32)
     lam = torch.from_numpy(lam_h).cuda()
     grad = torch.empty_like(lam)
@@ -385,8 +509,8 @@ def run_batch(args):
         d.dualip_batch_dual_grad_async(B.h, lam.data_ptr(), gam, grad.data_ptr(),
                                        out_dev.data_ptr(), sp)
 
-    with ClockSampler(0) as clk:
-        for _ in range(args.warmup):
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         t_end = time.perf_counter() + 1.0
@@ -397,82 +521,53 @@ def run_batch(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        d.dualip_batch_profile_enable(B.h, args.steps)
-        for _ in range(args.steps):
-            step()
-        torch.cuda.synchronize()
-        prof = d.dualip_batch_profile_collect(B.h)
+        k = profiled(d, B.h, steps, step, batch=True)
         # end to end with host buffers: lambda in, gradient out, scalars to host
         lam_pin = torch.from_numpy(lam_h).pin_memory()
         grad_pin = torch.empty(J_t, dtype=torch.float32).pin_memory()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             lam.copy_(lam_pin, non_blocking=True)
             B.dual_grad(lam, gam)
             grad_pin.copy_(grad, non_blocking=True)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-    ttg = None if args.no_solve else batch_time_to_gap(d, torch, probs, B)
-    alg = 12 * E_t + 8 * (I_t + len(probs)) + 12 * J_t
-    if args.storage == "bf16":
-        alg -= 4 * E_t
-    pass_ms = prof["ms_pass"] / max(prof["count"], 1)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = peaks.get("hbm_gbs") or 6800.0
-    achieved = alg / (pass_ms / 1e3) / 1e9
+    ttg = batch_time_to_gap(d, torch, probs, B) if solve else None
+    alg = (edge_bytes(storage) * E_t + 8 * (I_t + len(probs)) + 12 * J_t)
     out = {
-        "metric": METRIC, "value": E_t * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOADS["c4"] if args.scale == 1.0 else
-                   f"c4 at {args.scale:g} of the sources", "storage": args.storage,
-                   "problems": len(probs), "I": I_t, "J": J_t, "E": E_t, "gamma": GAMMA,
-                   "lambda": f"U(0,1) seed {LAM_SEED}",
+        "value": E_t * steps / (ms / 1e3), "ms_per_step": ms / steps,
+        "config": {"workload": WORKLOADS["c4"] if scale == 1.0 else f"c4 at {scale:g} of the sources",
+                   "storage": storage, "problems": len(probs), "I": I_t, "J": J_t, "E": E_t,
+                   "gamma": GAMMA, "lambda": f"U(0,1) seed {LAM_SEED}",
                    "l2": "inputs larger than L2; no flush", "parallelism": "replicas",
-                   "tile_shape": [tune["tile_edges"][tune["chosen"]],
-                                  tune["tile_sources"][tune["chosen"]]]},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": pass_traffic(E_t, J_t, "c4", args.storage,
-                                             [tune["tile_edges"][tune["chosen"]],
-                                              tune["tile_sources"][tune["chosen"]]]),
-                     "kernel": "dualgrad_pass_kernel (batched)", "kernel_ms": pass_ms,
-                     "algorithmic_bytes": alg,
-                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
-        "kernel_ms": {"prologue": prof["ms_prologue"] / max(prof["count"], 1), "pass": pass_ms,
-                      "epilogue": prof["ms_epilogue"] / max(prof["count"], 1)},
+                   "tile_shape": shape},
+        "roofline": roofline(alg, k["pass"], peak, note,
+                             pass_traffic(E_t, J_t, "c4", storage, shape),
+                             kernel="dualgrad_pass_kernel (batched)"),
+        "kernel_ms": k,
         "autotune": {"tile_edges": tune["tile_edges"], "tile_sources": tune["tile_sources"],
                      "ms": tune["ms"], "chosen": tune["chosen"], "lean80": tune["lean80"],
                      "ms_lean80": tune["ms_lean80"]},
-        "e2e": {"value": E_t * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * J_t,
+        "e2e": {"value": E_t * steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * J_t,
                 "d2h_bytes_per_step": 4 * J_t + 40 * len(probs),
                 "api": "dualip_batch_dual_grad (lambda and grad through pinned host buffers)"},
         "clocks": clk.summary(),
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 3 * steps,
         "time_to_gap": ttg,
     }
-    if not args.no_cpu_baseline and sample is not None:
-        out["cpu_baseline"] = cpu_baseline(sample, args.cpu_seconds)
-    print(json.dumps(out), flush=True)
     B.close()
-    return 0
+    for P in probs:
+        P.close()
+    return out, sample
 
 
-def run_serve(args):
-    """c5: replay the first N requests of the trace in real time through the
-    server; then solve each request alone with the plain FP32 form."""
+def run_batch(args):
     import torch
-    import synth
 
     torch.cuda.set_device(0)
     from paper_2603_04621_gb300 import build
@@ -480,10 +575,28 @@ def run_serve(args):
     build.build()
     import paper_2603_04621_gb300 as d
 
-    trace = synth.request_trace(400)[: args.requests]
+    peak, note = load_peak()
+    f, sample = batch_form(d, torch, args.steps, args.warmup, args.scale, args.storage,
+                           not args.no_solve, peak, note)
+    out = {"metric": METRIC, "value": f.pop("value"), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": f.pop("ms_per_step"),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", **f}
+    if not args.no_cpu_baseline and sample is not None:
+        out["cpu_baseline"] = cpu_baseline(sample, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def serve_form(d, torch, n, budget_gib):
+    """c5: replay the first n requests of the trace in real time through the
+    server; then solve each request alone with the plain FP32 form."""
+    import synth
+
+    trace = synth.request_trace(400)[:n]
     insts = [synth.greedy_budgets(synth.request_instance(r)) for r in trace]
-    srv = d.Server(int(args.budget_gib * (1 << 30)), max_slots=64, check_every=10)
-    with ClockSampler(0) as clk:
+    srv = d.Server(int(budget_gib * (1 << 30)), max_slots=64, check_every=10)
+    with ClockSampler(torch.cuda.current_device()) as clk:
         t0 = time.perf_counter()
         tickets = []
         for r, x in zip(trace, insts):
@@ -497,9 +610,10 @@ def run_serve(args):
     srv.close()
     infos = [o[0] for o in out]
     ok = [i for i in infos if i["state"] == d.DUALIP_REQ_DONE]
+    conv = [i for i in ok if i["converged"]]
     ttg = np.array([i["t_done"] - i["t_submit"] for i in ok])
+    ttg_c = np.array([i["t_done"] - i["t_submit"] for i in conv]) if conv else ttg
     qd = np.array([i["t_admit"] - i["t_submit"] for i in ok])
-    conv = sum(i["converged"] for i in ok)
     work = sum(x.E * i["iters"] for x, i in zip(insts, infos) if i["state"] == d.DUALIP_REQ_DONE)
     # the plain FP32 single-instance form, one request after another
     lone_t, lone_conv = 0.0, 0
@@ -512,24 +626,22 @@ def run_serve(args):
         lone_t += time.perf_counter() - t1
         lone_conv += r1["converged"]
         P.close()
-    n = len(insts)
-    out_line = {
-        "metric": "serve time-to-1e-4-gap p50", "value": float(np.median(ttg)), "unit": "s",
-        "n_gpus": 1, "steps": n, "warmup": 0, "ms_per_step": 1e3 * span / n,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
+    return {
         "config": {"workload": WORKLOADS["c5"], "requests": n, "arrival_rate_per_s": 20.0,
-                   "budget_gib": args.budget_gib, "max_slots": 64, "check_every": 10,
+                   "budget_gib": budget_gib, "max_slots": 64, "check_every": 10,
                    "E_mean": float(np.mean([x.E for x in insts])),
                    "bf16_requests": sum(r["storage"] == "bf16" for r in trace),
                    "parallelism": "replicas"},
         "serve": {"p50_s": float(np.median(ttg)), "p99_s": float(np.quantile(ttg, 0.99)),
+                  "converged_p50_s": float(np.median(ttg_c)),
+                  "converged_p99_s": float(np.quantile(ttg_c, 0.99)),
                   "queue_p50_s": float(np.median(qd)), "queue_p99_s": float(np.quantile(qd, 0.99)),
-                  "done": len(ok), "converged": conv, "failed": n - len(ok),
+                  "done": len(ok), "converged": len(conv), "failed": n - len(ok),
                   "solves_per_s": len(ok) / span, "span_s": span,
                   "arrival_span_s": trace[-1]["t"],
                   "edge_iterations_per_s": work / span,
-                  "busy_s": st["busy_seconds"], "peak_resident_gib": st["peak_resident_bytes"] / 2**30},
+                  "busy_s": st["busy_seconds"],
+                  "peak_resident_gib": st["peak_resident_bytes"] / 2**30},
         "lone_fp32_sequential": {"seconds": lone_t, "solves_per_s": n / lone_t,
                                  "converged": lone_conv},
         "e2e": {"value": float(np.median(ttg)), "unit": "s",
@@ -539,8 +651,47 @@ def run_serve(args):
         "clocks": clk.summary(),
         "gpu_launches": int(st["chunks"] * 10 * 5),
     }
+
+
+def run_serve(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2603_04621_gb300 import build
+
+    build.build()
+    import paper_2603_04621_gb300 as d
+
+    f = serve_form(d, torch, args.requests, args.budget_gib)
+    n = args.requests
+    out_line = {
+        "metric": "serve time-to-1e-4-gap p50", "value": f["serve"]["p50_s"], "unit": "s",
+        "n_gpus": 1, "steps": n, "warmup": 0, "ms_per_step": 1e3 * f["serve"]["span_s"] / n,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", **f}
     print(json.dumps(out_line), flush=True)
     return 0
+
+
+def forms(d, torch, args, plain, peak, note):
+    """The BF16, batched and serving forms beside the plain FP32 form (c2)."""
+    import synth
+
+    out = {"plain_fp32_c2": plain}
+    t0 = time.perf_counter()
+    c3 = synth.config("c3")
+    gen_s = time.perf_counter() - t0
+    for storage in ("bf16", "f32"):
+        f = pass_form(d, torch, c3, "c3", storage, 20, 3, peak, note)
+        f["workload"] = WORKLOADS["c3"]
+        f["time_to_gap"], _ = time_to_gap(d, torch, c3, "c3", storage)
+        out[f"{storage}_c3"] = f
+    out["bf16_c3"]["generation_s"] = gen_s
+    del c3
+    f, _ = batch_form(d, torch, 20, 3, 1.0, "f32", True, peak, note)
+    out["batched_c4"] = f
+    out["serving_c5"] = serve_form(d, torch, args.form_requests, args.budget_gib)
+    return out
 
 
 def run_ours(args):
@@ -601,11 +752,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         # kernel durations: events around each kernel (which also orders them)
-        d.dualip_profile_enable(P.h, min(args.steps, 500))
-        for _ in range(min(args.steps, 500)):
-            step()
-        torch.cuda.synchronize()
-        prof = d.dualip_profile_collect(P.h)
+        k = profiled(d, P.h, min(args.steps, 500), step)
         d.dualip_check_device_status(P.h, sp)
         ms = max_over_ranks(ms, ws)
         if ws > 1:
@@ -620,51 +767,47 @@ def run_ours(args):
             d.dualip_dual_grad_host(P.h, lam_pin.data_ptr(), GAMMA, grad_pin.data_ptr(), sp)
         e2e_s = time.perf_counter() - t0
         e2e_s = max_over_ranks(e2e_s, ws)
-    ttg = None
-    if not args.no_solve and rank == 0 and args.scale == 1.0:
-        P.close()
-        ttg = time_to_gap(d, torch, inst, args.workload, args.storage)
+    P.close()
     if rank != 0:
         if ws > 1:
             dist.barrier()
         return 0
+    peak, note = load_peak()
+    ttg = asc = fm = None
+    if not args.no_solve and args.scale == 1.0:
+        ttg, _ = time_to_gap(d, torch, inst, args.workload, args.storage)
+        if ws == 1 and args.workload == "c2":
+            asc = ascent_pass(d, torch, inst, args.storage, peak, note)
 
     E = inst.E
     value = whole_job_rate(E, args.steps, ws, ms / 1e3)
-    pass_ms = prof["ms_pass"] / max(prof["count"], 1)
     alg = algorithmic_bytes(inst, args.storage)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_note = "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
-    if not peak:
-        peak, peak_note = 6800.0, "fallback 6.8 TB/s"
-    achieved = alg / (pass_ms / 1e3) / 1e9
+    rl = roofline(alg, k["pass"], peak, note,
+                  pass_traffic(inst.E, inst.J, args.workload, args.storage))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(inst, args.workload, args.scale, args.storage),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": pass_traffic(inst.E, inst.J, args.workload, args.storage),
-                     "kernel": "dualgrad_pass_kernel",
-                     "kernel_ms": pass_ms, "algorithmic_bytes": alg, "peak_source": peak_note},
-        "kernel_ms": {"prologue": prof["ms_prologue"] / max(prof["count"], 1), "pass": pass_ms,
-                      "epilogue": prof["ms_epilogue"] / max(prof["count"], 1)},
-        "hbm_roofline_pct": 100.0 * achieved / peak,
+        "roofline": rl,
+        "kernel_ms": k,
+        "hbm_roofline_pct": 100.0 * rl["frac"],
         "e2e": {"value": whole_job_rate(E, args.steps, ws, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * inst.J, "d2h_bytes_per_step": 4 * inst.J + 40,
                 "api": "dualip_dual_grad_host (lambda in, grad + FP64 scalars out, pinned)"},
         "clocks": clk.summary(),
         "gpu_launches": 3 * args.steps,
         "time_to_gap": ttg,
+        "ascent_pass": asc,
     }
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
+    if (ws == 1 and args.workload == "c2" and args.scale == 1.0 and not args.no_forms
+            and not args.no_solve):
+        del inst
+        plain = {"ms_per_step": ms / args.steps, "roofline": rl, "time_to_gap": ttg,
+                 "clocks": out["clocks"]}
+        out["forms"] = forms(d, torch, args, plain, peak, note)
     print(json.dumps(out), flush=True)
     if ws > 1:
         dist.barrier()

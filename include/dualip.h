@@ -170,8 +170,13 @@ dualip_status dualip_get_info(const dualip_problem* p, int64_t* num_sources, int
  * gamma_k = max(gamma_final, gamma0 * 2^-floor(k / halve_every)) and the step
  * cap scaled in proportion to gamma (Section 5.1, "Regularization decay").
  * Step: eta_k = min(max_step * gamma_k / gamma0, secant estimate
- * ||y_k - y_{k-1}|| / ||G_k - G_{k-1}||), init_step right after a (re)start;
- * momentum restarts when gamma changes (restart_on_gamma_change).
+ * ||y_k - y_{k-1}|| / ||G_k - G_{k-1}||), init_step right after a gamma
+ * change; momentum restarts when gamma changes (restart_on_gamma_change) and,
+ * with restart_on_decrease, whenever the dual objective at the evaluated
+ * point is below that of the previous evaluation at the same gamma (an
+ * adaptive restart; the secant estimate is kept).  The scalars are exact
+ * fixed-point sums (objective partials) and fixed-order sums (per-row terms),
+ * so the restart decisions, and the whole trajectory, repeat bit for bit.
  * Stopping, tested every check_every iterations at gamma_final:
  *   |lambda^T (A x - b)| / max(1, |p|, |g|) <= tol_gap  (p = c^T x + ridge term)
  *   ||(A x - b)_+||_2 / max(1, ||b||_2)     <= tol_infeas.
@@ -190,6 +195,7 @@ typedef struct {
   int32_t restart_on_gamma_change; /* 1 (default) */
   int32_t stop_on_tol;      /* 1: stop at the tolerances; 0: run exactly max_iters */
   int32_t use_graph;        /* 1: capture check_every iterations in one CUDA graph */
+  int32_t restart_on_decrease; /* 1 (default): adaptive momentum restart, see above */
 } dualip_solve_opts;
 
 typedef struct {
@@ -203,7 +209,8 @@ typedef struct {
 
 /* Fill opts with the defaults: gamma0 0.1, gamma_final 1e-3, halve_every 25,
  * max_step 10, init_step 1e-5, max_iters 5000, tolerances 1e-4,
- * check_every 10, row_normalize 1, restart 1, stop_on_tol 1, use_graph 1. */
+ * check_every 10, row_normalize 1, restart 1, stop_on_tol 1, use_graph 1,
+ * restart_on_decrease 1. */
 void dualip_solve_opts_default(dualip_solve_opts* opts);
 
 /*

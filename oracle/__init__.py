@@ -47,7 +47,8 @@ class SolveOpts(ctypes.Structure):
                 ("init_step", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("tol_gap", ctypes.c_double), ("tol_infeas", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("row_normalize", ctypes.c_int32),
-                ("restart_on_gamma_change", ctypes.c_int32), ("stop_on_tol", ctypes.c_int32)]
+                ("restart_on_gamma_change", ctypes.c_int32), ("stop_on_tol", ctypes.c_int32),
+                ("restart_on_decrease", ctypes.c_int32)]
 
 
 class SolveResult(ctypes.Structure):
@@ -55,7 +56,7 @@ class SolveResult(ctypes.Structure):
                 ("dual", ctypes.c_double), ("primal_lin", ctypes.c_double),
                 ("reg", ctypes.c_double), ("infeas", ctypes.c_double),
                 ("gap_rel", ctypes.c_double), ("infeas_rel", ctypes.c_double),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("restarts", ctypes.c_int32)]
 
 
 def _load():
@@ -167,9 +168,11 @@ class Problem:
 
     def solve(self, lam0=None, gamma0=0.1, gamma_final=1e-3, halve_every=25, max_step=10.0,
               init_step=1e-5, max_iters=2000, tol_gap=1e-4, tol_infeas=1e-4, check_every=10,
-              row_normalize=True, restart=True, stop_on_tol=True, want_trace=False):
+              row_normalize=True, restart=True, stop_on_tol=True, want_trace=False,
+              restart_on_decrease=True):
         o = SolveOpts(gamma0, gamma_final, halve_every, max_step, init_step, max_iters, tol_gap,
-                      tol_infeas, check_every, int(row_normalize), int(restart), int(stop_on_tol))
+                      tol_infeas, check_every, int(row_normalize), int(restart), int(stop_on_tol),
+                      int(restart_on_decrease))
         lam = np.zeros(self.J) if lam0 is None else np.array(lam0, dtype=np.float64, copy=True)
         res = SolveResult()
         tr = np.zeros((max(max_iters, 1), TRACE_W)) if want_trace else None
@@ -178,7 +181,8 @@ class Problem:
             raise RuntimeError(f"oracle_solve failed ({rc})")
         out = dict(iters=res.iters, converged=bool(res.converged), dual=res.dual,
                    primal_lin=res.primal_lin, reg=res.reg, infeas=res.infeas,
-                   gap_rel=res.gap_rel, infeas_rel=res.infeas_rel, gamma=res.gamma, mu=lam)
+                   gap_rel=res.gap_rel, infeas_rel=res.infeas_rel, gamma=res.gamma, mu=lam,
+                   restarts=res.restarts)
         if want_trace:
             out["trace"] = tr[: res.iters]
         return out

@@ -331,6 +331,9 @@ int oracle_eval(const oracle_problem* p, const double* mu, double gamma, int met
  *   eta_max = max_step * gamma_k / gamma_0
  *   eta_k   = min(eta_max, ||y_k - y_{k-1}|| / ||G_k - G_{k-1}||)  (secant estimate)
  *             or min(init_step, eta_max) right after a (re)start
+ *   adaptive restart (restart_on_decrease): if g(D y_k) < g(D y_{k-1}) at the
+ *             same gamma, t_k = 1 (no momentum in the next point; the secant
+ *             history is kept)
  *   lam_{k+1} = max(0, y_k + eta_k G_k)
  *   t_{k+1}   = (1 + sqrt(1 + 4 t_k^2)) / 2
  *   y_{k+1}   = max(0, lam_{k+1} + ((t_k - 1) / t_{k+1}) (lam_{k+1} - lam_k))
@@ -349,12 +352,14 @@ typedef struct {
   int32_t row_normalize;
   int32_t restart_on_gamma_change;
   int32_t stop_on_tol;
+  int32_t restart_on_decrease;
 } oracle_solve_opts;
 
 typedef struct {
   int32_t iters;
   int32_t converged;
   double dual, primal_lin, reg, infeas, gap_rel, infeas_rel, gamma;
+  int32_t restarts;  /* adaptive restarts taken */
 } oracle_solve_result;
 
 #define TRACE_W 8
@@ -387,8 +392,8 @@ int oracle_solve(const oracle_problem* p, const oracle_solve_opts* o, double* la
     lam[j] = v > 0 ? v : 0.0;
     y[j] = lam[j];
   }
-  double t = 1.0, gprev = 0.0;
-  int have_prev = 0, converged = 0, rc = OR_OK;
+  double t = 1.0, gprev = 0.0, obj_prev = 0.0;
+  int have_prev = 0, converged = 0, rc = OR_OK, restarts = 0;
   int32_t k = 0, iters = 0;
   double scal[5] = {0, 0, 0, 0, 0}, gap_rel = 0.0, inf_rel = 0.0, gk = o->gamma0;
   for (k = 0; k < o->max_iters; ++k) {
@@ -432,6 +437,13 @@ int oracle_solve(const oracle_problem* p, const oracle_solve_opts* o, double* la
       eta = fmin(o->init_step, eta_max);
     }
     if (trace) trace[(size_t)k * TRACE_W + 6] = eta;
+    /* the dual objective fell since the last evaluation at this gamma: drop
+       the momentum (the secant history stays) */
+    if (o->restart_on_decrease && have_prev && scal[0] < obj_prev) {
+      t = 1.0;
+      restarts++;
+    }
+    obj_prev = scal[0];
     double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
     double beta = (t - 1.0) / tn;
     for (int32_t j = 0; j < J; ++j) {
@@ -454,6 +466,7 @@ int oracle_solve(const oracle_problem* p, const oracle_solve_opts* o, double* la
       res->iters = iters; res->converged = converged;
       res->dual = scal[0]; res->primal_lin = scal[1]; res->reg = scal[2]; res->infeas = scal[3];
       res->gap_rel = gap_rel; res->infeas_rel = inf_rel; res->gamma = gk;
+      res->restarts = restarts;
     }
   }
   free(D); free(lam); free(y); free(yp); free(G); free(Gp); free(mu); free(grad); free(lamn);

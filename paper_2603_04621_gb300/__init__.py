@@ -99,7 +99,7 @@ class SolveOpts(ctypes.Structure):
                 ("tol_gap", ctypes.c_double), ("tol_infeas", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("row_normalize", ctypes.c_int32),
                 ("restart_on_gamma_change", ctypes.c_int32), ("stop_on_tol", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("restart_on_decrease", ctypes.c_int32)]
 
 
 class SolveResult(ctypes.Structure):

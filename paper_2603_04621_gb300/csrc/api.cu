@@ -385,6 +385,17 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     int ex = 0;
     std::frexp(std::max((double)maxcnt * ma, 1e-30), &ex);  // bound < 2^ex
     P.exp_y = std::max(-100, std::min(100, 61 - ex));
+    // Objective partials: every source has sum_e x_e <= 1 and x_e <= 1, so
+    // |sum c x| <= I max|c| and sum w x^2 <= I max w (w = a^2, or 1 where
+    // a = 0, with primal scaling; w = 1 without).  The BF16 rounding of c and a
+    // stays far inside the two bits of headroom below 2^63.
+    float mc;
+    std::memcpy(&mc, &absmax[0], 4);
+    const double mw = P.weighted ? std::max(1.0, (double)ma * (double)ma) : 1.0;
+    std::frexp(std::max((double)I * mc, 1e-30), &ex);
+    P.exp_c = std::max(-100, std::min(100, 61 - ex));
+    std::frexp(std::max((double)I * mw, 1e-30), &ex);
+    P.exp_w = std::max(-100, std::min(100, 61 - ex));
   }
   DeviceStatus st{};
   if ((e = cudaMemcpyAsync(&st, P.status, sizeof(st), cudaMemcpyDeviceToHost, s)) ||

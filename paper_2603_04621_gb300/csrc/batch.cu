@@ -8,9 +8,11 @@
 // every slot has its own gamma schedule, step, momentum and stopping test, and
 // a slot that has converged leaves the lists, so its edges are no longer
 // streamed.  Every per-problem result equals the problem's own evaluation:
-// A x is exact in fixed point, so the gradient does not depend on the other
-// problems, and the scalars differ from a lone evaluation only in the order
-// of their FP32/FP64 partial sums.
+// A x and the objective partials (sum c x, sum w x^2) are exact fixed-point
+// sums, so the gradient, c^T x and the ridge term do not depend on the other
+// problems; lambda^T (A x - b) and ||(A x - b)_+|| differ from a lone
+// evaluation only in the order of their partial sums (chunk order here), and
+// are the same in any mix of problems.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -113,7 +115,7 @@ __global__ void bprep_kernel(const RowChunk* __restrict__ rc, const SlotDesc* __
 __global__ void bepi_kernel(const RowChunk* __restrict__ rc, int nchunks,
                             const SlotDesc* __restrict__ sd, float* __restrict__ grad, int solver,
                             float4* __restrict__ cpart, const int32_t* __restrict__ act, int nact,
-                            const int2* __restrict__ crange, double* slot_part,
+                            const int2* __restrict__ crange, long long* slot_part,
                             const double* __restrict__ gamma_d, double* eval, unsigned* ticket) {
   pdl_wait();  // A x and the partials of the pass
   pdl_trigger();
@@ -160,16 +162,18 @@ __global__ void bepi_kernel(const RowChunk* __restrict__ rc, int nchunks,
   for (int a = threadIdx.x; a < nact; a += blockDim.x) {
     const int s = act[a];
     const int2 cr = crange[s];
-    float mh = 0.f, ml = 0.f, nh = 0.f, nl = 0.f;
+    double mug = 0.0, inf = 0.0;  // chunk pairs combined in FP64, in chunk order
     for (int c = cr.x; c < cr.y; ++c) {
       const float4 u = __ldcg(cpart + c);
-      b_pair_addp(mh, ml, u.x, u.y);
-      b_pair_addp(nh, nl, u.z, u.w);
+      mug += (double)u.x + (double)u.y;
+      inf += (double)u.z + (double)u.w;
     }
-    const double cx = __ldcg(slot_part + 2 * s), wxx = __ldcg(slot_part + 2 * s + 1);
-    slot_part[2 * s] = 0.0;
-    slot_part[2 * s + 1] = 0.0;
-    const double mug = (double)mh + (double)ml, inf = (double)nh + (double)nl;
+    // the pass's exact fixed-point sums, in the slot's scales
+    const SlotDesc& ds = sd[s];
+    const double cx = ldexp((double)__ldcg(slot_part + 2 * s), -ds.ec);
+    const double wxx = ldexp((double)__ldcg(slot_part + 2 * s + 1), -ds.ew);
+    slot_part[2 * s] = 0;
+    slot_part[2 * s + 1] = 0;
     const double reg = 0.5 * gamma_d[s] * wxx;
     double* o = eval + 5 * (size_t)s;
     o[0] = cx + reg + mug;
@@ -197,22 +201,33 @@ __global__ void bnorms_kernel(const RowChunk* __restrict__ rc, int nchunks,
   const SlotDesc& d = sd[ch.slot];
   const SlotSolve& st = ss[ch.slot];
   const bool have_prev = st.k > 0 && !slot_restart(st, st.k);
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  // FP64 per row and through the trees (the step and the restart test read them)
+  double dy = 0.0, dg = 0.0;
   if (have_prev) {
     for (int j = ch.r0 + threadIdx.x; j < ch.r1; j += blockDim.x) {
-      const float u = __fsub_rn(d.yv[j], d.yp[j]);
-      const float w = __fsub_rn(d.G[j], d.Gp[j]);
-      const float uu = __fmul_rn(u, u), ww = __fmul_rn(w, w);
-      b_pair_add(v.x, v.y, uu);
-      v.y = __fadd_rn(v.y, __fmaf_rn(u, u, -uu));
-      b_pair_add(v.z, v.w, ww);
-      v.w = __fadd_rn(v.w, __fmaf_rn(w, w, -ww));
+      const double u = (double)d.yv[j] - (double)d.yp[j];
+      const double w = (double)d.G[j] - (double)d.Gp[j];
+      dy += u * u;
+      dg += w * w;
     }
   }
-  const float4 t = block_pair_sum2(v);
+  __shared__ double2 red[8];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    dy += __shfl_xor_sync(0xffffffffu, dy, o);
+    dg += __shfl_xor_sync(0xffffffffu, dg, o);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(dy, dg);
+  __syncthreads();
   __shared__ bool last;
+  double2* cpd = reinterpret_cast<double2*>(cpart);  // same 16 bytes per chunk
   if (threadIdx.x == 0) {
-    cpart[blockIdx.x] = t;
+    double2 t = red[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      t.x += red[k].x;
+      t.y += red[k].y;
+    }
+    cpd[blockIdx.x] = t;
     __threadfence();
     last = atomicAdd(ticket, 1u) == (unsigned)nchunks - 1;
   }
@@ -222,30 +237,33 @@ __global__ void bnorms_kernel(const RowChunk* __restrict__ rc, int nchunks,
   for (int a = threadIdx.x; a < nact; a += blockDim.x) {
     const int s = act[a];
     const int2 cr = crange[s];
-    float yh = 0.f, yl = 0.f, gh = 0.f, gl = 0.f;
+    double sdy = 0.0, sdg = 0.0;
     for (int c = cr.x; c < cr.y; ++c) {
-      const float4 u = __ldcg(cpart + c);
-      b_pair_addp(yh, yl, u.x, u.y);
-      b_pair_addp(gh, gl, u.z, u.w);
+      const double2 u = __ldcg(cpd + c);
+      sdy += u.x;
+      sdg += u.y;
     }
     SlotSolve& S = ss[s];
     const int32_t k = S.k;
     const bool hp = k > 0 && !slot_restart(S, k);
-    const double sdy = (double)yh + (double)yl, sdg = (double)gh + (double)gl;
     const double gk = slot_gamma(S, k);
     const double eta_max = S.max_step * gk / S.gamma0;
     double eta;
     if (hp) eta = sdg > 0.0 ? fmin(eta_max, sqrt(sdy) / sqrt(sdg)) : eta_max;
     else eta = fmin(S.init_step, eta_max);
-    const double tk = slot_restart(S, k) ? 1.0 : S.t;
+    const double* o = eval + 5 * (size_t)s;
+    const double g = o[0], p = o[1] + o[2];
+    // momentum restarts at a gamma change, and (restart_dec) when the dual
+    // objective fell since the previous evaluation at the same gamma
+    const bool dec = S.restart_dec && hp && g < S.g_prev;
+    const double tk = (slot_restart(S, k) || dec) ? 1.0 : S.t;
     const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
     S.eta = eta;
     S.beta = (tk - 1.0) / tn;
     S.t = tn;
     S.sdy = sdy;
     S.sdg = sdg;
-    const double* o = eval + 5 * (size_t)s;
-    const double g = o[0], p = o[1] + o[2];
+    S.g_prev = g;
     S.gap_rel = fabs(o[4]) / fmax(1.0, fmax(fabs(p), fabs(g)));
     S.infeas_rel = o[3] / fmax(1.0, S.bnorm);
     S.last_gamma = gk;
@@ -525,7 +543,7 @@ static cudaError_t batch_alloc_parts(Batch& B, int capacity, int storage, int we
       (e = cudaMalloc(&B.d_slots, sizeof(SlotDesc) * n)) ||
       (e = cudaMalloc(&B.d_gamma_f, sizeof(float) * n)) ||
       (e = cudaMalloc(&B.d_gamma_d, sizeof(double) * n)) ||
-      (e = cudaMalloc(&B.d_slot_part, sizeof(double) * 2 * n)) ||
+      (e = cudaMalloc(&B.d_slot_part, sizeof(long long) * 2 * n)) ||
       (e = cudaMalloc(&B.d_eval, sizeof(double) * 5 * n)) ||
       (e = cudaMalloc(&B.d_ss, sizeof(SlotSolve) * n)) ||
       (e = cudaMalloc(&B.d_act, sizeof(int32_t) * n)) ||
@@ -536,7 +554,7 @@ static cudaError_t batch_alloc_parts(Batch& B, int capacity, int storage, int we
       (e = cudaMallocHost(&B.h_eval, sizeof(double) * 5 * n)) ||
       (e = cudaMallocHost(&B.h_ss, sizeof(SlotSolve) * n)))
     return e;
-  if ((e = cudaMemsetAsync(B.d_slot_part, 0, sizeof(double) * 2 * n, B.stream)) ||
+  if ((e = cudaMemsetAsync(B.d_slot_part, 0, sizeof(long long) * 2 * n, B.stream)) ||
       (e = cudaMemsetAsync(B.d_tickets, 0, sizeof(unsigned) * 2, B.stream)) ||
       (e = cudaMemsetAsync(B.d_status, 0, sizeof(DeviceStatus), B.stream)) ||
       (e = cudaMemsetAsync(B.d_eval, 0, sizeof(double) * 5 * n, B.stream)) ||
@@ -573,6 +591,8 @@ SlotDesc slot_desc(Problem& P, int64_t joff) {
   d.h_y = P.h_y;
   d.sy = ldexpf(1.0f, P.exp_y);
   d.inv_sy = ldexpf(1.0f, -P.exp_y);
+  d.ec = P.exp_c;
+  d.ew = P.exp_w;
   d.joff = joff;
   return d;
 }
@@ -599,6 +619,7 @@ SlotSolve slot_solve_init(const dualip_solve_opts& o, double bnorm) {
   S.bnorm = bnorm;
   S.halve_every = o.halve_every;
   S.restart = o.restart_on_gamma_change ? 1 : 0;
+  S.restart_dec = o.restart_on_decrease ? 1 : 0;
   S.t = 1.0;
   return S;
 }
@@ -637,7 +658,7 @@ int batch_attach(Batch& B, Problem* P, const dualip_solve_opts& o, cudaError_t* 
       (e = upload_slots(B)) ||
       (e = cudaMemcpyAsync(B.d_ss + s, B.h_ss + s, sizeof(SlotSolve), cudaMemcpyHostToDevice,
                            B.stream)) ||
-      (e = cudaMemsetAsync(B.d_slot_part + 2 * s, 0, 2 * sizeof(double), B.stream)) ||
+      (e = cudaMemsetAsync(B.d_slot_part + 2 * s, 0, 2 * sizeof(long long), B.stream)) ||
       (e = slot_chunks(B, s))) {
     *err = e;
     batch_detach(B, s);

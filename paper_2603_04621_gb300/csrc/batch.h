@@ -37,7 +37,7 @@ struct Batch {
   SlotDesc* d_slots = nullptr;
   float* d_gamma_f = nullptr;
   double* d_gamma_d = nullptr;
-  double* d_slot_part = nullptr;
+  long long* d_slot_part = nullptr;  // [2 n] fixed-point (sum c x, sum w x^2) per slot
   double* d_eval = nullptr;
   SlotSolve* d_ss = nullptr;
   int32_t* d_act = nullptr;

@@ -91,7 +91,8 @@ struct EpiParams {
   unsigned long long* y;   // [J] fixed-point A x, reset to 0 after reading
   float sy;                // 2^-exp_y (exact in FP32: |exp_y| <= 100)
   float* grad;             // [J] caller numbering: D (A x - b) (D = 1 if null)
-  const float4* part;      // per-CTA partials of the pass (pairs, see PassParams)
+  const longlong2* part;   // per-CTA fixed-point partials of the pass (see PassParams)
+  int ec, ew;              // their exponents: sum c x = part.x 2^-ec, sum w x^2 = part.y 2^-ew
   int npart;
   float4* epi_part;        // [gridDim.x] per-block (lambda^T g, ||g_+||^2) as FP32 pairs
   const float* gamma_dev;
@@ -133,6 +134,7 @@ struct SlotDesc {
   const float* b_r;           // [J] budgets, renumbered
   int32_t J, h_mu, h_y, pad;
   float sy, inv_sy;           // 2^exp_y, 2^-exp_y
+  int32_t ec, ew;             // fixed-point exponents of the objective partials
   int64_t joff;               // offset of this problem in joint caller vectors
   // solver vectors in the caller's numbering (null outside the solver)
   float *lam, *yv, *yp, *G, *Gp, *D;
@@ -144,7 +146,8 @@ struct SlotSolve {
   double t, eta, beta;
   double gap_rel, infeas_rel, last_gamma;
   double sdy, sdg;            // ||y_k - y_{k-1}||^2, ||G_k - G_{k-1}||^2
-  int32_t k, halve_every, restart, pad;
+  double g_prev;              // dual objective of the previous evaluation (same gamma)
+  int32_t k, halve_every, restart, restart_dec;
 };
 
 // Kernel parameters of one pass (one dual evaluation).
@@ -168,8 +171,10 @@ struct PassParams {
   // outputs / scratch
   unsigned long long* y;  // [J] A x in fixed point (two's complement, scale 2^exp_y)
   int ey;                 // fixed-point exponent of A x (scale 2^ey)
-  float4* part;           // [gridDim.x] per-CTA (sum c x, sum w x^2), each an FP32
-                          // pair hi + lo (double-float)
+  int ec, ew;             // fixed-point exponents of sum c x and sum w x^2
+  longlong2* part;        // [gridDim.x] per-CTA (sum c x, sum w x^2) in fixed point
+                          // (scales 2^ec, 2^ew): exact sums of once-rounded terms, so
+                          // they do not depend on which CTA took which source
   float* x_out;           // [E] optional primal output (edge order)
   DeviceStatus* status;
   // batched pass: tiles from jt, per-slot arrays from slots, per-slot gamma,
@@ -177,7 +182,7 @@ struct PassParams {
   const JointTile* jt;
   const SlotDesc* slots;
   const float* gamma_of;
-  double* slot_part;
+  long long* slot_part;   // per-slot fixed-point (sum c x, sum w x^2) (slot scales)
   int lean80;  // 4-lane lean groups may take spans up to 80 (else 64)
 };
 
@@ -203,7 +208,11 @@ struct Problem {
   float* mu_r = nullptr;
   unsigned long long* y = nullptr;  // fixed-point accumulator of A x
   int exp_y = 0;                    // fixed-point scale of A x (power of two)
-  float4* part = nullptr;
+  // fixed-point exponents of the objective partials: sum_e c_e x_e and
+  // sum_e w_e x_e^2 are bounded by I max|c| and I max w (sum_e x_e <= 1 per
+  // source), kept below 2^61
+  int exp_c = 0, exp_w = 0;
+  longlong2* part = nullptr;
   int epi_blocks = 0;
   float4* epi_part = nullptr;
   double* eval_dev = nullptr;
@@ -266,7 +275,7 @@ cudaError_t launch_pdl(void (*k)(K...), dim3 grid, dim3 block, size_t smem, cuda
 
 // Batched pass over the joint tile list (ntiles entries) with the given grid.
 cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, int64_t ntiles,
-                              const SlotDesc* slots, const float* gamma_of, double* slot_part,
+                              const SlotDesc* slots, const float* gamma_of, long long* slot_part,
                               DeviceStatus* status, int grid, int lean80, cudaStream_t s);
 cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const float* gamma_dev,
                             double gamma, double* eval_out, cudaStream_t s, bool identity = false);

@@ -318,6 +318,8 @@ struct Ctx {
   unsigned long long* y;
   float gamma, inv_gamma;
   float sy;  // 2^ey: fixed-point scale of A x
+  float sc, sw;     // 2^ec, 2^ew: fixed-point scales of sum c x and sum w x^2
+  long long one_w;  // 2^ew (exact: ew >= 0 whenever the weights are all 1)
   float* x_out;
   // edge arrays in global memory (sources larger than a stage)
   const int32_t* dst_g;
@@ -359,24 +361,23 @@ __device__ __forceinline__ float edge_alpha(const Ctx& cx, float w) {
   return W ? __frcp_rn(__fmul_rn(cx.gamma, w)) : cx.inv_gamma;
 }
 
-// Per-lane objective partials sum c x and sum w x^2: FP32 running sums with
-// an exact TwoSum compensation each (FMA-pipe work only).
-struct Acc {
-  float s = 0.f, e = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float t = __fadd_rn(s, v);
-    e = __fadd_rn(e, two_sum_err(s, v, t));
-    s = t;
-  }
-};
+// Per-lane objective partials sum c x and sum w x^2 in 64-bit fixed point
+// (scales 2^ec and 2^ew, chosen at create so that neither total can reach
+// 2^61): each term is rounded once to the grid, and the integer adds are
+// exact, so every partial, and the scalars made from them, are the same
+// whichever warp or CTA took which source.
 struct Sums {
-  Acc cx, wxx;
-  int units = 0;  // lone unweighted candidates: each adds exactly 1 to sum w x^2
+  long long cx = 0, wxx = 0;
   __device__ __forceinline__ void account(const Ctx& c, int j, float cv, float a, float w,
                                           float x) {
     c.scatter(j, __fmul_rn(a, x));
-    cx.add(__fmul_rn(cv, x));
-    wxx.add(__fmul_rn(w, __fmul_rn(x, x)));
+    cx += to_fixed(__fmul_rn(cv, x), c.sc);
+    wxx += to_fixed(__fmul_rn(w, __fmul_rn(x, x)), c.sw);
+  }
+  // a lone unweighted candidate: x = 1, so c x = c and w x^2 = 1 (one_w = 2^ew)
+  __device__ __forceinline__ void lone(const Ctx& c, float cv) {
+    cx += to_fixed(cv, c.sc);
+    wxx += c.one_w;
   }
 };
 
@@ -403,6 +404,11 @@ __device__ __forceinline__ void warp_pair_sum(float& h, float& l) {
   }
 }
 __device__ __forceinline__ double pair_value(float h, float l) { return (double)h + (double)l; }
+__device__ __forceinline__ double warp_dsum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // ------------------------------------- group projection, registers ----
 // G lanes own one source (32/G sources per warp), each lane holds up to K of
@@ -567,8 +573,7 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
       acc.account(cx, j, c, a, edge_w<W>(a), 1.f);
     } else {
       cx.scatter(j, a);
-      acc.cx.add(c);
-      ++acc.units;
+      acc.lone(cx, c);
     }
   }
   return gvalid && (mode == 1 || (mode == 2 && !lone));
@@ -755,16 +760,18 @@ __device__ __forceinline__ void epi_write(const EpiParams& q, double cxs, double
   q.eval_out[4] = mug;
 }
 
-// A warp's objective partials of one problem, added to its slot's FP64 pair
-// (batched pass; a few atomics per warp and slot).
-__device__ __forceinline__ void flush_sums(const Sums& acc, double* dst, int lane) {
-  float ch = acc.cx.s, cl = acc.cx.e, wh = acc.wxx.s, wl = acc.wxx.e;
-  pair_add(wh, wl, (float)acc.units);
-  warp_pair_sum(ch, cl);
-  warp_pair_sum(wh, wl);
+__device__ __forceinline__ long long warp_isum64(long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// A warp's objective partials of one problem, added to its slot's fixed-point
+// sums (batched pass; two integer atomics per warp and slot, exact in any order).
+__device__ __forceinline__ void flush_sums(const Sums& acc, long long* dst, int lane) {
+  const long long c = warp_isum64(acc.cx), w = warp_isum64(acc.wxx);
   if (lane == 0) {
-    atomicAdd(dst, pair_value(ch, cl));
-    atomicAdd(dst + 1, pair_value(wh, wl));
+    if (c) atomicAdd(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)c);
+    if (w) atomicAdd(reinterpret_cast<unsigned long long*>(dst) + 1, (unsigned long long)w);
   }
 }
 
@@ -827,6 +834,9 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     cx.h_y = p.h_y;
     cx.y = p.y;
     cx.sy = ldexpf(1.f, p.ey);
+    cx.sc = ldexpf(1.f, p.ec);
+    cx.sw = ldexpf(1.f, p.ew);
+    cx.one_w = p.ew >= 0 && p.ew <= 62 ? (1ll << p.ew) : 0ll;
     cx.gamma = p.gamma_dev ? *p.gamma_dev : p.gamma;
     cx.inv_gamma = __frcp_rn(cx.gamma);
     cx.dst_g = p.dst;
@@ -838,6 +848,9 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     cx.h_y = 0;
     cx.y = nullptr;
     cx.sy = 1.f;
+    cx.sc = 1.f;
+    cx.sw = 1.f;
+    cx.one_w = 0ll;
     cx.gamma = 1.f;
     cx.inv_gamma = 1.f;
     cx.dst_g = nullptr;
@@ -1057,6 +1070,9 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         cx.h_y = h_y;
         cx.y = d->y;
         cx.sy = d->sy;
+        cx.sc = ldexpf(1.f, d->ec);
+        cx.sw = ldexpf(1.f, d->ew);
+        cx.one_w = d->ew >= 0 && d->ew <= 62 ? (1ll << d->ew) : 0ll;
         cx.gamma = p.gamma_of[cur];
         cx.inv_gamma = __frcp_rn(cx.gamma);
         cx.dst_g = d->dst;
@@ -1153,21 +1169,17 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       const unsigned long long v = y_s[j];
       if (v != 0ull) atomicAdd(p.y + j, v);
     }
-    // per-CTA objective partials: FP32 pairs through the shuffle and warp
-    // trees; the units are exact small integers
-    float ch = acc.cx.s, cl = acc.cx.e, wh = acc.wxx.s, wl = acc.wxx.e;
-    pair_add(wh, wl, (float)acc.units);
-    warp_pair_sum(ch, cl);
-    warp_pair_sum(wh, wl);
-    float4* wred = reinterpret_cast<float4*>(dred);  // one per warp
-    if (lane == 0) wred[warp] = make_float4(ch, cl, wh, wl);
+    // per-CTA objective partials: exact integer sums through the shuffle and
+    // warp trees
+    const long long csum = warp_isum64(acc.cx), wsum = warp_isum64(acc.wxx);
+    longlong2* wred = reinterpret_cast<longlong2*>(dred);  // one per warp
+    if (lane == 0) wred[warp] = make_longlong2(csum, wsum);
     __syncthreads();
     if (tid == 0) {
-      float4 t = wred[0];
+      longlong2 t = wred[0];
       for (int w = 1; w < kThreads / 32; ++w) {
-        const float4 u = wred[w];
-        pair_addp(t.x, t.y, u.x, u.y);
-        pair_addp(t.z, t.w, u.z, u.w);
+        t.x += wred[w].x;
+        t.y += wred[w].y;
       }
       p.part[blockIdx.x] = t;
       // the last CTA to finish rewinds the tile counter for the next launch
@@ -1196,7 +1208,8 @@ __global__ void prep_mu_kernel(int32_t J, const float* __restrict__ lambda,
 
 __global__ void epilogue_kernel(EpiParams q) {
   __shared__ float4 red[32];
-  __shared__ float4 fin[2][32];
+  __shared__ long long finq[2][32];
+  __shared__ double find[2][32];
   __shared__ bool last;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   pdl_wait();  // A x and the partials of the pass
@@ -1222,34 +1235,41 @@ __global__ void epilogue_kernel(EpiParams q) {
   if (!last) return;
   __threadfence();
   // fixed-order combination of every partial (strided per thread, then a
-  // fixed shuffle tree and a fixed warp order)
-  float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // fixed shuffle tree and a fixed warp order): the pass's fixed-point sums
+  // exactly in 64-bit integers, the row partials in FP64
+  long long cq = 0, wq = 0;
+  double mg = 0.0, nn = 0.0;
   for (int k = threadIdx.x; k < q.npart; k += blockDim.x) {
-    const float4 u = __ldcg(q.part + k);
-    pair_addp(v[0], v[1], u.x, u.y);
-    pair_addp(v[2], v[3], u.z, u.w);
+    const longlong2 u = __ldcg(q.part + k);
+    cq += u.x;
+    wq += u.y;
   }
   for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
     const float4 u = __ldcg(q.epi_part + k);
-    pair_addp(v[4], v[5], u.x, u.y);
-    pair_addp(v[6], v[7], u.z, u.w);
+    mg += pair_value(u.x, u.y);
+    nn += pair_value(u.z, u.w);
   }
-  for (int i = 0; i < 8; i += 2) warp_pair_sum(v[i], v[i + 1]);
+  cq = warp_isum64(cq);
+  wq = warp_isum64(wq);
+  mg = warp_dsum(mg);
+  nn = warp_dsum(nn);
   if (lane == 0) {
-    fin[0][w] = make_float4(v[0], v[1], v[2], v[3]);
-    fin[1][w] = make_float4(v[4], v[5], v[6], v[7]);
+    finq[0][w] = cq;
+    finq[1][w] = wq;
+    find[0][w] = mg;
+    find[1][w] = nn;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    long long tc = 0, tw = 0;
+    double tm = 0.0, tn = 0.0;
     for (int k = 0; k < nw; ++k) {
-      pair_addp(t[0], t[1], fin[0][k].x, fin[0][k].y);
-      pair_addp(t[2], t[3], fin[0][k].z, fin[0][k].w);
-      pair_addp(t[4], t[5], fin[1][k].x, fin[1][k].y);
-      pair_addp(t[6], t[7], fin[1][k].z, fin[1][k].w);
+      tc += finq[0][k];
+      tw += finq[1][k];
+      tm += find[0][k];
+      tn += find[1][k];
     }
-    epi_write(q, pair_value(t[0], t[1]), pair_value(t[2], t[3]), pair_value(t[4], t[5]),
-              pair_value(t[6], t[7]));
+    epi_write(q, ldexp((double)tc, -q.ec), ldexp((double)tw, -q.ew), tm, tn);
     q.status->ticket = 0u;
   }
 }
@@ -1375,6 +1395,8 @@ static PassParams pass_params(const Problem& P, const float* gamma_dev, float ga
   p.gamma = gamma;
   p.y = P.y;
   p.ey = P.exp_y;
+  p.ec = P.exp_c;
+  p.ew = P.exp_w;
   p.part = P.part;
   p.x_out = x_out;
   p.status = P.status;
@@ -1433,7 +1455,7 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
 }
 
 cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, int64_t ntiles,
-                              const SlotDesc* slots, const float* gamma_of, double* slot_part,
+                              const SlotDesc* slots, const float* gamma_of, long long* slot_part,
                               DeviceStatus* status, int grid, int lean80, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   PassParams p{};
@@ -1468,6 +1490,8 @@ cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const
   q.sy = ldexpf(1.0f, -P.exp_y);
   q.grad = grad;
   q.part = P.part;
+  q.ec = P.exp_c;
+  q.ew = P.exp_w;
   q.npart = P.grid;
   q.epi_part = P.epi_part;
   q.gamma_dev = gamma_dev;

@@ -6,8 +6,9 @@
 //   epi    (J)  G = D (A x - b) and the FP64 scalars (pass.cu)
 //   norms  (J)  ||y - y_prev||, ||G - G_prev|| in FP64; the last block picks
 //               the step (secant estimate capped by max_step * gamma / gamma0),
-//               the momentum weight, the stopping scalars and the trace row,
-//               advances k and publishes gamma_{k+1}
+//               the momentum weight (reset when gamma changes, or when the
+//               dual objective fell: an adaptive restart), the stopping
+//               scalars and the trace row, advances k and publishes gamma_{k+1}
 //   step   (J)  lam+ = max(0, y + eta G); y+ = max(0, lam+ + beta (lam+ - lam)),
 //               or y+ = lam+ when gamma changes at k+1 (momentum restart);
 //               mu = D y+ for the next pass
@@ -29,6 +30,8 @@ struct SolveState {
   // options (read-only during the run)
   double gamma0, gamma_final, max_step, init_step, bnorm;
   int32_t halve_every, restart;
+  int32_t restart_dec;  // adaptive restart when the dual objective falls
+  int32_t pad0;
   double* trace;
   // iteration state
   int32_t k;
@@ -37,6 +40,9 @@ struct SolveState {
   float pad;
   double t, eta, beta;
   double gap_rel, infeas_rel, last_gamma;
+  double g_prev;   // dual objective of the previous evaluation
+  int32_t restarts;  // adaptive restarts taken so far
+  int32_t pad1;
   double eval[5];  // written by the epilogue
   unsigned ticket;
   int32_t pad2;
@@ -154,12 +160,17 @@ __global__ void solve_norms_kernel(int32_t J, SolveState* st, Vecs v, double* pa
   double eta;
   if (have_prev) eta = sdg > 0.0 ? fmin(eta_max, sqrt(sdy) / sqrt(sdg)) : eta_max;
   else eta = fmin(st->init_step, eta_max);
-  const double t = restart_at(*st, k) ? 1.0 : st->t;
+  const double g = st->eval[0], p = st->eval[1] + st->eval[2];
+  // momentum restarts at a gamma change and, adaptively, when the dual
+  // objective fell since the previous evaluation at the same gamma
+  const bool dec = st->restart_dec && have_prev && g < st->g_prev;
+  st->restarts += dec ? 1 : 0;
+  const double t = (restart_at(*st, k) || dec) ? 1.0 : st->t;
   const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
   st->eta = eta;
   st->beta = (t - 1.0) / tn;
   st->t = tn;
-  const double g = st->eval[0], p = st->eval[1] + st->eval[2];
+  st->g_prev = g;
   const double den = fmax(1.0, fmax(fabs(p), fabs(g)));
   st->gap_rel = fabs(st->eval[4]) / den;
   st->infeas_rel = st->eval[3] / fmax(1.0, st->bnorm);
@@ -394,6 +405,7 @@ void dualip_solve_opts_default(dualip_solve_opts* o) {
   o->restart_on_gamma_change = 1;
   o->stop_on_tol = 1;
   o->use_graph = 1;
+  o->restart_on_decrease = 1;
 }
 
 dualip_status dualip_solve(dualip_problem* h, const dualip_solve_opts* o, float* lambda_io,
@@ -426,6 +438,7 @@ dualip_status dualip_solve(dualip_problem* h, const dualip_solve_opts* o, float*
   H.bnorm = P.bnorm;
   H.halve_every = o->halve_every;
   H.restart = o->restart_on_gamma_change ? 1 : 0;
+  H.restart_dec = o->restart_on_decrease ? 1 : 0;
   H.trace = trace;
   H.t = 1.0;
   if ((e = cudaMemcpyAsync(C.st, &H, sizeof(H), cudaMemcpyHostToDevice, C.stream)))

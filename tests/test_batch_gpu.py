@@ -65,7 +65,10 @@ def test_batch_matches_lone_and_oracle(dl, storage, weighted):
             g1, e1 = P.dual_grad(lk, gammas[k])
             gk = g[B.joff[k]:B.joff[k + 1]]
             assert np.array_equal(gk, g1.cpu().numpy()), (shape, k)
-            for key in ("dual_obj", "primal_obj", "reg", "infeas_l2", "lambda_dot_grad"):
+            # c^T x and the ridge term are exact fixed-point sums: equal bit for bit
+            for key in ("primal_obj", "reg"):
+                assert evs[k][key] == e1[key], (shape, k, key)
+            for key in ("dual_obj", "infeas_l2", "lambda_dot_grad"):
                 assert abs(evs[k][key] - e1[key]) <= 1e-9 * max(1.0, abs(e1[key])), (k, key)
             if shape is None:
                 ref = decoded(x) if storage == "bf16" else x

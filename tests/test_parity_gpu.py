@@ -142,6 +142,28 @@ def test_empty_problem(dl):
 
 
 @pytest.mark.parametrize("weighted", [False, True])
+def test_evaluations_repeat_bit_for_bit(dl, weighted):
+    """The pass hands tiles to CTAs and sources to warps dynamically, yet every
+    output of an evaluation repeats exactly: A x and the objective partials are
+    fixed-point sums (exact in any order) and the per-row terms are reduced in
+    a fixed order."""
+    import torch
+
+    inst = synth.config("c2", scale=0.05)
+    P = dl.Problem.from_instance(inst, primal_scaling=weighted)
+    lam = torch.from_numpy(np.random.default_rng(9).uniform(0, 1.5, inst.J).astype(np.float32))
+    lam = lam.cuda()
+    for gamma in (1e-3, 0.1):
+        g0, e0 = P.dual_grad(lam, gamma)
+        g0 = g0.cpu().numpy()
+        for _ in range(4):
+            g1, e1 = P.dual_grad(lam, gamma)
+            assert np.array_equal(g1.cpu().numpy(), g0)
+            assert e1 == e0
+    P.close()
+
+
+@pytest.mark.parametrize("weighted", [False, True])
 def test_bf16_storage_parity(dl, weighted):
     inst = synth.config("c2", scale=0.01)
     rng = np.random.default_rng(4)
