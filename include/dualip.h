@@ -196,6 +196,11 @@ typedef struct {
   int32_t stop_on_tol;      /* 1: stop at the tolerances; 0: run exactly max_iters */
   int32_t use_graph;        /* 1: capture check_every iterations in one CUDA graph */
   int32_t restart_on_decrease; /* 1 (default): adaptive momentum restart, see above */
+  int32_t resume;           /* 0 (default): start from lambda_inout; 1: continue the
+                               handle's ascent (left by its last solve or by
+                               dualip_solve_state_import) at its iteration k, with
+                               its momentum, step history and gamma position;
+                               lambda_inout is then only written */
 } dualip_solve_opts;
 
 typedef struct {
@@ -222,6 +227,32 @@ void dualip_solve_opts_default(dualip_solve_opts* opts);
  */
 dualip_status dualip_solve(dualip_problem* p, const dualip_solve_opts* opts, float* lambda_inout,
                            dualip_solve_result* result, double* trace, void* stream);
+
+/*
+ * Saved ascent, for the recurring solves of the paper's production setting
+ * (Section 3: the same matching problem is solved again and again as its data
+ * drift) and for pre-empting a solve: the state that dualip_solve leaves in a
+ * handle (the normalised dual lambda', the extrapolated point y and the
+ * previous one, the last two gradients, the row scale, the iteration counter
+ * k that fixes gamma's place in the schedule, the momentum t, the step and
+ * the last scalars) as an opaque host buffer of dualip_solve_state_size()
+ * bytes; vectors are stored in the caller's destination numbering.
+ *   export: needs a handle that has run dualip_solve (or imported a state);
+ *           buffer (host) of at least the size; waits for `stream`.
+ *   import: into a handle of a problem with the same J (normally the same
+ *           problem, or its drifted data: same graph, new c, a or b); the next
+ *           dualip_solve with opts.resume = 1 continues from it.  An ascent
+ *           stopped after k iterations, exported, imported into a fresh handle
+ *           of the same problem and resumed for n more iterations ends exactly
+ *           (bit for bit) where k + n uninterrupted iterations end.
+ * Errors: DUALIP_EINVAL (NULL pointers, small buffer, no state to export, a
+ * buffer that is not a state or has another J), DUALIP_ENOMEM, DUALIP_ECUDA.
+ */
+dualip_status dualip_solve_state_size(const dualip_problem* p, int64_t* bytes);
+dualip_status dualip_solve_state_export(dualip_problem* p, void* buffer, int64_t bytes,
+                                        void* stream);
+dualip_status dualip_solve_state_import(dualip_problem* p, const void* buffer, int64_t bytes,
+                                        void* stream);
 
 /*
  * Dual evaluation that allocates nothing (the paper has no counterpart; this

@@ -36,6 +36,7 @@ EXPORTS = [
     "dualip_batch_profile_collect", "dualip_server_create", "dualip_server_submit",
     "dualip_server_poll", "dualip_server_wait", "dualip_server_get_stats",
     "dualip_server_destroy", "dualip_debug_abort_waits", "dualip_server_cancel",
+    "dualip_solve_state_size", "dualip_solve_state_export", "dualip_solve_state_import",
 ]
 DUALIP_REQ_QUEUED, DUALIP_REQ_RUNNING, DUALIP_REQ_DONE, DUALIP_REQ_FAILED = 0, 1, 2, 3
 
@@ -99,7 +100,8 @@ class SolveOpts(ctypes.Structure):
                 ("tol_gap", ctypes.c_double), ("tol_infeas", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("row_normalize", ctypes.c_int32),
                 ("restart_on_gamma_change", ctypes.c_int32), ("stop_on_tol", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("restart_on_decrease", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("restart_on_decrease", ctypes.c_int32),
+                ("resume", ctypes.c_int32)]
 
 
 class SolveResult(ctypes.Structure):
@@ -204,6 +206,12 @@ def lib() -> ctypes.CDLL:
         L.dualip_server_cancel.restype = st
         L.dualip_debug_abort_waits.argtypes = [vp, vp]
         L.dualip_debug_abort_waits.restype = st
+        L.dualip_solve_state_size.argtypes = [vp, ctypes.POINTER(i64)]
+        L.dualip_solve_state_size.restype = st
+        L.dualip_solve_state_export.argtypes = [vp, vp, i64, vp]
+        L.dualip_solve_state_export.restype = st
+        L.dualip_solve_state_import.argtypes = [vp, vp, i64, vp]
+        L.dualip_solve_state_import.restype = st
         L.dualip_last_error.argtypes = []
         L.dualip_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -313,6 +321,20 @@ def dualip_solve(h: int, opts: SolveOpts, lam_ptr: int, trace_ptr: int, stream: 
     st = lib().dualip_solve(h, ctypes.byref(opts), lam_ptr, ctypes.byref(r), trace_ptr, stream)
     _check(st, ok=(DUALIP_OK, DUALIP_ENOTCONVERGED))
     return r
+
+
+def dualip_solve_state_size(h: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().dualip_solve_state_size(h, ctypes.byref(n)))
+    return n.value
+
+
+def dualip_solve_state_export(h: int, buf_ptr: int, nbytes: int, stream: int) -> None:
+    _check(lib().dualip_solve_state_export(h, buf_ptr, nbytes, stream))
+
+
+def dualip_solve_state_import(h: int, buf_ptr: int, nbytes: int, stream: int) -> None:
+    _check(lib().dualip_solve_state_import(h, buf_ptr, nbytes, stream))
 
 
 def dualip_batch_create(handles) -> int:
@@ -522,6 +544,17 @@ class Problem:
         if trace:
             return lam, res, tr[: r.iters].cpu().numpy()
         return lam, res
+
+    def export_state(self, stream=None) -> np.ndarray:
+        """The handle's saved ascent (dualip_solve_state_export) as a byte array."""
+        buf = np.empty(dualip_solve_state_size(self.h), dtype=np.uint8)
+        dualip_solve_state_export(self.h, _ptr(buf), buf.nbytes, _stream(stream))
+        return buf
+
+    def import_state(self, buf: np.ndarray, stream=None) -> None:
+        """Load a saved ascent; the next solve(resume=1) continues from it."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        dualip_solve_state_import(self.h, _ptr(buf), buf.nbytes, _stream(stream))
 
 
 class Batch:

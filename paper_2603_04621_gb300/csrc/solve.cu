@@ -36,6 +36,8 @@ struct SolveState {
   // iteration state
   int32_t k;
   int32_t last_k;
+  int32_t k0;       // k at the start of this dualip_solve call (trace row 0)
+  int32_t pad_k;
   float gamma_f;  // gamma of the current iteration, read by the pass
   float pad;
   double t, eta, beta;
@@ -177,7 +179,7 @@ __global__ void solve_norms_kernel(int32_t J, SolveState* st, Vecs v, double* pa
   st->last_k = k;
   st->last_gamma = gk;
   if (st->trace) {
-    double* tr = st->trace + 8 * (size_t)k;
+    double* tr = st->trace + 8 * (size_t)(k - st->k0);
     tr[0] = gk;
     tr[1] = g;
     tr[2] = p;
@@ -223,6 +225,35 @@ __global__ void solve_final_kernel(int32_t J, Vecs v, const int32_t* __restrict_
     lam_out[orig_of[j]] = __fmul_rn(v.D[j], v.yp[j]);
 }
 
+// The six ascent vectors (lam', y, y_prev, G, G_prev, D) between the solver's
+// renumbered order and a [6][J] array in the caller's numbering.
+__global__ void state_gather_kernel(int32_t J, Vecs v, const int32_t* __restrict__ orig_of,
+                                    float* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = orig_of[j];
+    out[o] = v.lam[j];
+    out[J + o] = v.y[j];
+    out[2 * (int64_t)J + o] = v.yp[j];
+    out[3 * (int64_t)J + o] = v.G[j];
+    out[4 * (int64_t)J + o] = v.Gp[j];
+    out[5 * (int64_t)J + o] = v.D[j];
+  }
+}
+__global__ void state_scatter_kernel(int32_t J, Vecs v, const int32_t* __restrict__ orig_of,
+                                     const float* __restrict__ in) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = orig_of[j];
+    v.lam[j] = in[o];
+    v.y[j] = in[J + o];
+    v.yp[j] = in[2 * (int64_t)J + o];
+    v.G[j] = in[3 * (int64_t)J + o];
+    v.Gp[j] = in[4 * (int64_t)J + o];
+    v.D[j] = in[5 * (int64_t)J + o];
+  }
+}
+
 // D_j = (sum_{e -> j} a_e^2 / w_e)^(-1/2), 1 for a zero row (Section 5.1)
 __global__ void row_norm_kernel(const int32_t* __restrict__ dst, const float2* __restrict__ ca2,
                                 const uint32_t* __restrict__ ca, int64_t E, int weighted,
@@ -250,6 +281,7 @@ __global__ void fill_kernel(int32_t J, float* __restrict__ D, float v) {
 
 struct SolveCtx {
   int row_normalize = -1;  // row scale currently held in D (-1: none yet)
+  bool has_state = false;  // the vectors and SolveState hold an ascent (solve or import)
   float *lam = nullptr, *y = nullptr, *yp = nullptr, *G = nullptr, *Gp = nullptr, *D = nullptr;
   double* part = nullptr;
   SolveState* st = nullptr;
@@ -427,10 +459,22 @@ dualip_status dualip_solve(dualip_problem* h, const dualip_solve_opts* o, float*
   // order the private stream after the caller's stream
   if ((e = cudaEventRecord(C.ev, us)) || (e = cudaStreamWaitEvent(C.stream, C.ev, 0)))
     return cuda_fail(e, "ordering streams");
+  const bool resume = o->resume != 0;
+  if (resume && !C.has_state)
+    return fail(DUALIP_EINVAL, "resume needs a solver state (a previous solve or an import)");
+  if (resume && C.row_normalize != (o->row_normalize ? 1 : 0))
+    return fail(DUALIP_EINVAL, "resume needs the row normalisation of the saved state");
   if ((e = ensure_row_scale(P, C, o->row_normalize ? 1 : 0, C.stream)))
     return cuda_fail(e, "computing the row scale");
   SolveState& H = *C.st_host;
-  std::memset(&H, 0, sizeof(H));
+  if (resume) {  // the iteration state as it stands; the options from opts
+    if ((e = cudaMemcpyAsync(&H, C.st, sizeof(H), cudaMemcpyDeviceToHost, C.stream)) ||
+        (e = cudaStreamSynchronize(C.stream)))
+      return cuda_fail(e, "reading solver state");
+  } else {
+    std::memset(&H, 0, sizeof(H));
+    H.t = 1.0;
+  }
   H.gamma0 = o->gamma0;
   H.gamma_final = o->gamma_final;
   H.max_step = o->max_step;
@@ -440,13 +484,18 @@ dualip_status dualip_solve(dualip_problem* h, const dualip_solve_opts* o, float*
   H.restart = o->restart_on_gamma_change ? 1 : 0;
   H.restart_dec = o->restart_on_decrease ? 1 : 0;
   H.trace = trace;
-  H.t = 1.0;
+  H.k0 = H.k;
+  H.ticket = 0u;
   if ((e = cudaMemcpyAsync(C.st, &H, sizeof(H), cudaMemcpyHostToDevice, C.stream)))
     return cuda_fail(e, "uploading solver state");
+  C.has_state = true;
   {
     Vecs v{C.lam, C.y, C.yp, C.G, C.Gp, C.D};
-    solve_init_kernel<<<C.blocks, 256, 0, C.stream>>>(P.J, lambda_io, P.orig_of, v);
-    if ((e = cudaGetLastError())) return cuda_fail(e, "initialising the solver");
+    if (!resume) {
+      solve_init_kernel<<<C.blocks, 256, 0, C.stream>>>(P.J, lambda_io, P.orig_of, v);
+      if ((e = cudaGetLastError())) return cuda_fail(e, "initialising the solver");
+    }
+    // mu and gamma of the next iteration (a resumed ascent continues at k)
     solve_prep_kernel<<<C.blocks, 256, 0, C.stream>>>(P.J, C.st, v, P.mu_r);
     if ((e = cudaGetLastError())) return cuda_fail(e, "initialising the solver");
   }
@@ -487,6 +536,135 @@ dualip_status dualip_solve(dualip_problem* h, const dualip_solve_opts* o, float*
   }
   if (!converged && o->stop_on_tol)
     return fail(DUALIP_ENOTCONVERGED, "max_iters reached before the tolerances held");
+  return DUALIP_OK;
+}
+
+}  // extern "C"
+
+namespace dualip {
+namespace {
+// Saved ascent: this header, then lam', y, y_prev, G, G_prev and the row
+// scale D, J floats each, in the caller's destination numbering.
+struct StateHeader {
+  char magic[8];           // "DUALIPS1"
+  int32_t J, row_normalize;
+  int32_t k, last_k, restarts, pad;
+  double t, eta, beta, g_prev, gap_rel, infeas_rel, last_gamma;
+  double eval[5];
+};
+constexpr char kStateMagic[8] = {'D', 'U', 'A', 'L', 'I', 'P', 'S', '1'};
+int64_t state_bytes(int32_t J) { return (int64_t)sizeof(StateHeader) + 24 * (int64_t)J; }
+}  // namespace
+}  // namespace dualip
+
+extern "C" {
+
+dualip_status dualip_solve_state_size(const dualip_problem* h, int64_t* bytes) {
+  if (!h || !bytes) return fail(DUALIP_EINVAL, "handle and bytes must be non-NULL");
+  *bytes = state_bytes(h->p.J);
+  return DUALIP_OK;
+}
+
+dualip_status dualip_solve_state_export(dualip_problem* h, void* buf, int64_t bytes,
+                                        void* stream) {
+  NvtxRange nvtx_("dualip_solve_state_export");
+  if (!h || !buf) return fail(DUALIP_EINVAL, "handle and buffer must be non-NULL");
+  Problem& P = h->p;
+  if (bytes < state_bytes(P.J)) return fail(DUALIP_EINVAL, "buffer smaller than the state");
+  SolveCtx* C = static_cast<SolveCtx*>(P.solve_ctx);
+  if (!C || !C->has_state) return fail(DUALIP_EINVAL, "the handle holds no solver state");
+  cudaStream_t us = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  float* tmp = nullptr;
+  if ((e = cudaEventRecord(C->ev, us)) || (e = cudaStreamWaitEvent(C->stream, C->ev, 0)) ||
+      (e = cudaMemcpyAsync(C->st_host, C->st, sizeof(SolveState), cudaMemcpyDeviceToHost,
+                           C->stream)) ||
+      (e = cudaMallocAsync(&tmp, sizeof(float) * 6 * std::max<int32_t>(P.J, 1), C->stream)))
+    return cuda_fail(e, "reading solver state");
+  Vecs v{C->lam, C->y, C->yp, C->G, C->Gp, C->D};
+  state_gather_kernel<<<C->blocks, 256, 0, C->stream>>>(P.J, v, P.orig_of, tmp);
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  if (!(e = cudaGetLastError()))
+    e = cudaMemcpyAsync(out + sizeof(StateHeader), tmp, sizeof(float) * 6 * (size_t)P.J,
+                        cudaMemcpyDeviceToHost, C->stream);
+  cudaFreeAsync(tmp, C->stream);
+  if (!e) e = cudaStreamSynchronize(C->stream);
+  if (e) return cuda_fail(e, "exporting solver state");
+  const SolveState& S = *C->st_host;
+  StateHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kStateMagic, 8);
+  hd.J = P.J;
+  hd.row_normalize = C->row_normalize;
+  hd.k = S.k;
+  hd.last_k = S.last_k;
+  hd.restarts = S.restarts;
+  hd.t = S.t;
+  hd.eta = S.eta;
+  hd.beta = S.beta;
+  hd.g_prev = S.g_prev;
+  hd.gap_rel = S.gap_rel;
+  hd.infeas_rel = S.infeas_rel;
+  hd.last_gamma = S.last_gamma;
+  std::memcpy(hd.eval, S.eval, sizeof(hd.eval));
+  std::memcpy(out, &hd, sizeof(hd));
+  return DUALIP_OK;
+}
+
+dualip_status dualip_solve_state_import(dualip_problem* h, const void* buf, int64_t bytes,
+                                        void* stream) {
+  NvtxRange nvtx_("dualip_solve_state_import");
+  if (!h || !buf) return fail(DUALIP_EINVAL, "handle and buffer must be non-NULL");
+  Problem& P = h->p;
+  StateHeader hd;
+  if (bytes < (int64_t)sizeof(hd)) return fail(DUALIP_EINVAL, "buffer smaller than a state");
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, kStateMagic, 8) != 0)
+    return fail(DUALIP_EINVAL, "not a saved solver state");
+  if (hd.J != P.J || bytes < state_bytes(P.J))
+    return fail(DUALIP_EINVAL, "the saved state belongs to a problem of another size");
+  if ((hd.row_normalize != 0 && hd.row_normalize != 1) || hd.k < 0)
+    return fail(DUALIP_EINVAL, "corrupt solver state");
+  SolveCtx* Cp = nullptr;
+  cudaError_t e = solve_ctx_get(P, &Cp);
+  if (e) return cuda_fail(e, "allocating solver state");
+  SolveCtx& C = *Cp;
+  cudaStream_t us = static_cast<cudaStream_t>(stream);
+  SolveState& S = *C.st_host;
+  std::memset(&S, 0, sizeof(S));
+  S.bnorm = P.bnorm;
+  S.k = hd.k;
+  S.last_k = hd.last_k;
+  S.restarts = hd.restarts;
+  S.t = hd.t;
+  S.eta = hd.eta;
+  S.beta = hd.beta;
+  S.g_prev = hd.g_prev;
+  S.gap_rel = hd.gap_rel;
+  S.infeas_rel = hd.infeas_rel;
+  S.last_gamma = hd.last_gamma;
+  std::memcpy(S.eval, hd.eval, sizeof(S.eval));
+  float* tmp = nullptr;
+  if ((e = cudaEventRecord(C.ev, us)) || (e = cudaStreamWaitEvent(C.stream, C.ev, 0)) ||
+      (e = cudaMemcpyAsync(C.st, &S, sizeof(S), cudaMemcpyHostToDevice, C.stream)) ||
+      (e = cudaMallocAsync(&tmp, sizeof(float) * 6 * std::max<int32_t>(P.J, 1), C.stream)) ||
+      (e = cudaMemcpyAsync(tmp, static_cast<const unsigned char*>(buf) + sizeof(hd),
+                           sizeof(float) * 6 * (size_t)P.J, cudaMemcpyHostToDevice, C.stream))) {
+    if (tmp) cudaFreeAsync(tmp, C.stream);
+    C.has_state = false;  // the device state may be half written
+    return cuda_fail(e, "importing solver state");
+  }
+  Vecs v{C.lam, C.y, C.yp, C.G, C.Gp, C.D};
+  state_scatter_kernel<<<C.blocks, 256, 0, C.stream>>>(P.J, v, P.orig_of, tmp);
+  e = cudaGetLastError();
+  cudaFreeAsync(tmp, C.stream);
+  if (!e) e = cudaStreamSynchronize(C.stream);
+  if (e) {
+    C.has_state = false;
+    return cuda_fail(e, "importing solver state");
+  }
+  C.row_normalize = hd.row_normalize;
+  C.has_state = true;
   return DUALIP_OK;
 }
 

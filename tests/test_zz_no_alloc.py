@@ -63,7 +63,7 @@ def noalloc(dl, inst, dev, lam, gamma, weighted):
     return grad.cpu().numpy().astype(np.float64), out.cpu().numpy()
 
 
-def check_oracle(inst, g, o, eo, factor=1.0):
+def check_oracle(inst, g, o, eo, lam, factor=1.0):
     b = inst.b.astype(np.float64)
     tol = factor * (GRAD_RTOL * (np.abs(eo.ax) + np.abs(b)) + 1e-6)
     err = np.abs(g - eo.grad)
@@ -71,6 +71,9 @@ def check_oracle(inst, g, o, eo, factor=1.0):
     for k, ref in zip(KEYS, (eo.dual, eo.primal_lin, eo.reg, eo.infeas, eo.mu_dot_grad)):
         if k == "infeas_l2":
             bound = 1e-5 * max(1.0, ref) + 1e-6 * np.linalg.norm(b)
+        elif k == "lambda_dot_grad":  # a dot product that may cancel: relative to its terms
+            terms = np.abs(np.asarray(lam, np.float64)) * (np.abs(eo.ax) + np.abs(b))
+            bound = OBJ_RTOL * max(1.0, float(terms.sum()))
         else:
             bound = OBJ_RTOL * max(1.0, abs(ref))
         assert abs(o[KEYS.index(k)] - ref) <= factor * bound, (k, o[KEYS.index(k)], ref)
@@ -91,16 +94,21 @@ def test_noalloc_matches_oracle_and_handle_path(dl, weighted):
         lam = torch.from_numpy(lam_h).cuda()
         g, o = noalloc(dl, inst, dev, lam, gamma, weighted)
         eo = Po.eval(lam_h.astype(np.float64), gamma)
-        check_oracle(inst, g, o, eo)
+        check_oracle(inst, g, o, eo, lam_h)
         ref_grad, ref = P.dual_grad(lam, gamma)
         torch.cuda.synchronize()
         gr = ref_grad.cpu().numpy().astype(np.float64)
         b = inst.b.astype(np.float64)
         tol = 2 * (GRAD_RTOL * (np.abs(gr + b) + np.abs(b)) + 1e-6)
         assert np.all(np.abs(g - gr) <= tol), (call, np.max(np.abs(g - gr) / tol))
+        dot_scale = float(np.sum(np.abs(lam_h) * (np.abs(gr + b) + np.abs(b))))
         for k, key in enumerate(KEYS):
             scale = max(1.0, abs(ref[key]))
-            bound = 2e-6 * scale if key != "infeas_l2" else 2e-5 * scale + 2e-6 * np.linalg.norm(b)
+            bound = 2e-6 * scale
+            if key == "infeas_l2":
+                bound = 2e-5 * scale + 2e-6 * np.linalg.norm(b)
+            elif key == "lambda_dot_grad":
+                bound = 2e-6 * max(1.0, dot_scale)
             assert abs(o[k] - ref[key]) <= bound, (call, key, o[k], ref[key])
     if gamma == 100.0:
         # the slack branch was taken: some source has sum x < 1 with x > 0
@@ -121,14 +129,14 @@ def test_noalloc_no_sources_and_empty_sources(dl):
                            np.zeros(0, np.float32), rng.uniform(0.5, 2, J).astype(np.float32), J)
     g, o = noalloc(dl, empty, to_dev(empty), lam, 1e-3, False)
     assert np.array_equal(g, -empty.b.astype(np.float64))
-    check_oracle(empty, g, o, oracle.Problem(empty).eval(lam_h.astype(np.float64), 1e-3))
+    check_oracle(empty, g, o, oracle.Problem(empty).eval(lam_h.astype(np.float64), 1e-3), lam_h)
     # sources with no edges between ordinary ones
     deg = np.array([0, 5, 0, 0, 40, 1, 0, 300, 0])
     inst = synth.from_degrees(deg, J, 13, synth.DST_UNIFORM, b_frac=0.4)
     Po = oracle.Problem(inst)
     for gamma in (1e-3, 0.5):
         g, o = noalloc(dl, inst, to_dev(inst), lam, gamma, False)
-        check_oracle(inst, g, o, Po.eval(lam_h.astype(np.float64), gamma))
+        check_oracle(inst, g, o, Po.eval(lam_h.astype(np.float64), gamma), lam_h)
 
 
 def test_noalloc_out_of_range_destination(dl):
@@ -146,7 +154,7 @@ def test_noalloc_out_of_range_destination(dl):
     assert np.all(np.isnan(g)) and np.all(np.isnan(o))
     dev["dst"][inst.E // 2] = int(inst.dst[inst.E // 2])
     g, o = noalloc(dl, inst, dev, lam, 1e-3, False)
-    check_oracle(inst, g, o, oracle.Problem(inst).eval(lam_h.astype(np.float64), 1e-3))
+    check_oracle(inst, g, o, oracle.Problem(inst).eval(lam_h.astype(np.float64), 1e-3), lam_h)
 
 
 def test_noalloc_rejects_too_many_destinations(dl):
