@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "appb"],
                     help="c2: 1M x 10k, ~50M edges (default); c3: 25M x 1M, ~2.0B edges; "
                          "c4: 256 problems in one batched pass, ~3.4B edges; "
                          "c5: a Poisson stream of solve requests through the server")
@@ -673,6 +673,72 @@ def run_serve(args):
     return 0
 
 
+def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0):
+    """The paper's two ablations on its own generator (Appendix B), at 1/25 of
+    the Section 7 size (10k resources, 10 edges per request):
+    * Jacobi row normalisation (Section 5.1) on and off, at a fixed gamma of
+      0.01 (Section 7's setting): iterations to the 1e-4 gap and the dual
+      objective's distance to the best value reached, log10 |g_k - g*|;
+    * gamma continuation 0.16 -> 0.01, halved every 25 iterations (Section 7),
+      against gamma fixed at 0.01."""
+    import synth
+
+    inst = synth.appb(I, J, nu)
+    P = d.Problem.from_instance(inst)
+    lam = torch.zeros(inst.J, dtype=torch.float32, device="cuda")
+    grad = torch.empty(inst.J, dtype=torch.float32, device="cuda")
+    out_dev = torch.empty(8, dtype=torch.float64, device="cuda")
+    sp = int(torch.cuda.current_stream().cuda_stream)
+
+    def step():
+        d.dualip_dual_grad_async(P.h, lam.data_ptr(), 0.01, grad.data_ptr(), out_dev.data_ptr(),
+                                 sp)
+
+    for _ in range(5):
+        step()
+    k = profiled(d, P.h, 50, step)
+    fixed = dict(gamma0=0.01, gamma_final=0.01, halve_every=0, max_iters=3000)
+    runs = {
+        "row_normalize_on": dict(row_normalize=1, **fixed),
+        "row_normalize_off": dict(row_normalize=0, **fixed),
+        "continuation_0.16_to_0.01": dict(gamma0=0.16, gamma_final=0.01, halve_every=25,
+                                          max_iters=3000),
+    }
+    res, traces = {}, {}
+    for name, o in runs.items():
+        P.solve(max_iters=20, **{kk: v for kk, v in o.items() if kk != "max_iters"})  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, r, tr = P.solve(trace=True, **o)
+        torch.cuda.synchronize()
+        res[name] = {"seconds": time.perf_counter() - t0, "iters": r["iters"],
+                     "converged": r["converged"], "gap_rel": r["gap_rel"],
+                     "infeas_rel": r["infeas_rel"], "dual_obj": r["dual_obj"]}
+        traces[name] = tr
+    # the fixed-gamma runs share one objective (gamma = 0.01): distance to the best
+    # value either reached, at a few iteration counts
+    g_star = max(float(np.max(traces[n][:, 1])) for n in ("row_normalize_on",
+                                                            "row_normalize_off"))
+    for name in ("row_normalize_on", "row_normalize_off"):
+        g = traces[name][:, 1]
+        res[name]["log10_gap_to_best"] = {
+            str(it): float(np.log10(max(g_star - g[min(it, len(g)) - 1], 1e-300)))
+            for it in (10, 25, 50, 100, 200, 500, 1000, 3000)}
+    res["fixed_gamma_0.01"] = res["row_normalize_on"]
+    P.close()
+    rown = np.sqrt(np.bincount(inst.dst, weights=inst.a.astype(np.float64) ** 2,
+                               minlength=inst.J))
+    return {"workload": f"Appendix B generator: {I} requests x {J} resources, {nu:g} edges per "
+                        "request, lognormal breadth, greedy-load budgets (unstated laws: "
+                        "synth.APPB_DEFAULTS)",
+            "I": inst.I, "J": inst.J, "E": inst.E,
+            "row_norm_p1_p50_p99": [float(x) for x in np.percentile(rown[rown > 0],
+                                                                    [1, 50, 99])],
+            "pass": {"kernel_ms": k["pass"], "edges_per_s": inst.E / (k["pass"] / 1e3),
+                     "roofline": roofline(algorithmic_bytes(inst), k["pass"], peak, note)},
+            "solves": res}
+
+
 def forms(d, torch, args, plain, peak, note):
     """The BF16, batched and serving forms beside the plain FP32 form (c2)."""
     import synth
@@ -691,7 +757,32 @@ def forms(d, torch, args, plain, peak, note):
     f, _ = batch_form(d, torch, 20, 3, 1.0, "f32", True, peak, note)
     out["batched_c4"] = f
     out["serving_c5"] = serve_form(d, torch, args.form_requests, args.budget_gib)
+    out["appendix_b_ablations"] = appb_ablations(d, torch, peak, note)
     return out
+
+
+def run_appb(args):
+    """The Appendix B generator's instance: pass roofline and the two ablations."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2603_04621_gb300 import build
+
+    build.build()
+    import paper_2603_04621_gb300 as d
+
+    peak, note = load_peak()
+    f = appb_ablations(d, torch, peak, note, I=max(1, int(1_000_000 * args.scale)))
+    ms = f["pass"]["kernel_ms"]
+    out = {"metric": METRIC, "value": f["pass"]["edges_per_s"], "unit": UNIT, "n_gpus": 1,
+           "steps": 50, "warmup": 5, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f["workload"], "I": f["I"], "J": f["J"], "E": f["E"],
+                      "gamma": 0.01, "parallelism": "replicas"},
+           "roofline": f["pass"]["roofline"], "ablations": f["solves"],
+           "row_norm_p1_p50_p99": f["row_norm_p1_p50_p99"]}
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_ours(args):
@@ -699,6 +790,8 @@ def run_ours(args):
         return run_batch(args)
     if args.workload == "c5":
         return run_serve(args)
+    if args.workload == "appb":
+        return run_appb(args)
     import torch
 
     ws, rank, local = dist_env()

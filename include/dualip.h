@@ -49,6 +49,14 @@ typedef enum {
 
 typedef enum { DUALIP_EDGE_F32 = 0, DUALIP_EDGE_BF16 = 1 } dualip_edge_dtype;
 
+/* The simple constraint set C of the primal (Section 3.2, Eqs. 4-5; Section
+ * 4's projection maps, Section 6's batched projections):
+ *   DUALIP_PROJ_SIMPLEX  each source's block in {x_i >= 0, sum_j x_ij <= 1}
+ *   DUALIP_PROJ_BOX      every edge in [0, 1] (the unit-box clamp)
+ * Box problems are evaluated and solved on their own handles; the batched and
+ * serving forms and dualip_dual_grad_noalloc take simplex problems only. */
+typedef enum { DUALIP_PROJ_SIMPLEX = 0, DUALIP_PROJ_BOX = 1 } dualip_projection;
+
 /*
  * Source-major edge list (the paper's CSC tensor T of Section 6, "Sparse
  * tensor computation": one column per source i holding diag(D_i), so the
@@ -66,6 +74,7 @@ typedef enum { DUALIP_EDGE_F32 = 0, DUALIP_EDGE_BF16 = 1 } dualip_edge_dtype;
  *   storage      DUALIP_EDGE_F32 keeps c and a in FP32; DUALIP_EDGE_BF16 stores
  *                them as bfloat16 (round to nearest even) and computes in FP32
  *   primal_scaling  0: w_e = 1; 1: w_e = a_e^2 (1 where a_e = 0)
+ *   projection   DUALIP_PROJ_SIMPLEX (0) or DUALIP_PROJ_BOX (1), see above
  * dualip_create copies everything into library-owned device memory; the
  * caller keeps ownership of its arrays and may free them on return.
  */
@@ -81,6 +90,7 @@ typedef struct {
   int32_t inputs_on_device;
   int32_t storage;
   int32_t primal_scaling;
+  int32_t projection;  /* dualip_projection: the simple constraint set C */
 } dualip_problem_desc;
 
 /* Scalars of one dual evaluation, computed on the GPU in FP64 (Section 6: the

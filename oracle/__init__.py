@@ -76,6 +76,8 @@ def _load():
         lib.oracle_solve.argtypes = [vp, ctypes.POINTER(SolveOpts), vp,
                                      ctypes.POINTER(SolveResult), vp]
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_box.argtypes = [vp, ctypes.c_int]
+        lib.oracle_set_box.restype = None
         _lib = lib
     return _lib
 
@@ -119,7 +121,7 @@ class Eval:
 class Problem:
     """One matching LP held by the oracle (keeps references to the arrays)."""
 
-    def __init__(self, inst, weighted: bool = False):
+    def __init__(self, inst, weighted: bool = False, box: bool = False):
         self._lib = _load()
         self.inst = inst
         self._keep = [np.ascontiguousarray(inst.off, dtype=np.int64),
@@ -134,6 +136,8 @@ class Problem:
                                           int(weighted))
         if not self._h:
             raise MemoryError("oracle_create failed")
+        self.box = bool(box)
+        self._lib.oracle_set_box(self._h, int(box))
 
     def close(self):
         if getattr(self, "_h", None):

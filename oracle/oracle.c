@@ -132,6 +132,7 @@ typedef struct oracle_problem {
   const int32_t* dst;
   const float *c, *a, *b;
   int weighted;
+  int box;         /* C = [0, 1]^E (the unit-box clamp) instead of per-source simplices */
   int64_t* tix;    /* edges in destination-major order, ascending edge index */
   int64_t* toff;   /* [J+1] */
   int64_t dmax;
@@ -169,6 +170,11 @@ oracle_problem* oracle_create(int64_t I, int32_t J, const int64_t* off, const in
   free(fill);
   return p;
 }
+
+/* Switch the simple constraint set to the unit box [0, 1]^E (Section 6's
+ * unit-box clamp map).  The block problem then separates by edge: each x_e
+ * minimises x^2 / (2 alpha_e) - r_e x over [0, 1], so x_e = min(1, alpha_e (r_e)_+). */
+void oracle_set_box(oracle_problem* p, int box) { p->box = box ? 1 : 0; }
 
 /* ridge weight of an edge: w_e = a_e^2 (1 where a_e = 0) with primal scaling, else 1 */
 static inline double edge_w(const oracle_problem* p, int64_t e) {
@@ -257,11 +263,13 @@ int oracle_eval(const oracle_problem* p, const double* mu, double gamma, int met
             r[k] = -((double)p->c[e] + (double)p->a[e] * mu[p->dst[e]]);
             al[k] = 1.0 / (gamma * edge_w(p, e));
           }
-          double tau = method == 0 ? tau_sort(d, r, al, buf) : tau_michelot(d, r, al, in);
+          double tau = 0.0;
+          if (!p->box) tau = method == 0 ? tau_sort(d, r, al, buf) : tau_michelot(d, r, al, in);
           nsum_t lin = {0, 0}, cx = {0, 0}, wxx = {0, 0};
           for (int64_t k = 0; k < d; ++k) {
             int64_t e = e0 + k;
             double xe = r[k] > tau ? al[k] * (r[k] - tau) : 0.0;
+            if (p->box && xe > 1.0) xe = 1.0;
             x[e] = xe;
             nsum_add(&lin, -r[k] * xe);
             nsum_add(&cx, (double)p->c[e] * xe);

@@ -21,6 +21,7 @@ DUALIP_OK, DUALIP_EINVAL, DUALIP_ENOMEM, DUALIP_ECUDA = 0, 1, 2, 3
 DUALIP_ETIMEOUT, DUALIP_EBUSY, DUALIP_ENOTCONVERGED, DUALIP_EDEVICE = 4, 5, 6, 7
 DUALIP_ECANCELED = 8
 DUALIP_EDGE_F32, DUALIP_EDGE_BF16 = 0, 1
+DUALIP_PROJ_SIMPLEX, DUALIP_PROJ_BOX = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY",
                 6: "ENOTCONVERGED", 7: "EDEVICE", 8: "ECANCELED"}
 
@@ -81,7 +82,8 @@ class ProblemDesc(ctypes.Structure):
                 ("num_dests", ctypes.c_int32), ("src_offsets", ctypes.c_void_p),
                 ("dst", ctypes.c_void_p), ("c", ctypes.c_void_p), ("a", ctypes.c_void_p),
                 ("b", ctypes.c_void_p), ("inputs_on_device", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("primal_scaling", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("primal_scaling", ctypes.c_int32),
+                ("projection", ctypes.c_int32)]
 
 
 class Eval(ctypes.Structure):
@@ -458,7 +460,7 @@ class Problem:
     """
 
     def __init__(self, off, dst, c, a, b, J: int, storage: str = "f32",
-                 primal_scaling: bool = False, stream=None):
+                 primal_scaling: bool = False, projection: str = "simplex", stream=None):
         import torch
 
         on_dev = isinstance(off, torch.Tensor) and off.is_cuda
@@ -476,7 +478,8 @@ class Problem:
         d = ProblemDesc(I, E, int(J), _ptr(off), _ptr(dst), _ptr(c), _ptr(a), _ptr(b),
                         1 if on_dev else 0,
                         DUALIP_EDGE_BF16 if storage == "bf16" else DUALIP_EDGE_F32,
-                        1 if primal_scaling else 0)
+                        1 if primal_scaling else 0,
+                        DUALIP_PROJ_BOX if projection == "box" else DUALIP_PROJ_SIMPLEX)
         self.h = dualip_create(d, _stream(stream))
         self._keep = None
         self.device = torch.device("cuda", torch.cuda.current_device())

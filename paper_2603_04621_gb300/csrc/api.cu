@@ -140,6 +140,8 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     return fail(DUALIP_EINVAL, "unknown edge storage");
   if (d->primal_scaling != 0 && d->primal_scaling != 1)
     return fail(DUALIP_EINVAL, "primal_scaling must be 0 or 1");
+  if (d->projection != DUALIP_PROJ_SIMPLEX && d->projection != DUALIP_PROJ_BOX)
+    return fail(DUALIP_EINVAL, "unknown projection");
   if (d->inputs_on_device != 0 && d->inputs_on_device != 1)
     return fail(DUALIP_EINVAL, "inputs_on_device must be 0 or 1");
   cudaStream_t s = as_stream(stream);
@@ -161,14 +163,14 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     if (off[i + 1] < off[i]) return fail(DUALIP_EINVAL, "src_offsets must be nondecreasing");
   if (off[I] != E) return fail(DUALIP_EINVAL, "src_offsets[I] must equal num_edges");
 
-  // Degree order: when the degrees spread widely, sources are stored by
+  // Degree order: when the pass's cost model says so, sources are stored by
   // increasing degree (ties in the caller's order), so that the pass's
   // batches of eight consecutive sources have similar spans and one window
   // width serves all eight.  Sources are independent blocks of the problem:
-  // only the order of the objective's partial sums changes, and
+  // the gradient and the objective partials are exact sums in any order, and
   // dualip_get_primal maps x back to the caller's order.
   std::vector<int64_t> src_of, off_st;
-  if (degrees_spread_widely(off)) degree_order(off, src_of, off_st);
+  choose_degree_order(off, tile_edges_for(d->storage), kTileSources, src_of, off_st);
   const bool seg = !src_of.empty();
   const std::vector<int64_t>& off_s = seg ? off_st : off;  // offsets as stored
 
@@ -180,6 +182,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   P.J = J;
   P.storage = d->storage;
   P.weighted = d->primal_scaling;
+  P.box = d->projection == DUALIP_PROJ_BOX ? 1 : 0;
   P.last_stream = s;
   auto bail = [&](dualip_status st) {
     cudaStreamSynchronize(s);

@@ -59,6 +59,14 @@ constexpr bool kSmemRed64 = DUALIP_SMEM_RED64 != 0;  // shared bins: one 64-bit 
 #define DUALIP_WAIT_HINT_NS 0
 #endif
 constexpr unsigned kWaitHintNs = DUALIP_WAIT_HINT_NS;  // mbarrier suspend hint (0: none)
+// Unweighted sources that the lane groups leave (unsaturated, near-ties) and
+// whose span fits a warp's registers take the candidate path (1) instead of
+// the multi-pass path (0).
+#ifndef DUALIP_WARP_CAND
+#define DUALIP_WARP_CAND 1
+#endif
+constexpr bool kWarpCand = DUALIP_WARP_CAND != 0;
+constexpr int kCandRounds = 16;  // Michelot rounds before the multi-pass path takes over
 constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
 constexpr int kMaxCachedDests = 10240; // hot destinations whose mu lives in smem
 constexpr int kMaxPrivDests = DUALIP_PRIV_DESTS;  // hot destinations accumulated in smem
@@ -191,6 +199,7 @@ struct Problem {
   int32_t J = 0;
   int storage = DUALIP_EDGE_F32;
   int weighted = 0;
+  int box = 0;  // projection onto the unit box [0, 1]^E instead of per-source simplices
   int64_t ntiles = 0;
   int h_mu = 0, h_y = 0;
   int num_sms = 0, grid = 0;

@@ -695,6 +695,119 @@ __device__ __forceinline__ void project_multipass(const View& v, int64_t base, i
   }
 }
 
+// Unweighted sources of at most 512 edges that the lane groups leave
+// (unsaturated, or several edges within gamma of the top).  One pass over the
+// staged source keeps each lane's FP32 scores r = -(c + a mu) (which equal the
+// high word of the exact pair) in registers and finds r_max and the saturation
+// sum.  The candidate edges, r > 0 when the sum constraint is slack and
+// r - r_max > lb otherwise (a set that holds the active set), are marked in a
+// bit mask, and only they are revisited: Michelot's rounds recompute their
+// exact shifted scores d = (hi - r_max) + lo, as the multi-pass path does,
+// and x = (d - t) / gamma goes out.  Near-ties have two or three candidates,
+// so the rounds cost little, and the code exists once, keeping the kernel's
+// instruction footprint small.  Returns false, having accounted nothing, if
+// the rounds have not settled after kCandRounds (the multi-pass path then
+// projects the source).
+template <bool BF16, bool MU_SMEM>
+__device__ __forceinline__ bool project_warp_cand(const StageView<BF16>& sv, int base, int d,
+                                                  int lane, const Ctx& cx, Sums& acc) {
+  constexpr int K = 16;  // 512 / 32 edges per lane
+  float rf[K];
+  float rmax = -CUDART_INF_F, s0 = 0.f;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int k = lane + 32 * i;
+    float r = -CUDART_INF_F;
+    if (k < d) {
+      int j;
+      float c, a;
+      sv.edge(base + k, j, c, a);
+      r = -__fmaf_rn(a, MU_SMEM ? cx.mu_smem(j) : cx.mu(j), c);
+    }
+    rf[i] = r;
+    rmax = fmaxf(rmax, r);
+    s0 += fmaxf(r, 0.f);
+  }
+  rmax = warp_max(rmax);
+  s0 = warp_sum(s0);
+  const int mode = rmax <= 0.f ? 0 : (__fmul_rn(s0, cx.inv_gamma) <= 1.f ? 1 : 2);
+  if (mode == 0) return true;  // every x is 0
+  const float lb = __fsub_rn(-cx.gamma, __fmul_rn(fabsf(rmax), 0x1p-20f));
+  unsigned cm = 0u;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    cm |= (mode == 1 ? rf[i] > 0.f : __fsub_rn(rf[i], rmax) > lb) ? (1u << i) : 0u;
+  auto shifted = [&](int k, int& j, float& c, float& a) {
+    float hi, lo;
+    sv.edge(base + k, j, c, a);
+    score(c, a, MU_SMEM ? cx.mu_smem(j) : cx.mu(j), hi, lo);
+    return __fadd_rn(__fsub_rn(hi, rmax), lo);
+  };
+  float t = 0.f;
+  if (mode == 2) {
+    float theta = lb, nprev = -1.f;
+    bool settled = false;
+    for (int it = 0; it < kCandRounds; ++it) {
+      float sr = 0.f, n = 0.f;
+      for (unsigned m = cm; m; m &= m - 1u) {
+        int j;
+        float c, a;
+        const float dk = shifted(lane + 32 * (__ffs(m) - 1), j, c, a);
+        if (dk > theta) {
+          sr += dk;
+          n += 1.f;
+        }
+      }
+      sr = warp_sum(sr);
+      n = warp_sum(n);
+      if (n == nprev) {
+        settled = true;
+        break;
+      }
+      t = __fdiv_rn(sr - cx.gamma, n);
+      nprev = n;
+      theta = fmaxf(theta, t);
+    }
+    if (!settled) return false;
+  }
+  for (unsigned m = cm; m; m &= m - 1u) {
+    const int k = lane + 32 * (__ffs(m) - 1);
+    int j;
+    float c, a, x;
+    if (mode == 1) {
+      sv.edge(base + k, j, c, a);
+      const float r = -__fmaf_rn(a, MU_SMEM ? cx.mu_smem(j) : cx.mu(j), c);
+      x = __fmul_rn(cx.inv_gamma, r);  // r > 0 for a candidate
+    } else {
+      const float dk = shifted(k, j, c, a);
+      x = dk > t ? __fmul_rn(cx.inv_gamma, __fsub_rn(dk, t)) : 0.f;
+    }
+    if (x > 0.f) acc.account(cx, j, c, a, 1.f, x);
+  }
+  return true;
+}
+
+// The unit-box projection (Section 6's clamp map, x_e in [0, 1] with no sum
+// constraint): the block problem separates by edge, and its minimiser is
+// x = clamp(alpha r, 0, 1), alpha = 1 / (gamma w), r = -(c + a mu) formed by one
+// FMA (a single rounding), so x carries FP32 accuracy.  Edges [e0, e1) of the
+// view; x_out (WX) at e_glob0 + (k - e0).
+template <bool BF16, bool W, bool WX, class View>
+__device__ __forceinline__ void project_box(const View& v, int64_t e0, int64_t e1,
+                                            int64_t e_glob0, int lane, const Ctx& cx,
+                                            Sums& acc) {
+  for (int64_t k = e0 + lane; k < e1; k += 32) {
+    int j;
+    float c, a;
+    v.edge(k, j, c, a);
+    const float r = -__fmaf_rn(a, cx.mu(j), c);
+    const float w = edge_w<W>(a);
+    const float x = fminf(fmaxf(__fmul_rn(edge_alpha<W>(cx, w), r), 0.f), 1.f);
+    if (x > 0.f) acc.account(cx, j, c, a, w, x);
+    if (WX) cx.x_out[e_glob0 + (k - e0)] = x;
+  }
+}
+
 // J-length epilogue rows: (A x)_j from the fixed-point accumulator (which is
 // reset to zero for the next evaluation), grad = D (A x - b) in the caller's
 // numbering, and the partials lambda^T (A x - b) and ||(A x - b)_+||^2 as FP32
@@ -783,7 +896,7 @@ __device__ __forceinline__ void flush_sums(const Sums& acc, long long* dst, int 
 // a tile of another slot the consumer warps meet at a shared barrier, flush
 // the previous slot's shared bins and objective partials, load the new slot's
 // mu cache, and meet again; the producer never waits for them there.
-template <bool BF16, bool W, bool MU_SMEM, bool WRITE_X, bool BATCH>
+template <bool BF16, bool W, bool MU_SMEM, bool WRITE_X, bool BATCH, bool BOX = false>
 __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p) {
   using L = Layout<BF16>;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1080,7 +1193,34 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         cx.ca_g = d->ca;
       }
       const uint32_t claim_a = smem_u32(claim + s);
-      if (si.big) {
+      if (BOX) {
+        // unit-box projection: every edge on its own; a warp takes the edges
+        // of a claimed batch of eight sources (or of an oversized source)
+        if (si.big) {
+          unsigned b = 0u;
+          if (lane == 0) b = atoms_add_u32(claim_a, 1u);
+          b = __shfl_sync(0xffffffffu, b, 0);
+          if (b == 0u) {
+            GlobalView<BF16> gv{cx.dst_g, cx.ca2_g, cx.ca_g};
+            project_box<BF16, W, WRITE_X>(gv, si.e0, si.e1, si.e0, lane, cx, acc);
+          }
+        } else {
+          const StageView<BF16> sv = stage_view<BF16>(smem, s);
+          const int nsrc = (int)(si.s1 - si.s0);
+          const int li0 = (int)(si.s0 - si.o0);
+          const unsigned nb = (unsigned)((nsrc + 7) >> 3);
+          for (;;) {
+            unsigned bi = 0u;
+            if (lane == 0) bi = atoms_add_u32(claim_a, 1u);
+            bi = __shfl_sync(0xffffffffu, bi, 0);
+            if (bi >= nb) break;
+            const int li = li0 + 8 * (int)bi;
+            const int n8 = nsrc - 8 * (int)bi < 8 ? nsrc - 8 * (int)bi : 8;
+            const int e_lo = (int)(sv.off(li) - si.a0), e_hi = (int)(sv.off(li + n8) - si.a0);
+            project_box<BF16, W, WRITE_X>(sv, e_lo, e_hi, si.a0 + e_lo, lane, cx, acc);
+          }
+        }
+      } else if (si.big) {
         // the warp that claims it projects a source larger than a stage
         // straight from global memory
         unsigned b = 0u;
@@ -1144,7 +1284,11 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
             needm &= needm - 1u;
             const int b = __shfl_sync(0xffffffffu, bq, q);
             const int dd = __shfl_sync(0xffffffffu, dq, q);
-            project_multipass<BF16, W>(sv, (int64_t)b, (int64_t)dd, si.a0 + b, lane, cx, acc);
+            // (the result is the same for every lane: it follows warp sums)
+            const bool done = !W && !WRITE_X && kWarpCand && dd <= 512 &&
+                              project_warp_cand<BF16, MU_SMEM>(sv, b, dd, lane, cx, acc);
+            if (!done)
+              project_multipass<BF16, W>(sv, (int64_t)b, (int64_t)dd, si.a0 + b, lane, cx, acc);
           }
         }
       }
@@ -1348,9 +1492,9 @@ size_t pass_smem_bytes(int storage) {
   return storage == DUALIP_EDGE_BF16 ? Layout<true>::kTotal : Layout<false>::kTotal;
 }
 
-template <bool BF16, bool W, bool MU, bool WX, bool B = false>
+template <bool BF16, bool W, bool MU, bool WX, bool B = false, bool BOX = false>
 static cudaError_t set_smem() {
-  return cudaFuncSetAttribute(dualgrad_pass_kernel<BF16, W, MU, WX, B>,
+  return cudaFuncSetAttribute(dualgrad_pass_kernel<BF16, W, MU, WX, B, BOX>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Layout<BF16>::kTotal);
 }
@@ -1364,7 +1508,15 @@ cudaError_t configure_pass_kernels() {
       set_smem<false, false, false, true>(),  set_smem<false, true, false, true>(),
       set_smem<true, false, false, true>(),   set_smem<true, true, false, true>(),
       set_smem<false, false, false, false, true>(), set_smem<false, true, false, false, true>(),
-      set_smem<true, false, false, false, true>(),  set_smem<true, true, false, false, true>()};
+      set_smem<true, false, false, false, true>(),  set_smem<true, true, false, false, true>(),
+      set_smem<false, false, false, false, false, true>(),
+      set_smem<false, true, false, false, false, true>(),
+      set_smem<true, false, false, false, false, true>(),
+      set_smem<true, true, false, false, false, true>(),
+      set_smem<false, false, false, true, false, true>(),
+      set_smem<false, true, false, true, false, true>(),
+      set_smem<true, false, false, true, false, true>(),
+      set_smem<true, true, false, true, false, true>()};
   for (cudaError_t e : es)
     if (e != cudaSuccess) return e;
   return cudaSuccess;
@@ -1425,7 +1577,25 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
   cudaError_t e = cudaSuccess;
 #define DUALIP_LAUNCH(B, W, M, X) \
   e = launch_pdl(dualgrad_pass_kernel<B, W, M, X, false>, grid, block, smem, s, p)
-  if (x_out) {
+#define DUALIP_LAUNCH_BOX(B, W, X) \
+  e = launch_pdl(dualgrad_pass_kernel<B, W, false, X, false, true>, grid, block, smem, s, p)
+  if (P.box) {
+    if (x_out) {
+      if (bf16) {
+        if (P.weighted) DUALIP_LAUNCH_BOX(true, true, true);
+        else DUALIP_LAUNCH_BOX(true, false, true);
+      } else {
+        if (P.weighted) DUALIP_LAUNCH_BOX(false, true, true);
+        else DUALIP_LAUNCH_BOX(false, false, true);
+      }
+    } else if (bf16) {
+      if (P.weighted) DUALIP_LAUNCH_BOX(true, true, false);
+      else DUALIP_LAUNCH_BOX(true, false, false);
+    } else {
+      if (P.weighted) DUALIP_LAUNCH_BOX(false, true, false);
+      else DUALIP_LAUNCH_BOX(false, false, false);
+    }
+  } else if (x_out) {
     if (bf16) {
       if (P.weighted) DUALIP_LAUNCH(true, true, false, true);
       else DUALIP_LAUNCH(true, false, false, true);
@@ -1451,6 +1621,7 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
     }
   }
 #undef DUALIP_LAUNCH
+#undef DUALIP_LAUNCH_BOX
   return e;
 }
 

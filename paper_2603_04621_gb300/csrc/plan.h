@@ -40,21 +40,6 @@ inline void build_tiles(const std::vector<int64_t>& off, std::vector<int64_t>& t
   tile_e.push_back(off[I]);
 }
 
-// Degrees spread widely when their standard deviation exceeds 0.3 of their
-// mean.  Such problems are stored in degree order (dualip_create).
-inline bool degrees_spread_widely(const std::vector<int64_t>& off) {
-  const int64_t I = (int64_t)off.size() - 1;
-  if (I < 2) return false;
-  double s1 = 0.0, s2 = 0.0;
-  for (int64_t i = 0; i < I; ++i) {
-    const double d = (double)(off[i + 1] - off[i]);
-    s1 += d;
-    s2 += d * d;
-  }
-  const double mean = s1 / (double)I, var = s2 / (double)I - mean * mean;
-  return mean > 0.0 && var > 0.09 * mean * mean;
-}
-
 // Degree order: src_of[i] is the caller's source stored at position i, by
 // increasing degree with ties in the caller's order; off_st are the stored
 // offsets (off_st[i+1] - off_st[i] = the degree of src_of[i]).  A counting
@@ -81,6 +66,80 @@ inline void degree_order(const std::vector<int64_t>& off, std::vector<int64_t>& 
   off_st[0] = 0;
   for (int64_t i = 0; i < I; ++i)
     off_st[i + 1] = off_st[i] + (off[src_of[i] + 1] - off[src_of[i]]);
+}
+
+// Element slots the lane-group projection of the pass sweeps for a stored
+// order (its offsets off), tiled greedily with max_edges / max_sources: each
+// tile's sources go in batches of eight; a source's span is (first edge mod 4)
+// + degree; per batch, one round per 32/G sources of each group width G, a
+// round sweeping 32 lanes x 4 S slots: G = 4 for spans up to 64 (S = 4), or up
+// to 80 (S = 5 when some span exceeds 64) when lean80 is set and no span of the
+// batch lies in (80, 128]; G = 8, 16, 32 for spans up to 128, 256, 512 (S = 4).
+// A source with a longer span is counted as four passes over it.  Used to pick
+// the stored order: the kernel's cost per edge follows these slots.
+inline double lean_slots(const std::vector<int64_t>& off, int64_t max_edges, int64_t max_sources,
+                         bool lean80) {
+  std::vector<int64_t> tiles, tile_e;
+  build_tiles(off, tiles, tile_e, max_edges, max_sources);
+  double slots = 0.0;
+  for (size_t t = 0; t + 1 < tiles.size(); ++t) {
+    for (int64_t b = tiles[t]; b < tiles[t + 1]; b += 8) {
+      const int64_t be = std::min<int64_t>(b + 8, tiles[t + 1]);
+      int64_t sp[8];
+      bool mid = false, over64 = false;
+      for (int64_t q = b; q < be; ++q) {
+        const int64_t d = off[q + 1] - off[q];
+        sp[q - b] = d > 0 ? (off[q] & 3) + d : 0;
+        mid = mid || (sp[q - b] > 80 && sp[q - b] <= 128);
+      }
+      const int64_t span4 = (!lean80 || mid) ? 64 : 80;
+      int64_t n4 = 0, n8 = 0, n16 = 0, n32 = 0;
+      for (int64_t q = 0; q < be - b; ++q) {
+        const int64_t s = sp[q];
+        if (s == 0) continue;
+        if (s <= span4) {
+          ++n4;
+          over64 = over64 || s > 64;
+        } else if (s <= 128) {
+          ++n8;
+        } else if (s <= 256) {
+          ++n16;
+        } else if (s <= 512) {
+          ++n32;
+        } else {
+          slots += 4.0 * (double)s;
+        }
+      }
+      slots += (double)((n4 + 7) / 8) * 128.0 * (over64 ? 5 : 4);
+      slots += (double)((n8 + 3) / 4 + (n16 + 1) / 2 + n32) * 512.0;
+    }
+  }
+  return slots;
+}
+
+// The stored order of a problem: degree order (src_of, off_st filled) when the
+// cost model above gives it at least 5% fewer element slots than the caller's
+// order, for tiles of max_edges / max_sources; else the caller's order
+// (src_of, off_st left empty).  DUALIP_DEGREE_ORDER = 0 or 1 forces never or
+// always (for measurements).
+#ifndef DUALIP_DEGREE_ORDER
+#define DUALIP_DEGREE_ORDER -1
+#endif
+inline bool choose_degree_order(const std::vector<int64_t>& off, int64_t max_edges,
+                                int64_t max_sources, std::vector<int64_t>& src_of,
+                                std::vector<int64_t>& off_st) {
+  src_of.clear();
+  off_st.clear();
+  const int64_t I = (int64_t)off.size() - 1;
+  if (I < 2 || DUALIP_DEGREE_ORDER == 0) return false;
+  degree_order(off, src_of, off_st);
+  if (DUALIP_DEGREE_ORDER == 1) return true;
+  if (lean_slots(off_st, max_edges, max_sources, true) <
+      0.95 * lean_slots(off, max_edges, max_sources, true))
+    return true;
+  src_of.clear();
+  off_st.clear();
+  return false;
 }
 
 // Autotuner histogram bucket of a degree: 0 for degrees 0 and 1, else k for

@@ -39,7 +39,15 @@ DEG_FIXED, DEG_POISSON, DEG_UNIFORM = 0, 1, 2
 DST_UNIFORM, DST_ZIPF = 0, 1
 C_NEG_UNIFORM, C_NEG_LOGNORMAL = 0, 1
 
-CONFIG_SEEDS = {"c1": 1001, "c2": 1002, "c3": 1003, "c4": 1004, "c5": 1005}
+CONFIG_SEEDS = {"c1": 1001, "c2": 1002, "c3": 1003, "c4": 1004, "c5": 1005, "appb": 1006}
+
+# The unstated parameters of the paper's Appendix B generator (the paper gives
+# the laws' families only; these values are this library's choices):
+# lognormal scales of the resource breadth, the resource value scale v_j, the
+# request responsiveness u_i, the edge noise eps_ij and the per-resource
+# coefficient scale s_j; the value cap c_max; the budget slack eps.
+APPB_DEFAULTS = dict(sig_breadth=1.0, sig_v=0.5, sig_u=0.5, sig_eps=0.25, c_max=10.0, mu_s=0.0,
+                     sig_s=1.0, eps=0.01)
 
 
 def build(force: bool = False) -> str:
@@ -68,6 +76,9 @@ def _load():
         lib.synth_budgets.argtypes = [i64, i32, vp, vp, dbl, vp]
         lib.synth_budgets_greedy.argtypes = [i64, i32, vp, vp, vp, u64, dbl, dbl, dbl, vp]
         lib.synth_set_threads.argtypes = [ctypes.c_int]
+        lib.synth_appb_degrees.argtypes = [i64, i32, dbl, u64, dbl, vp, vp]
+        lib.synth_appb_fill.argtypes = [i64, i32, vp, u64, dbl, dbl, dbl, dbl, dbl, dbl, vp, vp,
+                                        vp, vp]
         _lib = lib
     return _lib
 
@@ -197,6 +208,34 @@ def config(name: str, scale: float = 1.0) -> Instance:
         return matching(max(1, int(25_000_000 * scale)), 1_000_000, seed, ("poisson", 80, 1, 2000),
                         name="c3" if scale == 1.0 else f"c3x{scale:g}")
     raise ValueError(name)
+
+
+def appb(I: int, J: int, nu: float = 10.0, seed: int = CONFIG_SEEDS["appb"], **params) -> Instance:
+    """The paper's Appendix B instance: I requests (sources), J resources
+    (destinations), nu edges per request on average, resource breadths
+    lognormal, K_j ~ Poisson(p_j I nu) distinct requests per resource, values
+    min(v_j u_i eps_ij, c_max) (c = -value), coefficients a = s_j value, and
+    greedy-load budgets b_j = rho_j (l_j + eps), rho_j ~ U[0.5, 1].  Unstated
+    parameters default to APPB_DEFAULTS."""
+    lib = _load()
+    p = dict(APPB_DEFAULTS, **params)
+    K = np.empty(J, dtype=np.int64)
+    E = ctypes.c_int64(0)
+    rc = lib.synth_appb_degrees(I, J, float(nu), seed, p["sig_breadth"], _ptr(K), ctypes.byref(E))
+    if rc:
+        raise ValueError(f"synth_appb_degrees failed ({rc})")
+    off = np.empty(I + 1, dtype=np.int64)
+    dst = np.empty(E.value, dtype=np.int32)
+    c = np.empty(E.value, dtype=np.float32)
+    a = np.empty(E.value, dtype=np.float32)
+    rc = lib.synth_appb_fill(I, J, _ptr(K), seed, p["sig_v"], p["sig_u"], p["sig_eps"],
+                             p["c_max"], p["mu_s"], p["sig_s"], _ptr(off), _ptr(dst), _ptr(c),
+                             _ptr(a))
+    if rc:
+        raise ValueError(f"synth_appb_fill failed ({rc})")
+    inst = Instance(off, dst, c, a, np.zeros(J, dtype=np.float32), J, name=f"appb{I}x{J}",
+                    meta=dict(seed=seed, nu=nu, **p))
+    return greedy_budgets(inst, seed=seed, eps=p["eps"])
 
 
 def batch_shapes(n: int = 256, seed: int = CONFIG_SEEDS["c4"], i_range=(1_000, 2_000_000),

@@ -284,6 +284,175 @@ int synth_budgets_greedy(int64_t I, int32_t J, const int64_t* off, const int32_t
   return SYN_OK;
 }
 
+/* ---- the paper's Appendix B generator ------------------------------------ */
+/*
+ * Resource-major draw (Appendix B, "Synthetic LP construction"), stored
+ * source-major: requests are the sources i, resources the destinations j.
+ * The paper names the families of its laws but not their parameters; every
+ * one is an argument here:
+ *   breadth_j ~ LogNormal(0, sig_breadth), p_j = breadth_j / sum_k breadth_k
+ *   K_j ~ Poisson(p_j I nu), truncated at I (nu: mean edges per request);
+ *         by inversion for means below 64, else by the rounded normal
+ *         approximation mean + sqrt(mean) N(0,1) (clipped to [0, I])
+ *   the K_j requests of j: distinct, uniform (Floyd's sampling)
+ *   v_j ~ LogNormal(0, sig_v), u_i ~ LogNormal(0, sig_u),
+ *   eps_ij ~ LogNormal(0, sig_eps): value_ij = min(v_j u_i eps_ij, c_max)
+ *   s_j ~ LogNormal(mu_s, sig_s): a_ij = s_j value_ij
+ *   c_ij = -value_ij (values enter the minimisation with their sign flipped)
+ * appb_degrees fills K[J] and returns E = sum K; appb_fill then writes the
+ * source-major arrays (off[I+1], dst, c, a; within a request, its resources
+ * in increasing id).  Every random number is keyed by (seed, purpose, index),
+ * so the result does not depend on the thread count.
+ */
+enum { PURPOSE_APPB_BREADTH = 11, PURPOSE_APPB_K = 12, PURPOSE_APPB_PICK = 13,
+       PURPOSE_APPB_V = 14, PURPOSE_APPB_U = 15, PURPOSE_APPB_S = 16 };
+
+static int cmp_u32(const void* p, const void* q) {
+  uint32_t x = *(const uint32_t*)p, y = *(const uint32_t*)q;
+  return (x > y) - (x < y);
+}
+
+static int64_t poisson_draw(rng_t* r, double mean, int64_t cap) {
+  int64_t k;
+  if (mean <= 0.0) return 0;
+  if (mean < 64.0) {  /* inversion: the first k with F(k) > u */
+    double u = rng_u01(r), p = exp(-mean), F = p;
+    k = 0;
+    while (F <= u && k < cap) {
+      ++k;
+      p *= mean / (double)k;
+      F += p;
+    }
+  } else {
+    k = (int64_t)floor(mean + sqrt(mean) * rng_normal(r) + 0.5);
+  }
+  if (k < 0) k = 0;
+  if (k > cap) k = cap;
+  return k;
+}
+
+int synth_appb_degrees(int64_t I, int32_t J, double nu, uint64_t seed, double sig_breadth,
+                       int64_t* K, int64_t* E_out) {
+  if (I < 0 || J <= 0 || !(nu >= 0)) return SYN_EINVAL;
+  double* w = (double*)malloc(sizeof(double) * (size_t)J);
+  if (!w) return SYN_ENOMEM;
+  double tot = 0.0;
+  for (int32_t j = 0; j < J; ++j) {
+    rng_t r = rng_for(seed, PURPOSE_APPB_BREADTH, (uint64_t)j);
+    w[j] = exp(sig_breadth * rng_normal(&r));
+    tot += w[j];
+  }
+  int64_t E = 0;
+  for (int32_t j = 0; j < J; ++j) {
+    rng_t r = rng_for(seed, PURPOSE_APPB_K, (uint64_t)j);
+    K[j] = poisson_draw(&r, w[j] / tot * (double)I * nu, I);
+    E += K[j];
+  }
+  free(w);
+  *E_out = E;
+  return SYN_OK;
+}
+
+int synth_appb_fill(int64_t I, int32_t J, const int64_t* K, uint64_t seed, double sig_v,
+                    double sig_u, double sig_eps, double c_max, double mu_s, double sig_s,
+                    int64_t* off, int32_t* dst, float* c, float* a) {
+  if (I < 0 || J <= 0) return SYN_EINVAL;
+  int64_t* roff = (int64_t*)malloc(sizeof(int64_t) * ((size_t)J + 1));
+  if (!roff) return SYN_ENOMEM;
+  roff[0] = 0;
+  int64_t kmax = 0;
+  for (int32_t j = 0; j < J; ++j) {
+    if (K[j] < 0 || K[j] > I) { free(roff); return SYN_EINVAL; }
+    roff[j + 1] = roff[j] + K[j];
+    if (K[j] > kmax) kmax = K[j];
+  }
+  const int64_t E = roff[J];
+  int32_t* req = (int32_t*)malloc(sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
+  float* val = (float*)malloc(sizeof(float) * (size_t)(E > 0 ? E : 1));
+  float* coef = (float*)malloc(sizeof(float) * (size_t)(E > 0 ? E : 1));
+  double* u = (double*)malloc(sizeof(double) * (size_t)(I > 0 ? I : 1));
+  if (!req || !val || !coef || !u) {
+    free(roff); free(req); free(val); free(coef); free(u);
+    return SYN_ENOMEM;
+  }
+  for (int64_t i = 0; i < I; ++i) {
+    rng_t r = rng_for(seed, PURPOSE_APPB_U, (uint64_t)i);
+    u[i] = exp(sig_u * rng_normal(&r));
+  }
+  int err = 0;
+#pragma omp parallel
+  {
+    /* Floyd's sampling of min(K, I - K) distinct requests (the complement when
+     * K > I / 2), in a hash set sized for the largest K */
+    pickset_t ps;
+    const int64_t mmax = kmax < I - kmax ? kmax : I - kmax;
+    uint32_t* pick = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(mmax + 1));
+    int ok = pickset_init(&ps, mmax) == 0 && pick;
+    if (!ok) {
+#pragma omp atomic write
+      err = 1;
+    }
+#pragma omp for schedule(dynamic, 16)
+    for (int32_t j = 0; j < J; ++j) {
+      if (!ok) continue;
+      rng_t r = rng_for(seed, PURPOSE_APPB_PICK, (uint64_t)j);
+      const int64_t k = K[j], m = k <= I - k ? k : I - k;
+      pickset_clear(&ps);
+      int64_t np = 0;
+      for (int64_t t = I - m; t < I; ++t) { /* Floyd */
+        uint32_t v = (uint32_t)rng_below(&r, (uint64_t)t + 1);
+        if (!pickset_insert(&ps, v)) {
+          v = (uint32_t)t;
+          pickset_insert(&ps, v);
+        }
+        pick[np++] = v;
+      }
+      int64_t pos = roff[j];
+      if (m == k) {  /* the picks, in increasing request id */
+        qsort(pick, (size_t)np, sizeof(uint32_t), cmp_u32);
+        for (int64_t q = 0; q < np; ++q) req[pos++] = (int32_t)pick[q];
+      } else {       /* more than half of the requests: all but the picks */
+        for (int64_t i = 0; i < I && pos < roff[j + 1]; ++i)
+          if (!pickset_has(&ps, (uint32_t)i)) req[pos++] = (int32_t)i;
+      }
+      rng_t rv = rng_for(seed, PURPOSE_APPB_V, (uint64_t)j);
+      rng_t rs = rng_for(seed, PURPOSE_APPB_S, (uint64_t)j);
+      const double vj = exp(sig_v * rng_normal(&rv));
+      const double sj = exp(mu_s + sig_s * rng_normal(&rs));
+      for (int64_t e = roff[j]; e < roff[j + 1]; ++e) {
+        double x = vj * u[req[e]] * exp(sig_eps * rng_normal(&r));
+        if (x > c_max) x = c_max;
+        val[e] = (float)x;
+        coef[e] = (float)(sj * x);
+      }
+    }
+    if (ok) pickset_free(&ps);
+    free(pick);
+  }
+  if (!err) {
+    /* source-major by a stable counting sort on the request */
+    for (int64_t i = 0; i <= I; ++i) off[i] = 0;
+    for (int64_t e = 0; e < E; ++e) off[req[e] + 1]++;
+    for (int64_t i = 0; i < I; ++i) off[i + 1] += off[i];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(I > 0 ? I : 1));
+    if (!fill) {
+      err = 1;
+    } else {
+      for (int64_t i = 0; i < I; ++i) fill[i] = off[i];
+      for (int32_t j = 0; j < J; ++j)
+        for (int64_t e = roff[j]; e < roff[j + 1]; ++e) {
+          const int64_t p = fill[req[e]]++;
+          dst[p] = j;
+          c[p] = -val[e];
+          a[p] = coef[e];
+        }
+      free(fill);
+    }
+  }
+  free(roff); free(req); free(val); free(coef); free(u);
+  return err ? SYN_ENOMEM : SYN_OK;
+}
+
 int synth_set_threads(int n) {
 #ifdef _OPENMP
   if (n > 0) omp_set_num_threads(n);

@@ -460,3 +460,61 @@ def test_generator_properties():
     assert np.array_equal(inst.dst, again.dst) and np.array_equal(inst.c, again.c)
     bsum = np.bincount(inst.dst, weights=inst.a.astype(float), minlength=inst.J)
     assert np.allclose(inst.b, (0.2 * bsum).astype(np.float32), rtol=1e-6)
+
+
+# --------------------------------------------------------------------------
+# Unit-box projection (Section 6's clamp map): C = [0, 1]^E
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("weighted", [False, True])
+def test_box_minimiser_by_bounded_search(weighted):
+    """Each x_e of the box problem minimises x^2 / (2 alpha_e) + (c_e + a_e mu_j) x
+    over [0, 1]: checked edge by edge with scipy's bounded scalar search."""
+    scalar = pytest.importorskip("scipy.optimize").minimize_scalar
+    inst = _tiny(I=25, J=6, seed=8)
+    P = oracle.Problem(inst, weighted=weighted, box=True)
+    mu = RNG.uniform(0.0, 1.5, inst.J)
+    for gamma in (2.0, 0.3, 0.01):
+        x = P.eval(mu, gamma, want_x=True).x
+        for e in range(inst.E):
+            a = float(inst.a[e])
+            w = (a * a if a != 0 else 1.0) if weighted else 1.0
+            lin = float(inst.c[e]) + a * mu[inst.dst[e]]
+            f = lambda t: t * t * gamma * w / 2 + lin * t  # noqa: E731
+            s = scalar(f, bounds=(0.0, 1.0), method="bounded", options=dict(xatol=1e-12))
+            xb = min((0.0, 1.0, s.x), key=f)  # the ends are candidates too
+            assert abs(x[e] - xb) <= 1e-6, (gamma, e, x[e], xb)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_box_gradient_is_central_difference(weighted):
+    inst = _tiny(seed=9)
+    P = oracle.Problem(inst, weighted=weighted, box=True)
+    for gamma in (0.5, 0.02):
+        mu = RNG.uniform(0.0, 1.5, inst.J)
+        ev = P.eval(mu, gamma)
+        for j in range(inst.J):
+            h = 1e-6 * max(1.0, abs(mu[j]))
+            e = np.zeros(inst.J)
+            e[j] = h
+            fd = (P.eval(mu + e, gamma).dual - P.eval(mu - e, gamma).dual) / (2 * h)
+            assert abs(fd - ev.grad[j]) <= 1e-6 * (abs(ev.ax[j]) + abs(inst.b[j]) + 1.0)
+
+
+def test_box_relates_to_the_simplex():
+    """The simplex {x >= 0, sum x <= 1} lies inside the unit box, so the box
+    minimum is never above the simplex one: g_box(mu) <= g_simplex(mu); with one
+    edge per source the two sets coincide and so do the evaluations."""
+    inst = _tiny(I=60, J=8, seed=10)
+    Pb, Ps = oracle.Problem(inst, box=True), oracle.Problem(inst)
+    for gamma in (1.0, 0.05, 1e-3):
+        for _ in range(3):
+            mu = RNG.uniform(0.0, 2.0, inst.J)
+            assert Pb.eval(mu, gamma).dual <= Ps.eval(mu, gamma).dual + 1e-12
+    one = synth.from_degrees(np.ones(200, dtype=np.int64), 5, 3, synth.DST_UNIFORM)
+    Pb, Ps = oracle.Problem(one, box=True), oracle.Problem(one)
+    mu = RNG.uniform(0.0, 1.0, one.J)
+    for gamma in (1.0, 0.01):
+        eb, es = Pb.eval(mu, gamma, want_x=True), Ps.eval(mu, gamma, want_x=True)
+        # (the simplex reaches x = 1 through its threshold, to within rounding)
+        assert np.allclose(eb.x, es.x, rtol=0, atol=1e-12)
+        assert abs(eb.dual - es.dual) <= 1e-12 * max(1.0, abs(es.dual))

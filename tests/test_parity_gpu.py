@@ -49,12 +49,13 @@ def dot_tol(lam, ax, b):
     return OBJ_RTOL * max(1.0, float(np.sum(lam * (np.abs(ax) + np.abs(np.asarray(b, np.float64))))))
 
 
-def check_eval(d, inst, lam, gamma, weighted=False, storage="f32", P=None, Po=None):
+def check_eval(d, inst, lam, gamma, weighted=False, storage="f32", P=None, Po=None, box=False):
     import torch
 
-    P = P or d.Problem.from_instance(inst, storage=storage, primal_scaling=weighted)
+    P = P or d.Problem.from_instance(inst, storage=storage, primal_scaling=weighted,
+                                     projection="box" if box else "simplex")
     ref_inst = decoded(inst) if storage == "bf16" else inst
-    Po = Po or oracle.Problem(ref_inst, weighted=weighted)
+    Po = Po or oracle.Problem(ref_inst, weighted=weighted, box=box)
     lam32 = np.asarray(lam, dtype=np.float32)
     grad, ev = P.dual_grad(torch.from_numpy(lam32).cuda(), gamma)
     grad = grad.cpu().numpy().astype(np.float64)
@@ -149,6 +150,45 @@ def test_empty_problem(dl):
     P, Po, grad, ev = check_eval(dl, inst, np.ones(4), 0.1)
     assert np.array_equal(grad, -np.arange(4))
     assert ev["dual_obj"] == pytest.approx(-6.0)
+
+
+@pytest.mark.parametrize("storage,weighted", [("f32", False), ("f32", True), ("bf16", False)])
+def test_unit_box_projection_parity(dl, storage, weighted):
+    """The unit-box clamp (x_e in [0, 1], no sum constraint) against the oracle:
+    c2-shaped sources, adversarial degrees (oversized sources read from global
+    memory), and the primal x edge by edge."""
+    import torch
+
+    rng = np.random.default_rng(31)
+    inst = synth.config("c2", scale=0.01)
+    P = Po = None
+    for gamma in (2.0, 0.05, 1e-3):
+        P, Po, _, _ = check_eval(dl, inst, rng.uniform(0, 2, inst.J), gamma, weighted, storage,
+                                 P=P, Po=Po, box=True)
+    degs = [0, 1, 33, 500, 3300, 7, 0, 5000, 2]
+    big = synth.from_degrees(np.array(degs), 8_000, 33, synth.DST_UNIFORM, b_frac=0.5)
+    check_eval(dl, big, rng.uniform(0, 1, big.J), 0.2, weighted, storage, box=True)
+    lam = rng.uniform(0, 1.5, inst.J).astype(np.float32)
+    x = P.primal(torch.from_numpy(lam).cuda(), 0.05).cpu().numpy().astype(np.float64)
+    xo = Po.eval(lam.astype(np.float64), 0.05, want_x=True).x
+    assert np.all((x >= 0) & (x <= 1))
+    assert np.all(np.abs(x - xo) <= 2e-6 * np.maximum(1.0, np.abs(xo)))
+
+
+def test_unit_box_solve_matches_oracle(dl):
+    inst = synth.greedy_budgets(synth.matching(10_000, 300, 26, ("poisson", 20, 1, 200)))
+    opts = dict(gamma0=0.1, gamma_final=0.01, halve_every=25, max_step=10.0, init_step=1e-5)
+    Po = oracle.Problem(inst, box=True)
+    ro = Po.solve(max_iters=3000, **opts)
+    P = dl.Problem.from_instance(inst, projection="box")
+    lam, rg = P.solve(max_iters=3000, **opts)
+    assert ro["converged"] and rg["converged"]
+    ev = Po.eval(lam.cpu().numpy().astype(np.float64), 0.01)
+    assert abs(rg["dual_obj"] - ev.dual) <= 1e-6 * abs(ev.dual)
+    assert abs(ev.dual - ro["dual"]) <= 2e-4 * abs(ro["dual"])
+    # the batched and serving forms take simplex problems only
+    with pytest.raises(dl.DualipError):
+        dl.Batch([P])
 
 
 @pytest.mark.parametrize("weighted", [False, True])

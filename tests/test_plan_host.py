@@ -1,11 +1,13 @@
 """Host planning of the stored layout (paper_2603_04621_gb300/csrc/plan.h),
 compiled on its own with g++ (no CUDA): the greedy tiling of the
-source-major edge list, the degree-spread rule and the degree order.
+source-major edge list, the lane-group slot model, the choice of the stored
+order and the degree order.
 
 * Tiles cover the sources in order.  Each tile is a single oversized source,
   or holds at most max_edges edges and max_sources sources.  It is greedy:
   the next source would break a limit.
-* The spread rule is "standard deviation above 0.3 of the mean".
+* The slot model counts the element slots of the pass's lane-group rounds
+  (checked by hand); degree order is stored when it saves at least 5%.
 * The degree order is a stable permutation by degree, and its offsets move
   each source's edges as one segment.
 * The autotuner's histogram buckets are [2^k, 2^(k+1)) (0 and 1 in bucket 0);
@@ -36,8 +38,13 @@ int64_t plan_tiles(const int64_t* off, int64_t I, int64_t max_e, int64_t max_s,
   for (size_t k = 0; k < t.size() && (int64_t)k < cap; ++k) { tiles[k] = t[k]; tile_e[k] = te[k]; }
   return (int64_t)t.size();
 }
-int plan_spread(const int64_t* off, int64_t I) {
-  return dualip::degrees_spread_widely(std::vector<int64_t>(off, off + I + 1)) ? 1 : 0;
+double plan_lean_slots(const int64_t* off, int64_t I, int64_t max_e, int64_t max_s, int lean80) {
+  return dualip::lean_slots(std::vector<int64_t>(off, off + I + 1), max_e, max_s, lean80 != 0);
+}
+int plan_choose(const int64_t* off, int64_t I, int64_t max_e, int64_t max_s) {
+  std::vector<int64_t> s, os;
+  return dualip::choose_degree_order(std::vector<int64_t>(off, off + I + 1), max_e, max_s, s,
+                                     os) ? 1 : 0;
 }
 int plan_bucket(int64_t d) { return dualip::degree_bucket(d); }
 int64_t plan_p99(const int64_t* hist, int64_t nsrc) { return dualip::degree_p99(hist, nsrc); }
@@ -84,8 +91,11 @@ def plan(tmp_path_factory):
     L.plan_tiles.argtypes = [p64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, p64, p64,
                              ctypes.c_int64]
     L.plan_tiles.restype = ctypes.c_int64
-    L.plan_spread.argtypes = [p64, ctypes.c_int64]
-    L.plan_spread.restype = ctypes.c_int
+    i64 = ctypes.c_int64
+    L.plan_lean_slots.argtypes = [p64, i64, i64, i64, ctypes.c_int]
+    L.plan_lean_slots.restype = ctypes.c_double
+    L.plan_choose.argtypes = [p64, i64, i64, i64]
+    L.plan_choose.restype = ctypes.c_int
     L.plan_bucket.argtypes = [ctypes.c_int64]
     L.plan_bucket.restype = ctypes.c_int
     L.plan_p99.argtypes = [p64, ctypes.c_int64]
@@ -153,24 +163,52 @@ def test_tiles_cover_in_order_within_limits_and_greedily(plan, law):
             assert b - a == max_s or e + deg[b] > max_e
 
 
-def test_spread_rule_is_a_coefficient_of_variation_above_0_3(plan):
+def test_lean_slot_model_by_hand(plan):
+    """Element slots of the lane-group projection, counted by hand."""
+    def slots(deg, lean80=True, max_e=3200, max_s=256):
+        off = offsets(np.asarray(deg))
+        return plan.plan_lean_slots(_p(off), len(deg), max_e, max_s, int(lean80))
+
+    # eight sources of 50 edges: spans 50 / 52 (first edge mod 4 is 0 or 2),
+    # one 4-lane round of 64-slot windows = 32 lanes x 16 slots
+    assert slots([50] * 8) == 512
+    # spans of 70..73 take 80-slot windows under lean80 (one round, 640
+    # slots), else two 8-lane rounds of 512
+    assert slots([70] * 8) == 640
+    assert slots([70] * 8, lean80=False) == 1024
+    # a span in (80, 128] sends the spans over 64 to the 8-lane pass as well
+    assert slots([70] * 7 + [100]) == 512 * 2
+    # 16- and 32-lane rounds: two sources of 200 edges, one of 400
+    assert slots([200, 200]) == 512 and slots([400]) == 512
+    # a span over 512 is counted as four passes over it; empty sources cost nothing
+    assert slots([600, 0, 0]) == 4 * 600
+    # batches restart at every tile: 5-source tiles split 8 sources 5 + 3
+    assert slots([10] * 8, max_s=5) == 2 * 512
+
+
+def test_degree_order_is_chosen_by_the_slot_model(plan):
     rng = np.random.default_rng(5)
-    cases = {
-        "poisson50": rng.poisson(50, 50_000),
-        "uniform5_100": rng.integers(5, 101, 50_000),
-        "constant": np.full(1_000, 10),
-        "one_source": np.array([7]),
-        "all_empty": np.zeros(100, np.int64),
-        "two_levels": np.repeat([10, 20], 500),
-    }
-    for name, deg in cases.items():
+
+    def choose(deg, max_e=3200):
+        off = offsets(np.asarray(deg))
+        return plan.plan_choose(_p(off), len(deg), max_e, 256)
+
+    # constant degrees: sorting changes nothing
+    assert choose(np.full(1_000, 10)) == 0
+    assert choose(np.array([7])) == 0 and choose(np.zeros(100, np.int64)) == 0
+    # uniform 5..100 (the batched workload): batches of mixed spans
+    assert choose(rng.integers(5, 101, 50_000)) == 1
+    # Poisson(80) in [1, 2000] with 4800-edge BF16 tiles (the precision workload):
+    # about half the spans exceed 80, so unsorted batches mix 4- and 8-lane rounds
+    assert choose(np.clip(rng.poisson(80, 50_000), 1, 2000), max_e=4800) == 1
+    # whatever it picks, the model never prefers an order it scores higher
+    for deg in (rng.poisson(50, 20_000), rng.poisson(40, 20_000), rng.integers(1, 300, 20_000)):
         off = offsets(deg)
-        d = deg.astype(np.float64)
-        expect = len(d) >= 2 and d.mean() > 0 and d.var() > 0.09 * d.mean() ** 2
-        assert plan.plan_spread(_p(off), len(deg)) == int(expect), name
-    # the workload laws on either side of the rule
-    assert plan.plan_spread(_p(offsets(cases["poisson50"])), 50_000) == 0
-    assert plan.plan_spread(_p(offsets(cases["uniform5_100"])), 50_000) == 1
+        src, off_st = np.empty(len(deg), np.int64), np.empty(len(deg) + 1, np.int64)
+        plan.plan_degree_order(_p(off), len(deg), _p(src), _p(off_st))
+        a = plan.plan_lean_slots(_p(off), len(deg), 3200, 256, 1)
+        b = plan.plan_lean_slots(_p(off_st), len(deg), 3200, 256, 1)
+        assert choose(deg) == int(b < 0.95 * a)
 
 
 @pytest.mark.parametrize("case", ["counting", "comparison"])

@@ -110,3 +110,49 @@ def test_batched_and_request_degree_laws():
     # the degree spread of the two laws: c4's is about 0.53, c5's about 0.16
     assert 0.5 < np.std(np.diff(inst.off)) / np.mean(np.diff(inst.off)) < 0.56
     assert 0.14 < deg.std() / deg.mean() < 0.18
+
+
+def test_appendix_b_generator_laws():
+    """The paper's Appendix B construction: each resource j draws K_j distinct
+    requests; values are min(v_j u_i eps_ij, c_max) with c = -value; a = s_j value
+    (one scale per resource); budgets follow the greedy-load rule; the draw does
+    not depend on the thread count."""
+    I, J, nu = 50_000, 400, 10.0
+    x = synth.appb(I, J, nu)
+    assert x.I == I and x.J == J and x.off[0] == 0 and x.off[-1] == x.E
+    assert abs(x.E / I - nu) < 0.5  # K_j ~ Poisson(p_j I nu): E ~ I nu
+    # distinct resources per request, in increasing id
+    for i in range(0, I, 499):
+        row = x.dst[x.off[i]:x.off[i + 1]]
+        assert np.all(np.diff(row) > 0)
+    val = -x.c.astype(np.float64)
+    assert np.all(val > 0) and np.all(val <= synth.APPB_DEFAULTS["c_max"] * (1 + 1e-6))
+    # a / value is the resource's own scale s_j: one value per resource
+    ratio = x.a.astype(np.float64) / val
+    for j in range(0, J, 37):
+        rj = ratio[x.dst == j]
+        if rj.size > 1:
+            assert np.allclose(rj, rj[0], rtol=1e-6)
+    # budgets: b_j = rho_j (l_j + eps) with rho_j in [0.5, 1]
+    load = np.zeros(J)
+    for i in range(I):
+        s, e = x.off[i], x.off[i + 1]
+        if e > s:
+            k = s + int(np.argmax(x.a[s:e]))
+            load[x.dst[k]] += x.a[k]
+    rho = x.b.astype(np.float64) / (load + synth.APPB_DEFAULTS["eps"])
+    assert np.all(rho >= 0.5 - 1e-6) and np.all(rho <= 1.0 + 1e-6)
+    # row norms spread over orders of magnitude (the regime of Section 5.1)
+    rown = np.sqrt(np.bincount(x.dst, weights=x.a.astype(np.float64) ** 2, minlength=J))
+    assert np.percentile(rown, 99) / np.percentile(rown, 1) > 30
+    # independent of the thread count
+    import os
+
+    lib = synth._load()
+    lib.synth_set_threads(1)
+    try:
+        y = synth.appb(I, J, nu)
+    finally:
+        lib.synth_set_threads(os.cpu_count() or 1)
+    for f in ("off", "dst", "c", "a", "b"):
+        assert np.array_equal(getattr(x, f), getattr(y, f)), f
