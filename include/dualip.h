@@ -75,6 +75,15 @@ typedef enum { DUALIP_PROJ_SIMPLEX = 0, DUALIP_PROJ_BOX = 1 } dualip_projection;
  *                them as bfloat16 (round to nearest even) and computes in FP32
  *   primal_scaling  0: w_e = 1; 1: w_e = a_e^2 (1 where a_e = 0)
  *   projection   DUALIP_PROJ_SIMPLEX (0) or DUALIP_PROJ_BOX (1), see above
+ *   num_families m >= 1 constraint families (Section 3.2, Definition 1: each
+ *                source block stacks m diagonal blocks).  With m > 1, a holds
+ *                m E floats, family-major (a[k E + e] is the coefficient of
+ *                edge e in family k), and b holds m J floats; A then has
+ *                m J rows, row k J + j, and lambda and grad of every call
+ *                have m J entries in that order.  m > 1 needs FP32 storage;
+ *                its pass is one warp per source without the lane-group
+ *                tiling, and the batched, serving and allocation-free forms
+ *                take one family only.
  * dualip_create copies everything into library-owned device memory; the
  * caller keeps ownership of its arrays and may free them on return.
  */
@@ -91,6 +100,7 @@ typedef struct {
   int32_t storage;
   int32_t primal_scaling;
   int32_t projection;  /* dualip_projection: the simple constraint set C */
+  int32_t num_families; /* m: constraint families (Definition 1); 0 or 1 = one */
 } dualip_problem_desc;
 
 /* Scalars of one dual evaluation, computed on the GPU in FP64 (Section 6: the

@@ -67,6 +67,8 @@ def _load():
         vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         lib.oracle_create.restype = vp
         lib.oracle_create.argtypes = [i64, i32, vp, vp, vp, vp, vp, ctypes.c_int]
+        lib.oracle_create_multi.restype = vp
+        lib.oracle_create_multi.argtypes = [i64, i32, i32, vp, vp, vp, vp, vp, ctypes.c_int]
         lib.oracle_destroy.argtypes = [vp]
         lib.oracle_project.argtypes = [i64, vp, vp, ctypes.c_int, vp, vp]
         lib.oracle_row_scale.argtypes = [vp, vp]
@@ -122,18 +124,24 @@ class Problem:
     """One matching LP held by the oracle (keeps references to the arrays)."""
 
     def __init__(self, inst, weighted: bool = False, box: bool = False):
+        """``inst.a`` is [E] (one constraint family) or [m, E] (m families,
+        Definition 1); ``inst.b`` then has m J entries, row k J + j."""
         self._lib = _load()
         self.inst = inst
+        a = np.asarray(inst.a, dtype=np.float32)
+        self.m = 1 if a.ndim == 1 else int(a.shape[0])
         self._keep = [np.ascontiguousarray(inst.off, dtype=np.int64),
                       np.ascontiguousarray(inst.dst, dtype=np.int32),
                       np.ascontiguousarray(inst.c, dtype=np.float32),
-                      np.ascontiguousarray(inst.a, dtype=np.float32),
-                      np.ascontiguousarray(inst.b, dtype=np.float32)]
+                      np.ascontiguousarray(a.reshape(-1)),
+                      np.ascontiguousarray(inst.b, dtype=np.float32).reshape(-1)]
         self.I, self.J, self.E = inst.I, inst.J, inst.E
+        self.R = self.m * self.J  # rows of A: one dual entry each
+        assert self._keep[3].shape[0] == self.m * self.E and self._keep[4].shape[0] == self.R
         self.weighted = bool(weighted)
         off, dst, c, a, b = self._keep
-        self._h = self._lib.oracle_create(self.I, self.J, _p(off), _p(dst), _p(c), _p(a), _p(b),
-                                          int(weighted))
+        self._h = self._lib.oracle_create_multi(self.I, self.J, self.m, _p(off), _p(dst), _p(c),
+                                                _p(a), _p(b), int(weighted))
         if not self._h:
             raise MemoryError("oracle_create failed")
         self.box = bool(box)
@@ -148,7 +156,7 @@ class Problem:
         self.close()
 
     def row_scale(self) -> np.ndarray:
-        D = np.empty(self.J, dtype=np.float64)
+        D = np.empty(self.R, dtype=np.float64)
         self._lib.oracle_row_scale(self._h, _p(D))
         return D
 
@@ -158,10 +166,10 @@ class Problem:
 
     def eval(self, mu, gamma: float, method: str = "sort", want_x: bool = False) -> Eval:
         mu = np.ascontiguousarray(mu, dtype=np.float64)
-        assert mu.shape == (self.J,)
+        assert mu.shape == (self.R,)
         x = np.empty(self.E, dtype=np.float64) if want_x else None
-        ax = np.empty(self.J, dtype=np.float64)
-        grad = np.empty(self.J, dtype=np.float64)
+        ax = np.empty(self.R, dtype=np.float64)
+        grad = np.empty(self.R, dtype=np.float64)
         sc = np.empty(5, dtype=np.float64)
         rc = self._lib.oracle_eval(self._h, _p(mu), float(gamma), 0 if method == "sort" else 1,
                                    _p(x), _p(ax), _p(grad), _p(sc))
@@ -177,7 +185,7 @@ class Problem:
         o = SolveOpts(gamma0, gamma_final, halve_every, max_step, init_step, max_iters, tol_gap,
                       tol_infeas, check_every, int(row_normalize), int(restart), int(stop_on_tol),
                       int(restart_on_decrease))
-        lam = np.zeros(self.J) if lam0 is None else np.array(lam0, dtype=np.float64, copy=True)
+        lam = np.zeros(self.R) if lam0 is None else np.array(lam0, dtype=np.float64, copy=True)
         res = SolveResult()
         tr = np.zeros((max(max_iters, 1), TRACE_W)) if want_trace else None
         rc = self._lib.oracle_solve(self._h, ctypes.byref(o), _p(lam), ctypes.byref(res), _p(tr))

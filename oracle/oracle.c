@@ -10,10 +10,11 @@
  *   smoothed dual (Eq. 2): g(mu) = min_{x in C} c^T x + (gamma/2)||x||_W^2 + mu^T (A x - b)
  *   Danskin gradient (Section 3.1): grad g(mu) = A x*(mu) - b,
  *                          x*(mu) = Pi_C( -(A^T mu + c) / gamma )
- *   matching structure (Section 3.2, Eqs. 3-5 and Definition 1 with one
- *   family): A = [D_1 ... D_I], D_i = diag(a_i.), so (A^T mu)_ij = a_ij mu_j and
- *   (A x)_j = sum_i a_ij x_ij; C = product over sources of
- *   {x_i >= 0, sum_j x_ij <= 1}.
+ *   matching structure (Section 3.2, Eqs. 3-5 and Definition 1): with one
+ *   family A = [D_1 ... D_I], D_i = diag(a_i.), so (A^T mu)_ij = a_ij mu_j and
+ *   (A x)_j = sum_i a_ij x_ij; with m families each source block stacks m
+ *   diagonal blocks D_ki (rows k J + j); C = product over sources of
+ *   {x_i >= 0, sum_j x_ij <= 1} (or the unit box).
  *   primal scaling (Section 5.1, "Primal scaling", view (i)): the ridge term
  *   becomes (gamma/2) sum w_e x_e^2 with w_e = v_e^2, v_e = |a_e| (1 where a_e = 0).
  *   Jacobi row normalisation (Section 5.1): D_j = ||A'_j||^-1 with the row norm
@@ -125,9 +126,19 @@ int oracle_project(int64_t n, const double* r, const double* alpha, int method, 
 }
 
 /* ---------------------------------------------------------------------- */
+/*
+ * Constraint families (Section 3.2, Definition 1): with m families every
+ * edge e = (i, j) has m coefficients a_{k,e} (k = 0..m-1, stored family-major,
+ * a[k E + e]) and enters the m rows (k, j) of A, numbered k J + j: the dual,
+ * the gradient and b have R = m J entries.  So
+ *   (A^T mu)_e = sum_k a_{k,e} mu_{k J + j},  (A x)_{k J + j} = sum_{e -> j} a_{k,e} x_e.
+ * m = 1 is the single family used everywhere else.
+ */
 typedef struct oracle_problem {
   int64_t I, E;
-  int32_t J;
+  int32_t J;       /* destinations */
+  int32_t m;       /* constraint families */
+  int64_t R;       /* rows of A: m J */
   const int64_t* off;
   const int32_t* dst;
   const float *c, *a, *b;
@@ -145,12 +156,15 @@ void oracle_destroy(oracle_problem* p) {
   free(p);
 }
 
-oracle_problem* oracle_create(int64_t I, int32_t J, const int64_t* off, const int32_t* dst,
-                              const float* c, const float* a, const float* b, int weighted) {
-  if (I < 0 || J < 0 || (I > 0 && !off)) return NULL;
+oracle_problem* oracle_create_multi(int64_t I, int32_t J, int32_t m, const int64_t* off,
+                                    const int32_t* dst, const float* c, const float* a,
+                                    const float* b, int weighted) {
+  if (I < 0 || J < 0 || m < 1 || (I > 0 && !off)) return NULL;
   oracle_problem* p = (oracle_problem*)calloc(1, sizeof(oracle_problem));
   if (!p) return NULL;
   p->I = I; p->J = J; p->off = off; p->dst = dst; p->c = c; p->a = a; p->b = b;
+  p->m = m;
+  p->R = (int64_t)m * J;
   p->weighted = weighted;
   p->E = I > 0 ? off[I] : 0;
   for (int64_t i = 0; i < I; ++i) {
@@ -171,49 +185,94 @@ oracle_problem* oracle_create(int64_t I, int32_t J, const int64_t* off, const in
   return p;
 }
 
+oracle_problem* oracle_create(int64_t I, int32_t J, const int64_t* off, const int32_t* dst,
+                              const float* c, const float* a, const float* b, int weighted) {
+  return oracle_create_multi(I, J, 1, off, dst, c, a, b, weighted);
+}
+
+/* coefficient of edge e in family k */
+static inline double coef(const oracle_problem* p, int k, int64_t e) {
+  return (double)p->a[(int64_t)k * p->E + e];
+}
+
 /* Switch the simple constraint set to the unit box [0, 1]^E (Section 6's
  * unit-box clamp map).  The block problem then separates by edge: each x_e
  * minimises x^2 / (2 alpha_e) - r_e x over [0, 1], so x_e = min(1, alpha_e (r_e)_+). */
 void oracle_set_box(oracle_problem* p, int box) { p->box = box ? 1 : 0; }
 
-/* ridge weight of an edge: w_e = a_e^2 (1 where a_e = 0) with primal scaling, else 1 */
+/* ridge weight of an edge with primal scaling: w_e = v_e^2 with v_e the norm of
+ * the edge's column of A, sum_k a_{k,e}^2 (1 where the column is zero); 1
+ * without primal scaling */
 static inline double edge_w(const oracle_problem* p, int64_t e) {
   if (!p->weighted) return 1.0;
-  double av = (double)p->a[e];
-  return av != 0.0 ? av * av : 1.0;
+  double s = 0.0;
+  for (int k = 0; k < p->m; ++k) s += coef(p, k, e) * coef(p, k, e);
+  return s != 0.0 ? s : 1.0;
 }
 
-/* Jacobi row scale D_j = (sum_{e -> j} a_e^2 / w_e)^(-1/2), 1 for a zero row. */
+/* Jacobi row scale D_r = (sum_{e in row r} a_{k,e}^2 / w_e)^(-1/2) for row
+ * r = k J + j, 1 for a zero row. */
 int oracle_row_scale(const oracle_problem* p, double* D) {
-  for (int32_t j = 0; j < p->J; ++j) {
-    nsum_t s = {0, 0};
-    for (int64_t k = p->toff[j]; k < p->toff[j + 1]; ++k) {
-      int64_t e = p->tix[k];
-      double av = (double)p->a[e];
-      nsum_add(&s, av * av / edge_w(p, e));
+  for (int k = 0; k < p->m; ++k)
+    for (int32_t j = 0; j < p->J; ++j) {
+      nsum_t s = {0, 0};
+      for (int64_t t = p->toff[j]; t < p->toff[j + 1]; ++t) {
+        int64_t e = p->tix[t];
+        double av = coef(p, k, e);
+        nsum_add(&s, av * av / edge_w(p, e));
+      }
+      double n2 = nsum_get(&s);
+      D[(int64_t)k * p->J + j] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
     }
-    double n2 = nsum_get(&s);
-    D[j] = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
-  }
   return OR_OK;
 }
 
-/* Squared spectral norm of A in the ridge metric.  With one matching family
- * every column of A has a single nonzero, so A W^-1 A^T is diagonal and its
- * largest entry is ||A W^-1/2||_2^2; L = that / gamma bounds the Lipschitz
- * constant of grad g (Appendix A, Lemma 2). */
+/* Squared spectral norm of D A W^-1/2 (D = I when NULL).  Rows of different
+ * destinations share no column, so D A W^-1 A^T D is block diagonal with one
+ * m x m block per destination j, M_kl = D_kj D_lj sum_{e -> j} a_{k,e} a_{l,e} / w_e;
+ * the norm is the largest eigenvalue over the blocks (power iteration on each
+ * positive semidefinite block; with one family the block is that one entry).
+ * L = the norm / gamma bounds the Lipschitz constant of grad g (Appendix A). */
 double oracle_norm2_sq(const oracle_problem* p, const double* D /* NULL = unscaled */) {
+  const int m = p->m;
   double best = 0.0;
+  double* M = (double*)calloc((size_t)m * m, sizeof(double));
+  double* v = (double*)malloc(sizeof(double) * (size_t)m);
+  double* u = (double*)malloc(sizeof(double) * (size_t)m);
+  if (!M || !v || !u) { free(M); free(v); free(u); return -1.0; }
   for (int32_t j = 0; j < p->J; ++j) {
-    double s = 0.0;
-    for (int64_t k = p->toff[j]; k < p->toff[j + 1]; ++k) {
-      int64_t e = p->tix[k];
-      double av = (double)p->a[e];
-      s += av * av / edge_w(p, e);
+    memset(M, 0, sizeof(double) * (size_t)m * m);
+    for (int64_t t = p->toff[j]; t < p->toff[j + 1]; ++t) {
+      int64_t e = p->tix[t];
+      double w = edge_w(p, e);
+      for (int k = 0; k < m; ++k)
+        for (int l = 0; l < m; ++l) M[k * m + l] += coef(p, k, e) * coef(p, l, e) / w;
     }
-    if (D) s *= D[j] * D[j];
-    if (s > best) best = s;
+    if (D)
+      for (int k = 0; k < m; ++k)
+        for (int l = 0; l < m; ++l)
+          M[k * m + l] *= D[(int64_t)k * p->J + j] * D[(int64_t)l * p->J + j];
+    double lam = 0.0;
+    if (m == 1) {
+      lam = M[0];
+    } else {
+      for (int k = 0; k < m; ++k) v[k] = 1.0 + 0.1 * k;
+      for (int it = 0; it < 500; ++it) {
+        double nrm = 0.0;
+        for (int k = 0; k < m; ++k) {
+          u[k] = 0.0;
+          for (int l = 0; l < m; ++l) u[k] += M[k * m + l] * v[l];
+          nrm += u[k] * u[k];
+        }
+        nrm = sqrt(nrm);
+        if (nrm == 0.0) break;
+        for (int k = 0; k < m; ++k) v[k] = u[k] / nrm;
+        lam = nrm;
+      }
+    }
+    if (lam > best) best = lam;
   }
+  free(M); free(v); free(u);
   return best;
 }
 
@@ -231,6 +290,7 @@ int oracle_eval(const oracle_problem* p, const double* mu, double gamma, int met
   if (!(gamma > 0)) return OR_EINVAL;
   const int64_t I = p->I;
   const int32_t J = p->J;
+  const int64_t R = p->R;
   double* x = x_out;
   double* xbuf = NULL;
   if (!x) {
@@ -241,7 +301,7 @@ int oracle_eval(const oracle_problem* p, const double* mu, double gamma, int met
   double* src_lin = (double*)calloc((size_t)(I > 0 ? I : 1), sizeof(double)); /* sum (c + a mu) x */
   double* src_cx = (double*)calloc((size_t)(I > 0 ? I : 1), sizeof(double));
   double* src_wxx = (double*)calloc((size_t)(I > 0 ? I : 1), sizeof(double));
-  double* axv = (double*)malloc(sizeof(double) * (size_t)(J > 0 ? J : 1));
+  double* axv = (double*)malloc(sizeof(double) * (size_t)(R > 0 ? R : 1));
   int fail = !src_lin || !src_cx || !src_wxx || !axv;
   if (!fail) {
 #pragma omp parallel
@@ -260,7 +320,9 @@ int oracle_eval(const oracle_problem* p, const double* mu, double gamma, int met
           int64_t e0 = p->off[i], d = p->off[i + 1] - e0;
           for (int64_t k = 0; k < d; ++k) {
             int64_t e = e0 + k;
-            r[k] = -((double)p->c[e] + (double)p->a[e] * mu[p->dst[e]]);
+            double am = 0.0;  /* (A^T mu)_e */
+            for (int f = 0; f < p->m; ++f) am += coef(p, f, e) * mu[(int64_t)f * J + p->dst[e]];
+            r[k] = -((double)p->c[e] + am);
             al[k] = 1.0 / (gamma * edge_w(p, e));
           }
           double tau = 0.0;
@@ -287,15 +349,17 @@ int oracle_eval(const oracle_problem* p, const double* mu, double gamma, int met
     free(xbuf); free(src_lin); free(src_cx); free(src_wxx); free(axv);
     return OR_ENOMEM;
   }
-  /* A x per destination, summed in ascending source order */
+  /* A x per row (family k, destination j), summed in ascending source order */
 #pragma omp parallel for schedule(dynamic, 64)
-  for (int32_t j = 0; j < J; ++j) {
+  for (int64_t row = 0; row < R; ++row) {
+    const int f = (int)(row / J);
+    const int32_t j = (int32_t)(row % J);
     nsum_t s = {0, 0};
     for (int64_t k = p->toff[j]; k < p->toff[j + 1]; ++k) {
       int64_t e = p->tix[k];
-      nsum_add(&s, (double)p->a[e] * x[e]);
+      nsum_add(&s, coef(p, f, e) * x[e]);
     }
-    axv[j] = nsum_get(&s);
+    axv[row] = nsum_get(&s);
   }
   nsum_t lin = {0, 0}, cx = {0, 0}, wxx = {0, 0}, mub = {0, 0}, inf = {0, 0}, comp = {0, 0};
   for (int64_t i = 0; i < I; ++i) {
@@ -303,13 +367,13 @@ int oracle_eval(const oracle_problem* p, const double* mu, double gamma, int met
     nsum_add(&cx, src_cx[i]);
     nsum_add(&wxx, src_wxx[i]);
   }
-  for (int32_t j = 0; j < J; ++j) {
-    double gj = axv[j] - (double)p->b[j];
-    nsum_add(&mub, mu[j] * (double)p->b[j]);
-    nsum_add(&comp, mu[j] * gj);
+  for (int64_t row = 0; row < R; ++row) {
+    double gj = axv[row] - (double)p->b[row];
+    nsum_add(&mub, mu[row] * (double)p->b[row]);
+    nsum_add(&comp, mu[row] * gj);
     if (gj > 0) nsum_add(&inf, gj * gj);
-    if (ax_out) ax_out[j] = axv[j];
-    if (grad_out) grad_out[j] = gj;
+    if (ax_out) ax_out[row] = axv[row];
+    if (grad_out) grad_out[row] = gj;
   }
   double reg = 0.5 * gamma * nsum_get(&wxx);
   if (scal) {
@@ -380,7 +444,7 @@ static double gamma_at(const oracle_solve_opts* o, int32_t k) {
 
 int oracle_solve(const oracle_problem* p, const oracle_solve_opts* o, double* lambda_io,
                  oracle_solve_result* res, double* trace) {
-  const int32_t J = p->J;
+  const int32_t J = (int32_t)p->R;  /* dual entries: one per row of A */
   if (!(o->gamma0 > 0) || !(o->gamma_final > 0) || o->max_iters < 0) return OR_EINVAL;
   size_t n = (size_t)(J > 0 ? J : 1);
   double *D = malloc(n * 8), *lam = malloc(n * 8), *y = malloc(n * 8), *yp = malloc(n * 8),

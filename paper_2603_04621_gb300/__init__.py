@@ -83,7 +83,7 @@ class ProblemDesc(ctypes.Structure):
                 ("dst", ctypes.c_void_p), ("c", ctypes.c_void_p), ("a", ctypes.c_void_p),
                 ("b", ctypes.c_void_p), ("inputs_on_device", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("primal_scaling", ctypes.c_int32),
-                ("projection", ctypes.c_int32)]
+                ("projection", ctypes.c_int32), ("num_families", ctypes.c_int32)]
 
 
 class Eval(ctypes.Structure):
@@ -470,16 +470,20 @@ class Problem:
             c = np.ascontiguousarray(c, dtype=np.float32)
             a = np.ascontiguousarray(a, dtype=np.float32)
             b = np.ascontiguousarray(b, dtype=np.float32)
+        # a: [E] (one constraint family) or [m, E] (m families, family-major);
+        # the dual then has m J entries (row k J + j), and self.J counts them
+        m = 1 if a.ndim == 1 else int(a.shape[0])
         self._keep = (off, dst, c, a, b)
         I = int(off.shape[0]) - 1
         E = int(dst.shape[0])
-        self.I, self.J, self.E = I, int(J), E
+        self.I, self.E, self.m, self.num_dests = I, E, m, int(J)
+        self.J = m * int(J)
         self.storage = storage
         d = ProblemDesc(I, E, int(J), _ptr(off), _ptr(dst), _ptr(c), _ptr(a), _ptr(b),
                         1 if on_dev else 0,
                         DUALIP_EDGE_BF16 if storage == "bf16" else DUALIP_EDGE_F32,
                         1 if primal_scaling else 0,
-                        DUALIP_PROJ_BOX if projection == "box" else DUALIP_PROJ_SIMPLEX)
+                        DUALIP_PROJ_BOX if projection == "box" else DUALIP_PROJ_SIMPLEX, m)
         self.h = dualip_create(d, _stream(stream))
         self._keep = None
         self.device = torch.device("cuda", torch.cuda.current_device())

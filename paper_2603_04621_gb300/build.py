@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdualip.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["pass.cu", "api.cu", "solve.cu", "noalloc.cu", "batch.cu", "serve.cu", "order.cu"]
+SOURCES = ["pass.cu", "api.cu", "solve.cu", "noalloc.cu", "batch.cu", "serve.cu", "order.cu",
+           "multi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

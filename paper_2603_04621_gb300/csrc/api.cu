@@ -118,6 +118,130 @@ static cudaError_t enqueue_eval(Problem& P, const float* lambda, double gamma, f
   return cudaSuccess;
 }
 
+// A problem with m > 1 constraint families (Definition 1).  The edges keep
+// the caller's order and destination ids (rows k Jd + j need no renumbering),
+// c and the m coefficient arrays stay separate FP32 arrays, and every J-length
+// array of the handle has m Jd rows in the caller's row order; the prologue,
+// epilogue and solver kernels then work unchanged on those rows.
+dualip_status create_multi(const dualip_problem_desc* d, void* stream, dualip_problem** out) {
+  const int64_t I = d->num_sources, E = d->num_edges;
+  const int32_t Jd = d->num_dests, m = d->num_families;
+  const int64_t R64 = (int64_t)m * Jd;
+  if (R64 > INT32_MAX) return fail(DUALIP_EINVAL, "num_families * num_dests exceeds 2^31 - 1");
+  const int32_t R = (int32_t)R64;
+  if (d->storage != DUALIP_EDGE_F32)
+    return fail(DUALIP_EINVAL, "several constraint families need FP32 edge storage");
+  cudaStream_t s = as_stream(stream);
+  const cudaMemcpyKind h2d = d->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e;
+  std::vector<int64_t> off((size_t)I + 1);
+  if ((e = cudaMemcpyAsync(off.data(), d->src_offsets, sizeof(int64_t) * (I + 1),
+                           d->inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                           s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(e, "reading src_offsets");
+  if (off[0] != 0) return fail(DUALIP_EINVAL, "src_offsets[0] must be 0");
+  for (int64_t i = 0; i < I; ++i)
+    if (off[i + 1] < off[i]) return fail(DUALIP_EINVAL, "src_offsets must be nondecreasing");
+  if (off[I] != E) return fail(DUALIP_EINVAL, "src_offsets[I] must equal num_edges");
+  std::vector<float> b((size_t)R);
+  if ((e = cudaMemcpyAsync(b.data(), d->b, sizeof(float) * R,
+                           d->inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                           s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(e, "reading b");
+  double bn = 0.0;
+  for (int32_t r = 0; r < R; ++r) {
+    if (!std::isfinite(b[r])) return fail(DUALIP_EINVAL, "b must be finite");
+    bn += (double)b[r] * (double)b[r];
+  }
+
+  auto* h = new (std::nothrow) dualip_problem();
+  if (!h) return fail(DUALIP_ENOMEM, "host allocation failed");
+  Problem& P = h->p;
+  P.I = I;
+  P.E = E;
+  P.J = R;
+  P.Jd = Jd;
+  P.m = m;
+  P.storage = DUALIP_EDGE_F32;
+  P.weighted = d->primal_scaling;
+  P.box = d->projection == DUALIP_PROJ_BOX ? 1 : 0;
+  P.bnorm = std::sqrt(bn);
+  P.last_stream = s;
+  auto bail = [&](dualip_status st) {
+    cudaStreamSynchronize(s);
+    free_all(P);
+    delete h;
+    return st;
+  };
+  if ((e = cudaGetDevice(&P.device))) return bail(cuda_fail(e, "cudaGetDevice"));
+  if ((e = cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, P.device)))
+    return bail(cuda_fail(e, "querying the SM count"));
+  // one warp per source, eight warps per block, a few blocks per SM
+  P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(8 * (int64_t)P.num_sms, (I + 7) / 8));
+  P.epi_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((R + 255) / 256, 2 * P.num_sms));
+  std::vector<int32_t> ident((size_t)R);
+  std::iota(ident.begin(), ident.end(), 0);
+  if ((e = dev_alloc(P, &P.off, (size_t)I + 1)) || (e = dev_alloc(P, &P.dst, (size_t)E)) ||
+      (e = dev_alloc(P, &P.cm, (size_t)E)) || (e = dev_alloc(P, &P.am, (size_t)m * E)) ||
+      (e = dev_alloc(P, &P.b_r, R)) || (e = dev_alloc(P, &P.orig_of, R)) ||
+      (e = dev_alloc(P, &P.new_of, R)) || (e = dev_alloc(P, &P.mu_r, R)) ||
+      (e = dev_alloc(P, &P.y, R)) || (e = dev_alloc(P, &P.part, (size_t)P.grid)) ||
+      (e = dev_alloc(P, &P.epi_part, (size_t)P.epi_blocks)) || (e = dev_alloc(P, &P.eval_dev, 8)) ||
+      (e = dev_alloc(P, &P.lam_stage, R)) || (e = dev_alloc(P, &P.grad_stage, R)) ||
+      (e = dev_alloc(P, &P.status, 1)))
+    return bail(cuda_fail(e, "allocating problem memory"));
+  if ((e = cudaMallocHost(&P.eval_host, 16 * sizeof(double))))
+    return bail(cuda_fail(e, "allocating pinned memory"));
+  unsigned* counts = nullptr;
+  if ((e = cudaMemsetAsync(P.y, 0, (size_t)R * 8, s)) ||
+      (e = cudaMemsetAsync(P.status, 0, sizeof(DeviceStatus), s)) ||
+      (e = cudaMemcpyAsync(P.off, off.data(), sizeof(int64_t) * (I + 1), cudaMemcpyHostToDevice,
+                           s)) ||
+      (E > 0 && (e = cudaMemcpyAsync(P.dst, d->dst, 4 * (size_t)E, h2d, s))) ||
+      (E > 0 && (e = cudaMemcpyAsync(P.cm, d->c, 4 * (size_t)E, h2d, s))) ||
+      (E > 0 && (e = cudaMemcpyAsync(P.am, d->a, 4 * (size_t)m * E, h2d, s))) ||
+      (e = cudaMemcpyAsync(P.b_r, b.data(), 4 * (size_t)R, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(P.orig_of, ident.data(), 4 * (size_t)R, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(P.new_of, ident.data(), 4 * (size_t)R, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMallocAsync(&counts, sizeof(unsigned) * (Jd + 2), s)) ||
+      (e = cudaMemsetAsync(counts, 0, sizeof(unsigned) * (Jd + 2), s)) ||
+      (E > 0 && (e = launch_histogram(P.dst, E, Jd, counts, P.status, s))) ||
+      (E > 0 && (e = launch_check_finite(P.cm, E, P.status, s))) ||
+      (E > 0 && (e = launch_check_finite(P.am, (int64_t)m * E, P.status, s))) ||
+      (E > 0 && (e = launch_absmax(P.cm, E, counts + Jd, s))) ||
+      (E > 0 && (e = launch_absmax(P.am, (int64_t)m * E, counts + Jd + 1, s)))) {
+    if (counts) cudaFreeAsync(counts, s);
+    return bail(cuda_fail(e, "building the problem"));
+  }
+  std::vector<unsigned> cnt((size_t)Jd + 2);
+  e = cudaMemcpyAsync(cnt.data(), counts, sizeof(unsigned) * (Jd + 2), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(counts, s);
+  DeviceStatus st{};
+  if (e || (e = cudaMemcpyAsync(&st, P.status, sizeof(st), cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return bail(cuda_fail(e, "building the problem"));
+  if (st.err) return bail(fail(DUALIP_EINVAL, "dst out of [0, J) or non-finite c / a"));
+  // fixed-point scales: |(A x)_r| <= max in-degree max|a|; |sum c x| <= I max|c|;
+  // sum w x^2 <= I max w with w = sum_k a_k^2 (primal scaling) or 1
+  float mc, ma;
+  std::memcpy(&mc, &cnt[Jd], 4);
+  std::memcpy(&ma, &cnt[Jd + 1], 4);
+  const unsigned maxcnt = Jd > 0 ? *std::max_element(cnt.begin(), cnt.begin() + Jd) : 0u;
+  const double mw = P.weighted ? std::max(1.0, (double)m * (double)ma * (double)ma) : 1.0;
+  int ex = 0;
+  std::frexp(std::max((double)maxcnt * ma, 1e-30), &ex);
+  P.exp_y = std::max(-100, std::min(100, 61 - ex));
+  std::frexp(std::max((double)I * mc, 1e-30), &ex);
+  P.exp_c = std::max(-100, std::min(100, 61 - ex));
+  std::frexp(std::max((double)I * mw, 1e-30), &ex);
+  P.exp_w = std::max(-100, std::min(100, 61 - ex));
+  P.off_host = std::move(off);
+  *out = h;
+  return DUALIP_OK;
+}
+
 }  // namespace dualip
 
 using namespace dualip;
@@ -144,6 +268,8 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     return fail(DUALIP_EINVAL, "unknown projection");
   if (d->inputs_on_device != 0 && d->inputs_on_device != 1)
     return fail(DUALIP_EINVAL, "inputs_on_device must be 0 or 1");
+  if (d->num_families < 0) return fail(DUALIP_EINVAL, "num_families must be >= 0");
+  if (d->num_families > 1) return create_multi(d, stream, out);
   cudaStream_t s = as_stream(stream);
   const cudaMemcpyKind h2d = d->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaError_t e;

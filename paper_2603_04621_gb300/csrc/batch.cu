@@ -773,7 +773,9 @@ dualip_status dualip_batch_create(int32_t n, dualip_problem* const* problems, du
     const Problem& P0 = problems[0]->p;
     if (P.storage != P0.storage || P.weighted != P0.weighted || P.device != P0.device)
       return fail(DUALIP_EINVAL, "problems of a batch share storage, primal_scaling and device");
-    if (P.box) return fail(DUALIP_EINVAL, "the batched form takes simplex problems only");
+    if (P.box || P.m > 1)
+      return fail(DUALIP_EINVAL,
+                  "the batched form takes simplex problems with one constraint family only");
     for (int m = 0; m < k; ++m)
       if (problems[m] == problems[k]) return fail(DUALIP_EINVAL, "a problem appears twice");
   }

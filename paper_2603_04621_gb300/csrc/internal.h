@@ -200,6 +200,13 @@ struct Problem {
   int storage = DUALIP_EDGE_F32;
   int weighted = 0;
   int box = 0;  // projection onto the unit box [0, 1]^E instead of per-source simplices
+  // constraint families (Definition 1): with m > 1, J counts rows (m Jd, row
+  // k Jd + j), the edges keep the caller's order and destination ids, and c,
+  // a (family-major, a[k E + e]) live in cm, am; the pass is multi.cu's
+  int m = 1;
+  int32_t Jd = 0;
+  float* cm = nullptr;
+  float* am = nullptr;
   int64_t ntiles = 0;
   int h_mu = 0, h_y = 0;
   int num_sms = 0, grid = 0;
@@ -315,6 +322,13 @@ cudaError_t launch_absmax(const float* v, int64_t n, unsigned* out, cudaStream_t
 
 // solve.cu
 void solve_ctx_free(Problem& P);
+
+// multi.cu: problems with several constraint families (m > 1)
+dualip_status create_multi(const dualip_problem_desc* d, void* stream, dualip_problem** out);
+cudaError_t launch_pass_multi(const Problem& P, const float* gamma_dev, float gamma, float* x_out,
+                              cudaStream_t s);
+// acc[r] += a_{k,e}^2 / w_e over the edges of row r = k Jd + j (row norms)
+cudaError_t launch_row_norm_multi(const Problem& P, double* acc, cudaStream_t s);
 
 // api.cu helpers (the tiling and the degree order are in plan.h)
 cudaStream_t as_stream(void* s);

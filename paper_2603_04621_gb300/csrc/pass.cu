@@ -1565,6 +1565,7 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
 
 cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, float* x_out,
                         cudaStream_t s) {
+  if (P.m > 1) return launch_pass_multi(P, gamma_dev, gamma, x_out, s);
   return dispatch_pass(P, pass_params(P, gamma_dev, gamma, x_out), x_out != nullptr, s);
 }
 

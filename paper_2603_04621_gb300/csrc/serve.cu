@@ -381,8 +381,9 @@ dualip_status dualip_server_submit(dualip_server* h, const dualip_problem_desc* 
       o.gamma_final > o.gamma0 || o.gamma_final < 1e-30 || o.max_iters < 1 ||
       !(o.max_step > 0) || !(o.init_step > 0))
     return fail(DUALIP_EINVAL, "invalid solve options");
-  if (desc->projection != DUALIP_PROJ_SIMPLEX)
-    return fail(DUALIP_EINVAL, "the serving form takes simplex problems only");
+  if (desc->projection != DUALIP_PROJ_SIMPLEX || desc->num_families > 1)
+    return fail(DUALIP_EINVAL,
+                "the serving form takes simplex problems with one constraint family only");
   Server& S = h->s;
   std::lock_guard<std::mutex> lk(S.mu);
   const int64_t t = S.next_ticket++;

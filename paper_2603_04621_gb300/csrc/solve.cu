@@ -342,7 +342,9 @@ cudaError_t compute_row_scale(const Problem& P, int row_normalize, float* D, cud
   double* acc = nullptr;
   if ((e = cudaMalloc(&acc, sizeof(double) * std::max<int32_t>(P.J, 1)))) return e;
   e = cudaMemsetAsync(acc, 0, sizeof(double) * P.J, s);
-  if (!e && P.E > 0) {
+  if (!e && P.E > 0 && P.m > 1) {
+    e = launch_row_norm_multi(P, acc, s);
+  } else if (!e && P.E > 0) {
     const int64_t g = std::min<int64_t>((P.E + 255) / 256, 8192);
     row_norm_kernel<<<(int)g, 256, 0, s>>>(P.dst, P.ca2, P.ca, P.E, P.weighted, acc);
     e = cudaGetLastError();

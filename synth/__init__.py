@@ -238,6 +238,32 @@ def appb(I: int, J: int, nu: float = 10.0, seed: int = CONFIG_SEEDS["appb"], **p
     return greedy_budgets(inst, seed=seed, eps=p["eps"])
 
 
+def add_families(inst: Instance, m: int, seed: int = 77, a_range=(0.5, 1.5),
+                 rho=(0.5, 1.0), eps: float = 0.01) -> Instance:
+    """The same graph and costs with m constraint families (Definition 1):
+    family 0 keeps inst.a and inst.b; family k >= 1 draws its coefficients
+    a_k ~ U(a_range) per edge and takes greedy-load budgets of its own (each
+    source's largest a_k edge), b_k = rho (l_k + eps).  a becomes [m, E] and b
+    [m J] (row k J + j)."""
+    lib = _load()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a = np.empty((m, inst.E), dtype=np.float32)
+    b = np.empty(m * inst.J, dtype=np.float32)
+    a[0] = inst.a
+    b[: inst.J] = inst.b
+    for k in range(1, m):
+        a[k] = rng.uniform(a_range[0], a_range[1], inst.E).astype(np.float32)
+        bk = np.empty(inst.J, dtype=np.float32)
+        ak = np.ascontiguousarray(a[k])
+        rc = lib.synth_budgets_greedy(inst.I, inst.J, _ptr(inst.off), _ptr(inst.dst), _ptr(ak),
+                                      seed * 1000 + k, rho[0], rho[1], eps, _ptr(bk))
+        if rc:
+            raise ValueError(f"synth_budgets_greedy failed ({rc})")
+        b[k * inst.J:(k + 1) * inst.J] = bk
+    return Instance(inst.off, inst.dst, inst.c, a, b, inst.J, name=f"{inst.name}x{m}families",
+                    meta=dict(inst.meta, families=m))
+
+
 def batch_shapes(n: int = 256, seed: int = CONFIG_SEEDS["c4"], i_range=(1_000, 2_000_000),
                  j_range=(10, 50_000)):
     """(I, J, seed) of each instance of the batched workload c4."""

@@ -518,3 +518,100 @@ def test_box_relates_to_the_simplex():
         # (the simplex reaches x = 1 through its threshold, to within rounding)
         assert np.allclose(eb.x, es.x, rtol=0, atol=1e-12)
         assert abs(eb.dual - es.dual) <= 1e-12 * max(1.0, abs(es.dual))
+
+
+# --------------------------------------------------------------------------
+# Several constraint families (Section 3.2, Definition 1), rows k J + j
+# --------------------------------------------------------------------------
+def _families(inst, a_list, b_list):
+    a = np.stack([np.asarray(x, np.float32) for x in a_list])
+    b = np.concatenate([np.asarray(x, np.float32) for x in b_list])
+    return synth.Instance(inst.off, inst.dst, inst.c, a, b, inst.J)
+
+
+def test_families_split_one_family_in_two():
+    """Halving every coefficient and budget into two identical families gives
+    sum_k mu_k^T (A/2 x - b/2) = ((mu_1 + mu_2)/2)^T (A x - b): the two-family dual
+    at (mu_1, mu_2) is the one-family dual at their mean, with the same x and
+    half the gradient in each family."""
+    inst = _tiny(I=80, J=9, seed=61)
+    two = _families(inst, [inst.a / 2, inst.a / 2], [inst.b / 2, inst.b / 2])
+    P1, P2 = oracle.Problem(inst), oracle.Problem(two)
+    assert P2.m == 2 and P2.R == 2 * inst.J
+    for gamma in (0.5, 0.01):
+        mu = RNG.uniform(0.0, 2.0, 2 * inst.J)
+        mid = (mu[:inst.J] + mu[inst.J:]) / 2
+        e1, e2 = P1.eval(mid, gamma, want_x=True), P2.eval(mu, gamma, want_x=True)
+        assert np.allclose(e2.x, e1.x, rtol=0, atol=1e-12)
+        assert e2.dual == pytest.approx(e1.dual, rel=1e-12)
+        assert np.allclose(e2.grad[:inst.J], e1.grad / 2, atol=1e-12)
+        assert np.allclose(e2.grad[inst.J:], e1.grad / 2, atol=1e-12)
+
+
+def test_families_zero_family_leaves_the_rest():
+    """A family of zero coefficients changes no score: x and the first family's
+    gradient are the one-family ones, its own rows have A x = 0 (gradient -b_2),
+    and g gains -mu_2^T b_2."""
+    inst = _tiny(I=60, J=7, seed=62)
+    b2 = RNG.uniform(0.5, 2.0, inst.J)
+    two = _families(inst, [inst.a, np.zeros(inst.E)], [inst.b, b2])
+    P1, P2 = oracle.Problem(inst), oracle.Problem(two)
+    mu = RNG.uniform(0.0, 1.5, 2 * inst.J)
+    e1, e2 = P1.eval(mu[:inst.J], 0.05, want_x=True), P2.eval(mu, 0.05, want_x=True)
+    assert np.allclose(e2.x, e1.x, atol=1e-14)
+    assert np.allclose(e2.grad[:inst.J], e1.grad, atol=1e-12)
+    assert np.allclose(e2.grad[inst.J:], -b2.astype(np.float32), atol=0)
+    assert e2.dual == pytest.approx(e1.dual - mu[inst.J:] @ b2.astype(np.float32), rel=1e-12)
+    D = P2.row_scale()
+    assert np.all(D[inst.J:] == 1.0)  # zero rows keep D = 1
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_families_gradient_and_norm(weighted):
+    """Danskin's gradient over all m J rows by central differences, and the
+    block-diagonal spectral norm against numpy on the dense operator."""
+    inst = synth.add_families(_tiny(I=50, J=6, seed=63), 3, seed=64)
+    P = oracle.Problem(inst, weighted=weighted)
+    R = 3 * inst.J
+    for gamma in (0.4, 0.02):
+        mu = RNG.uniform(0.0, 1.0, R)
+        ev = P.eval(mu, gamma)
+        for r in range(R):
+            h = 1e-6 * max(1.0, abs(mu[r]))
+            e = np.zeros(R)
+            e[r] = h
+            fd = (P.eval(mu + e, gamma).dual - P.eval(mu - e, gamma).dual) / (2 * h)
+            assert abs(fd - ev.grad[r]) <= 1e-6 * (abs(ev.ax[r]) + abs(inst.b[r]) + 1.0)
+    A = np.zeros((R, inst.E))
+    for k in range(3):
+        A[k * inst.J + inst.dst, np.arange(inst.E)] = inst.a[k]
+    w = np.sum(inst.a.astype(np.float64) ** 2, axis=0) if weighted else np.ones(inst.E)
+    Aw = A / np.sqrt(w)
+    assert P.norm2_sq() == pytest.approx(np.linalg.norm(Aw, 2) ** 2, rel=1e-9)
+    D = P.row_scale()
+    assert np.allclose(np.sum((D[:, None] * Aw) ** 2, axis=1), 1.0)  # unit rows
+    assert P.norm2_sq(D) == pytest.approx(np.linalg.norm(D[:, None] * Aw, 2) ** 2, rel=1e-9)
+
+
+def test_families_tiny_lp_bounds():
+    """Two families on tiny LPs: the solver's g*(gamma) lies between the LP
+    optimum (HiGHS on the dense constraints) and that plus gamma I / 2."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    for seed in (1, 2, 3):
+        inst = synth.add_families(_tiny_lp(seed), 2, seed=seed, rho=(0.3, 0.6))
+        c, G1, h1 = _lp_parts(synth.Instance(inst.off, inst.dst, inst.c, inst.a[0],
+                                             inst.b[:inst.J], inst.J))
+        A2 = np.zeros((inst.J, inst.E))
+        A2[inst.dst, np.arange(inst.E)] = inst.a[1]
+        G = np.vstack([G1, A2])
+        h = np.concatenate([h1, inst.b[inst.J:].astype(float)])
+        lp = scipy_opt.linprog(c, A_ub=G, b_ub=h, bounds=(None, None), method="highs")
+        assert lp.status == 0
+        P = oracle.Problem(inst)
+        for gamma in (0.1, 0.01):
+            res = P.solve(gamma0=gamma, gamma_final=gamma, halve_every=0,
+                          max_step=gamma / P.norm2_sq(), init_step=1e-3 * gamma,
+                          max_iters=20000, stop_on_tol=False, row_normalize=False)
+            g = P.eval(res["mu"], gamma).dual
+            assert lp.fun - 1e-9 <= g + 2e-6
+            assert g <= lp.fun + gamma * inst.I / 2 + 1e-9
