@@ -223,19 +223,21 @@ dualip_status create_multi(const dualip_problem_desc* d, void* stream, dualip_pr
       (e = cudaStreamSynchronize(s)))
     return bail(cuda_fail(e, "building the problem"));
   if (st.err) return bail(fail(DUALIP_EINVAL, "dst out of [0, J) or non-finite c / a"));
-  // fixed-point scales: |(A x)_r| <= max in-degree max|a|; |sum c x| <= I max|c|;
-  // sum w x^2 <= I max w with w = sum_k a_k^2 (primal scaling) or 1
+  // fixed-point scales: |(A x)_r| <= max in-degree max|a|; |sum c x| <= U max|c|
+  // and sum w x^2 <= U max w with w = sum_k a_k^2 (primal scaling) or 1, where
+  // U = I on the simplex (sum_e x_e <= 1 per source) and E on the unit box
   float mc, ma;
   std::memcpy(&mc, &cnt[Jd], 4);
   std::memcpy(&ma, &cnt[Jd + 1], 4);
   const unsigned maxcnt = Jd > 0 ? *std::max_element(cnt.begin(), cnt.begin() + Jd) : 0u;
   const double mw = P.weighted ? std::max(1.0, (double)m * (double)ma * (double)ma) : 1.0;
+  const double units = (double)(P.box ? E : I);
   int ex = 0;
   std::frexp(std::max((double)maxcnt * ma, 1e-30), &ex);
   P.exp_y = std::max(-100, std::min(100, 61 - ex));
-  std::frexp(std::max((double)I * mc, 1e-30), &ex);
+  std::frexp(std::max(units * mc, 1e-30), &ex);
   P.exp_c = std::max(-100, std::min(100, 61 - ex));
-  std::frexp(std::max((double)I * mw, 1e-30), &ex);
+  std::frexp(std::max(units * mw, 1e-30), &ex);
   P.exp_w = std::max(-100, std::min(100, 61 - ex));
   P.off_host = std::move(off);
   *out = h;
@@ -309,6 +311,9 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   P.storage = d->storage;
   P.weighted = d->primal_scaling;
   P.box = d->projection == DUALIP_PROJ_BOX ? 1 : 0;
+  // small mean degree (at most 16 edges per source): the pass takes sources
+  // 32 at a time and gives a span of up to 16 slots one lane
+  P.tiny = (kTinyBatches && I > 0 && E <= 16 * I) ? 1 : 0;
   P.last_stream = s;
   auto bail = [&](dualip_status st) {
     cudaStreamSynchronize(s);
@@ -325,6 +330,8 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   std::vector<int64_t> tiles, tile_e;
   build_tiles(off_s, tiles, tile_e, tile_edges_for(P.storage), kTileSources);
   P.ntiles = (int64_t)tiles.size() - 1;
+  for (int64_t t = 0; t < P.ntiles && !P.has_big; ++t)
+    P.has_big = tile_e[t + 1] - tile_e[t] > tile_edges_for(P.storage) ? 1 : 0;
   P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P.num_sms, P.ntiles));
   P.h_mu = std::min(J, kMaxCachedDests);
   P.h_y = std::min(J, kMaxPrivDests);
@@ -514,16 +521,18 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
     int ex = 0;
     std::frexp(std::max((double)maxcnt * ma, 1e-30), &ex);  // bound < 2^ex
     P.exp_y = std::max(-100, std::min(100, 61 - ex));
-    // Objective partials: every source has sum_e x_e <= 1 and x_e <= 1, so
-    // |sum c x| <= I max|c| and sum w x^2 <= I max w (w = a^2, or 1 where
-    // a = 0, with primal scaling; w = 1 without).  The BF16 rounding of c and a
-    // stays far inside the two bits of headroom below 2^63.
+    // Objective partials: on the simplex every source has sum_e x_e <= 1 and
+    // x_e <= 1, so |sum c x| <= I max|c| and sum w x^2 <= I max w (w = a^2, or
+    // 1 where a = 0, with primal scaling; w = 1 without); on the unit box only
+    // x_e <= 1 holds, and E takes the place of I.  The BF16 rounding of c and
+    // a stays far inside the two bits of headroom below 2^63.
     float mc;
     std::memcpy(&mc, &absmax[0], 4);
     const double mw = P.weighted ? std::max(1.0, (double)ma * (double)ma) : 1.0;
-    std::frexp(std::max((double)I * mc, 1e-30), &ex);
+    const double units = (double)(P.box ? E : I);
+    std::frexp(std::max(units * mc, 1e-30), &ex);
     P.exp_c = std::max(-100, std::min(100, 61 - ex));
-    std::frexp(std::max((double)I * mw, 1e-30), &ex);
+    std::frexp(std::max(units * mw, 1e-30), &ex);
     P.exp_w = std::max(-100, std::min(100, 61 - ex));
   }
   DeviceStatus st{};

@@ -67,6 +67,20 @@ constexpr unsigned kWaitHintNs = DUALIP_WAIT_HINT_NS;  // mbarrier suspend hint 
 #endif
 constexpr bool kWarpCand = DUALIP_WARP_CAND != 0;
 constexpr int kCandRounds = 16;  // Michelot rounds before the multi-pass path takes over
+// A source larger than a stage is projected by all consumer warps of the CTA
+// (1) or by one warp (0).
+#ifndef DUALIP_BLOCK_CLASS
+#define DUALIP_BLOCK_CLASS 1
+#endif
+constexpr bool kBlockClass = DUALIP_BLOCK_CLASS != 0;
+constexpr int kBlockUnroll = 4;  // edges in flight per consumer thread in the block class
+constexpr int kBlockCand = 4;    // candidate edges a consumer thread keeps in registers
+// Problems with at most 16 edges per source on average take the pass variant
+// with 32-source batches and one-lane groups (1), or the standard one (0).
+#ifndef DUALIP_TINY_BATCHES
+#define DUALIP_TINY_BATCHES 1
+#endif
+constexpr bool kTinyBatches = DUALIP_TINY_BATCHES != 0;
 constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
 constexpr int kMaxCachedDests = 10240; // hot destinations whose mu lives in smem
 constexpr int kMaxPrivDests = DUALIP_PRIV_DESTS;  // hot destinations accumulated in smem
@@ -192,6 +206,7 @@ struct PassParams {
   const float* gamma_of;
   long long* slot_part;   // per-slot fixed-point (sum c x, sum w x^2) (slot scales)
   int lean80;  // 4-lane lean groups may take spans up to 80 (else 64)
+  int grab;    // tiles per grab of the single-problem schedule (1..31)
 };
 
 struct Problem {
@@ -200,6 +215,8 @@ struct Problem {
   int storage = DUALIP_EDGE_F32;
   int weighted = 0;
   int box = 0;  // projection onto the unit box [0, 1]^E instead of per-source simplices
+  int tiny = 0;  // small mean degree: the pass claims 32 sources at a time (1-lane groups)
+  int has_big = 0;  // some source is larger than a stage: tiles are grabbed one at a time
   // constraint families (Definition 1): with m > 1, J counts rows (m Jd, row
   // k Jd + j), the edges keep the caller's order and destination ids, and c,
   // a (family-major, a[k E + e]) live in cm, am; the pass is multi.cu's

@@ -695,6 +695,222 @@ __device__ __forceinline__ void project_multipass(const View& v, int64_t base, i
   }
 }
 
+// ---------------------------------------------- block class (big sources) ----
+// A source larger than a stage is projected by every consumer warp of the CTA
+// together, straight from global memory: each pass is strided over the
+// kConsumerWarps * 32 consumer threads and ends in a block reduction.  The
+// reductions combine the per-warp partials in a fixed order, so every thread
+// gets the same values and the result does not depend on timing.  sm holds
+// 3 floats per consumer warp; barrier 2 is the consumers' named barrier.
+__device__ __forceinline__ void consumer_bar() {
+  asm volatile("bar.sync 2, %0;" ::"r"(kConsumerWarps * 32) : "memory");
+}
+template <bool MAX0, bool MAX2>
+__device__ __forceinline__ float3 block_reduce3(float a, float b, float c, float* sm, int cw,
+                                                int lane) {
+  a = MAX0 ? warp_max(a) : warp_sum(a);
+  b = warp_sum(b);
+  c = MAX2 ? warp_max(c) : warp_sum(c);
+  if (lane == 0) {
+    sm[3 * cw] = a;
+    sm[3 * cw + 1] = b;
+    sm[3 * cw + 2] = c;
+  }
+  consumer_bar();
+  float ra = MAX0 ? -CUDART_INF_F : 0.f, rb = 0.f, rc = MAX2 ? -CUDART_INF_F : 0.f;
+  for (int w = 0; w < kConsumerWarps; ++w) {
+    ra = MAX0 ? fmaxf(ra, sm[3 * w]) : ra + sm[3 * w];
+    rb += sm[3 * w + 1];
+    rc = MAX2 ? fmaxf(rc, sm[3 * w + 2]) : rc + sm[3 * w + 2];
+  }
+  consumer_bar();  // sm is free again
+  return make_float3(ra, rb, rc);
+}
+
+// The projection of a source larger than a stage by every consumer thread
+// ct = 0 .. NT - 1 (NT = kConsumerWarps * 32), thread ct taking edges ct,
+// ct + NT, ... (a fixed assignment, so every sum is the same from run to run).
+// Each pass loads kBlockUnroll edges per thread before using them.
+//   pass 1: r_max, the saturation sum and max(r - gamma w) (block reductions);
+//   pass 2 (sum constraint binding): each thread keeps the shifted scores d of
+//     its candidate edges (d > lb, a set that holds the active set; at most
+//     kBlockCand per thread) in registers; Michelot's rounds then run on the
+//     registers alone, and x goes out for the candidates only.  A thread with
+//     more candidates sends the source to full passes (the multi-pass
+//     arithmetic) for the rounds and x;
+//   unsaturated sum constraint: x = alpha r_+ on one more pass.
+template <bool BF16, bool W>
+__device__ __forceinline__ void project_block_body(const GlobalView<BF16>& v, int64_t base,
+                                                   int64_t d, int64_t e_glob, int ct, int cw,
+                                                   int lane, const Ctx& cx, Sums& acc, float* sm);
+// Out of line, with its inputs by value and its objective partials returned:
+// it is rare, and its registers (edges in flight, candidates) must not weigh
+// on the hot loop's allocation.
+template <bool BF16, bool W>
+__device__ __noinline__ longlong2 project_block(const GlobalView<BF16> v, int64_t base, int64_t d,
+                                                int64_t e_glob, int ct, int cw, int lane,
+                                                const Ctx cx, float* sm) {
+  Sums acc;
+  project_block_body<BF16, W>(v, base, d, e_glob, ct, cw, lane, cx, acc, sm);
+  return make_longlong2(acc.cx, acc.wxx);
+}
+template <bool BF16, bool W>
+__device__ __forceinline__ void project_block_body(const GlobalView<BF16>& v, int64_t base,
+                                                   int64_t d, int64_t e_glob, int ct, int cw,
+                                                   int lane, const Ctx& cx, Sums& acc, float* sm) {
+  constexpr int NT = kConsumerWarps * 32;
+  constexpr int U = kBlockUnroll;
+  constexpr int NC = kBlockCand;
+  auto load = [&](int64_t k, int& j, float& c, float& a, float& hi, float& lo) {
+    v.edge(base + k, j, c, a);
+    score(c, a, cx.mu(j), hi, lo);
+  };
+  float rmax = -CUDART_INF_F, s0 = 0.f, mb = -CUDART_INF_F;
+  for (int64_t k0 = ct; k0 < d; k0 += (int64_t)U * NT) {
+    int j[U];
+    float c[U], a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {  // the loads first
+      const int64_t k = k0 + (int64_t)u * NT;
+      if (k < d) v.edge(base + k, j[u], c[u], a[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + (int64_t)u * NT >= d) break;
+      float hi, lo;
+      score(c[u], a[u], cx.mu(j[u]), hi, lo);
+      const float rf = __fadd_rn(hi, lo);
+      rmax = fmaxf(rmax, rf);
+      if (rf > 0.f) s0 += __fmul_rn(edge_alpha<W>(cx, edge_w<W>(a[u])), rf);
+      if (W) mb = fmaxf(mb, __fsub_rn(rf, __fmul_rn(cx.gamma, edge_w<W>(a[u]))));
+    }
+  }
+  const float3 r1 = block_reduce3<true, true>(rmax, s0, mb, sm, cw, lane);
+  rmax = r1.x;
+  s0 = r1.y;
+  const int mode = rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2);
+  if (mode == 0 && cx.x_out == nullptr) return;  // every x is 0
+  float t = 0.f;
+  if (mode == 2) {
+    const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
+    const float lb = W ? __fsub_rn(fminf(__fsub_rn(r1.z, rmax), 0.f), slack)
+                       : __fsub_rn(-cx.gamma, slack);
+    // pass 2: the candidates of this thread, in registers
+    int64_t ck[NC];
+    float cd[NC], ca[NC];
+    int nc = 0;
+    for (int64_t k0 = ct; k0 < d; k0 += (int64_t)U * NT) {
+      int j[U];
+      float c[U], a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = k0 + (int64_t)u * NT;
+        if (k < d) v.edge(base + k, j[u], c[u], a[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = k0 + (int64_t)u * NT;
+        if (k >= d) break;
+        float hi, lo;
+        score(c[u], a[u], cx.mu(j[u]), hi, lo);
+        const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
+        if (dk > lb) {
+#pragma unroll
+          for (int q = 0; q < NC; ++q)
+            if (q == nc) {
+              ck[q] = k;
+              cd[q] = dk;
+              ca[q] = edge_alpha<W>(cx, edge_w<W>(a[u]));
+            }
+          ++nc;
+        }
+      }
+    }
+    const float3 ov = block_reduce3<true, false>(nc > NC ? 1.f : 0.f, 0.f, 0.f, sm, cw, lane);
+    if (ov.x == 0.f) {
+      // Michelot's rounds on the registers
+      float theta = lb, nprev = -1.f;
+      t = lb;
+      for (int it = 0; it <= NC * NT; ++it) {
+        float sr = 0.f, sa = 0.f, n = 0.f;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          if (q < nc && cd[q] > theta) {
+            sr += W ? __fmul_rn(ca[q], cd[q]) : cd[q];
+            sa += W ? ca[q] : 0.f;
+            n += 1.f;
+          }
+        }
+        const float3 r = block_reduce3<false, false>(sr, sa, n, sm, cw, lane);
+        if (r.z == nprev) break;
+        t = W ? __fdiv_rn(r.x - 1.f, r.y) : __fdiv_rn(r.x - cx.gamma, r.z);
+        nprev = r.z;
+        theta = fmaxf(theta, t);
+      }
+      // x of the candidates (every other edge has x = 0)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        if (q < nc && cd[q] > t) {
+          int j;
+          float c, a;
+          v.edge(base + ck[q], j, c, a);
+          acc.account(cx, j, c, a, edge_w<W>(a), __fmul_rn(ca[q], __fsub_rn(cd[q], t)));
+        }
+      }
+      if (cx.x_out != nullptr) {
+        for (int64_t k = ct; k < d; k += NT) {
+          float x = 0.f;
+#pragma unroll
+          for (int q = 0; q < NC; ++q)
+            if (q < nc && ck[q] == k && cd[q] > t) x = __fmul_rn(ca[q], __fsub_rn(cd[q], t));
+          cx.x_out[e_glob + k] = x;
+        }
+      }
+      return;
+    }
+    // too many candidates on some thread: full passes
+    float theta = lb, nprev = -1.f;
+    t = lb;
+    for (int64_t it = 0; it <= d; ++it) {
+      float sr = 0.f, sa = 0.f, n = 0.f;
+      for (int64_t k = ct; k < d; k += NT) {
+        int j;
+        float c, a, hi, lo;
+        load(k, j, c, a, hi, lo);
+        const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
+        if (dk > theta) {
+          const float al = edge_alpha<W>(cx, edge_w<W>(a));
+          sr += W ? __fmul_rn(al, dk) : dk;
+          sa += W ? al : 0.f;
+          n += 1.f;
+        }
+      }
+      const float3 r = block_reduce3<false, false>(sr, sa, n, sm, cw, lane);
+      if (r.z == nprev) break;
+      t = W ? __fdiv_rn(r.x - 1.f, r.y) : __fdiv_rn(r.x - cx.gamma, r.z);
+      nprev = r.z;
+      theta = fmaxf(theta, t);
+    }
+  }
+  for (int64_t k = ct; k < d; k += NT) {
+    int j;
+    float c, a, hi, lo;
+    load(k, j, c, a, hi, lo);
+    const float w = edge_w<W>(a);
+    const float al = edge_alpha<W>(cx, w);
+    float x = 0.f;
+    if (mode == 1) {
+      const float rf = __fadd_rn(hi, lo);
+      x = rf > 0.f ? __fmul_rn(al, rf) : 0.f;
+    } else if (mode == 2) {
+      const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
+      x = dk > t ? __fmul_rn(al, __fsub_rn(dk, t)) : 0.f;
+    }
+    if (x > 0.f) acc.account(cx, j, c, a, w, x);
+    if (cx.x_out != nullptr) cx.x_out[e_glob + k] = x;
+  }
+}
+
 // Unweighted sources of at most 512 edges that the lane groups leave
 // (unsaturated, or several edges within gamma of the top).  One pass over the
 // staged source keeps each lane's FP32 scores r = -(c + a mu) (which equal the
@@ -791,12 +1007,13 @@ __device__ __forceinline__ bool project_warp_cand(const StageView<BF16>& sv, int
 // constraint): the block problem separates by edge, and its minimiser is
 // x = clamp(alpha r, 0, 1), alpha = 1 / (gamma w), r = -(c + a mu) formed by one
 // FMA (a single rounding), so x carries FP32 accuracy.  Edges [e0, e1) of the
-// view; x_out (WX) at e_glob0 + (k - e0).
+// view, edge e0 + first + k stride for k = 0, 1, ...; x_out (WX) at
+// e_glob0 + (k - e0).
 template <bool BF16, bool W, bool WX, class View>
 __device__ __forceinline__ void project_box(const View& v, int64_t e0, int64_t e1,
-                                            int64_t e_glob0, int lane, const Ctx& cx,
+                                            int64_t e_glob0, int first, int stride, const Ctx& cx,
                                             Sums& acc) {
-  for (int64_t k = e0 + lane; k < e1; k += 32) {
+  for (int64_t k = e0 + first; k < e1; k += stride) {
     int j;
     float c, a;
     v.edge(k, j, c, a);
@@ -896,7 +1113,11 @@ __device__ __forceinline__ void flush_sums(const Sums& acc, long long* dst, int 
 // a tile of another slot the consumer warps meet at a shared barrier, flush
 // the previous slot's shared bins and objective partials, load the new slot's
 // mu cache, and meet again; the producer never waits for them there.
-template <bool BF16, bool W, bool MU_SMEM, bool WRITE_X, bool BATCH, bool BOX = false>
+// BIG: the problem has sources larger than a stage, which the block class
+// projects (its call lives only in these instances and in the WRITE_X ones,
+// so the other instances keep the hot loop's registers to themselves).
+template <bool BF16, bool W, bool MU_SMEM, bool WRITE_X, bool BATCH, bool BOX = false,
+          bool TINY = false, bool BIG = false>
 __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p) {
   using L = Layout<BF16>;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1074,7 +1295,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       // Dynamic tile grabs of kGrab tiles from a counter shared by all CTAs
       // (balanced ends); the next grab is requested while this one is
       // staged.  The end marker stops the consumers.
-      constexpr int kGrab = DUALIP_GRAB;
+      const int kGrab = p.grab;
       unsigned long long* next = &p.status->tile_next;
       long long nxt = 0;
       if (lane == 0) nxt = (long long)atomicAdd(next, (unsigned long long)kGrab);
@@ -1196,14 +1417,10 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       if (BOX) {
         // unit-box projection: every edge on its own; a warp takes the edges
         // of a claimed batch of eight sources (or of an oversized source)
-        if (si.big) {
-          unsigned b = 0u;
-          if (lane == 0) b = atoms_add_u32(claim_a, 1u);
-          b = __shfl_sync(0xffffffffu, b, 0);
-          if (b == 0u) {
-            GlobalView<BF16> gv{cx.dst_g, cx.ca2_g, cx.ca_g};
-            project_box<BF16, W, WRITE_X>(gv, si.e0, si.e1, si.e0, lane, cx, acc);
-          }
+        if (si.big) {  // every consumer thread takes a share of the edges
+          GlobalView<BF16> gv{cx.dst_g, cx.ca2_g, cx.ca_g};
+          project_box<BF16, W, WRITE_X>(gv, si.e0, si.e1, si.e0, tid - 32, kConsumerWarps * 32,
+                                        cx, acc);
         } else {
           const StageView<BF16> sv = stage_view<BF16>(smem, s);
           const int nsrc = (int)(si.s1 - si.s0);
@@ -1217,43 +1434,53 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
             const int li = li0 + 8 * (int)bi;
             const int n8 = nsrc - 8 * (int)bi < 8 ? nsrc - 8 * (int)bi : 8;
             const int e_lo = (int)(sv.off(li) - si.a0), e_hi = (int)(sv.off(li + n8) - si.a0);
-            project_box<BF16, W, WRITE_X>(sv, e_lo, e_hi, si.a0 + e_lo, lane, cx, acc);
+            project_box<BF16, W, WRITE_X>(sv, e_lo, e_hi, si.a0 + e_lo, lane, 32, cx, acc);
           }
         }
       } else if (si.big) {
-        // the warp that claims it projects a source larger than a stage
-        // straight from global memory
-        unsigned b = 0u;
-        if (lane == 0) b = atoms_add_u32(claim_a, 1u);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (b == 0u) {
-          GlobalView<BF16> gv{cx.dst_g, cx.ca2_g, cx.ca_g};
-          project_multipass<BF16, W>(gv, si.e0, si.e1 - si.e0, si.e0, lane, cx, acc);
+        // a source larger than a stage: every consumer warp projects it
+        // together from global memory (block class), or (kBlockClass off)
+        // the warp that claims it does
+        GlobalView<BF16> gv{cx.dst_g, cx.ca2_g, cx.ca_g};
+        if (kBlockClass && (BIG || WRITE_X)) {
+          const longlong2 ps = project_block<BF16, W>(gv, si.e0, si.e1 - si.e0, si.e0, tid - 32,
+                                                      warp - 1, lane, cx, dred);
+          acc.cx += ps.x;
+          acc.wxx += ps.y;
+        } else {
+          unsigned b = 0u;
+          if (lane == 0) b = atoms_add_u32(claim_a, 1u);
+          b = __shfl_sync(0xffffffffu, b, 0);
+          if (b == 0u) project_multipass<BF16, W>(gv, si.e0, si.e1 - si.e0, si.e0, lane, cx, acc);
         }
       } else {
         const StageView<BF16> sv = stage_view<BF16>(smem, s);
         const int nsrc = (int)(si.s1 - si.s0);
         const int li0 = (int)(si.s0 - si.o0);
-        // Sources are taken in batches of eight.  The span of a source (stage
-        // slot of its first edge mod 4, plus its degree) picks the group
-        // width: 4 lanes (span <= 64, eight sources per warp), 8 (<= 128),
-        // 16 (<= 256), 32 (<= 512), else the multi-pass path.  Whatever the
-        // lean path leaves (unsaturated sources, near-ties, the primal output)
-        // goes through the multi-pass path.
-        const unsigned nb = (unsigned)((nsrc + 7) >> 3);
+        // Sources are taken in batches of eight (32 in the small-degree
+        // variant TINY).  The span of a source (stage slot of its first edge
+        // mod 4, plus its degree) picks the group width: 1 lane (TINY only,
+        // span <= 16, 32 sources per warp), 4 lanes (span <= 64, eight
+        // sources per warp), 8 (<= 128), 16 (<= 256), 32 (<= 512), else the
+        // multi-pass path.  Whatever the lean path leaves (unsaturated
+        // sources, near-ties, the primal output) goes through the candidate
+        // or multi-pass path.
+        constexpr int NB = TINY ? 32 : 8;
+        const unsigned nb = (unsigned)((nsrc + NB - 1) / NB);
         for (;;) {
           unsigned bi = 0u;
           if (lane == 0) bi = atoms_add_u32(claim_a, 1u);
           bi = __shfl_sync(0xffffffffu, bi, 0);
           if (bi >= nb) break;
-          const int li = li0 + 8 * (int)bi;
-          const int n8 = nsrc - 8 * (int)bi < 8 ? nsrc - 8 * (int)bi : 8;
+          const int li = li0 + NB * (int)bi;
+          const int n8 = nsrc - NB * (int)bi < NB ? nsrc - NB * (int)bi : NB;
           const int64_t oq = sv.off(li + (lane <= n8 ? lane : n8));
-          const int64_t on = __shfl_down_sync(0xffffffffu, oq, 1);
+          int64_t on = __shfl_down_sync(0xffffffffu, oq, 1);
+          if (TINY && lane == 31) on = sv.off(li + n8);  // the batch's end offset
           const int dq = lane < n8 ? (int)(on - oq) : 0;
           const int bq = (int)(oq - si.a0);
           const int spq = dq > 0 ? (bq & 3) + dq : 0;
-          unsigned needm;
+          unsigned needm, needm_tiny = 0u;
           if (WRITE_X) {
             needm = __ballot_sync(0xffffffffu, dq > 0);
           } else {
@@ -1261,9 +1488,15 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
             // lean80 up to 80 in one pass (a window of 64 or 80 slots, by the
             // batch's largest span) unless the batch needs an 8-lane pass
             // anyway: then spans over 64 join that pass
+            const bool in1 = TINY && dq > 0 && spq <= 16;
             const bool over80 = !p.lean80 || __any_sync(0xffffffffu, spq > 80 && spq <= 128);
             const int span4 = over80 ? 64 : 80;
-            const bool in4 = dq > 0 && spq <= span4;
+            const bool in4 = dq > 0 && spq <= span4 && !in1;
+            if (TINY) {
+              const unsigned m1 = __ballot_sync(0xffffffffu, in1);
+              if (m1) needm_tiny = lean_over<1, 4, BF16, W, MU_SMEM, BATCH>(sv, m1, bq, dq, lane,
+                                                                            cx, acc);
+            }
             const unsigned m4 = __ballot_sync(0xffffffffu, in4);
             const unsigned m128 = __ballot_sync(0xffffffffu, spq > span4 && spq <= 128);
             const unsigned m256 = __ballot_sync(0xffffffffu, spq > 128 && spq <= 256);
@@ -1278,6 +1511,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
             if (m128) needm |= lean_over<8, 4, BF16, W, MU_SMEM, BATCH>(sv, m128, bq, dq, lane, cx, acc);
             if (m256) needm |= lean_over<16, 4, BF16, W, MU_SMEM, BATCH>(sv, m256, bq, dq, lane, cx, acc);
             if (m512) needm |= lean_over<32, 4, BF16, W, MU_SMEM, BATCH>(sv, m512, bq, dq, lane, cx, acc);
+            needm |= needm_tiny;
           }
           while (needm) {
             const int q = __ffs(needm) - 1;
@@ -1492,9 +1726,10 @@ size_t pass_smem_bytes(int storage) {
   return storage == DUALIP_EDGE_BF16 ? Layout<true>::kTotal : Layout<false>::kTotal;
 }
 
-template <bool BF16, bool W, bool MU, bool WX, bool B = false, bool BOX = false>
+template <bool BF16, bool W, bool MU, bool WX, bool B = false, bool BOX = false,
+          bool TINY = false, bool BIG = false>
 static cudaError_t set_smem() {
-  return cudaFuncSetAttribute(dualgrad_pass_kernel<BF16, W, MU, WX, B, BOX>,
+  return cudaFuncSetAttribute(dualgrad_pass_kernel<BF16, W, MU, WX, B, BOX, TINY, BIG>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Layout<BF16>::kTotal);
 }
@@ -1516,7 +1751,23 @@ cudaError_t configure_pass_kernels() {
       set_smem<false, false, false, true, false, true>(),
       set_smem<false, true, false, true, false, true>(),
       set_smem<true, false, false, true, false, true>(),
-      set_smem<true, true, false, true, false, true>()};
+      set_smem<true, true, false, true, false, true>(),
+      set_smem<false, false, false, false, false, false, true>(),
+      set_smem<false, false, true, false, false, false, true>(),
+      set_smem<false, true, false, false, false, false, true>(),
+      set_smem<false, true, true, false, false, false, true>(),
+      set_smem<true, false, false, false, false, false, true>(),
+      set_smem<true, false, true, false, false, false, true>(),
+      set_smem<true, true, false, false, false, false, true>(),
+      set_smem<true, true, true, false, false, false, true>(),
+      set_smem<false, false, false, false, false, false, false, true>(),
+      set_smem<false, false, true, false, false, false, false, true>(),
+      set_smem<false, true, false, false, false, false, false, true>(),
+      set_smem<false, true, true, false, false, false, false, true>(),
+      set_smem<true, false, false, false, false, false, false, true>(),
+      set_smem<true, false, true, false, false, false, false, true>(),
+      set_smem<true, true, false, false, false, false, false, true>(),
+      set_smem<true, true, true, false, false, false, false, true>()};
   for (cudaError_t e : es)
     if (e != cudaSuccess) return e;
   return cudaSuccess;
@@ -1557,6 +1808,9 @@ static PassParams pass_params(const Problem& P, const float* gamma_dev, float ga
   p.gamma_of = nullptr;
   p.slot_part = nullptr;
   p.lean80 = 1;
+  // a tile holding a source larger than a stage takes a whole CTA for a
+  // while: one tile per grab keeps two of them off the same CTA
+  p.grab = P.has_big ? 1 : DUALIP_GRAB;
   return p;
 }
 
@@ -1576,8 +1830,14 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
   const size_t smem = pass_smem_bytes(P.storage);
   const dim3 grid(P.grid), block(kThreads);
   cudaError_t e = cudaSuccess;
-#define DUALIP_LAUNCH(B, W, M, X) \
-  e = launch_pdl(dualgrad_pass_kernel<B, W, M, X, false>, grid, block, smem, s, p)
+#define DUALIP_LAUNCH(B, W, M, X)                                                            \
+  e = (!(X) && P.has_big)                                                                    \
+          ? launch_pdl(dualgrad_pass_kernel<B, W, M, false, false, false, false, true>, grid,   \
+                       block, smem, s, p)                                                    \
+      : (!(X) && P.tiny)                                                                     \
+          ? launch_pdl(dualgrad_pass_kernel<B, W, M, false, false, false, true>, grid, block,   \
+                       smem, s, p)                                                           \
+          : launch_pdl(dualgrad_pass_kernel<B, W, M, X, false>, grid, block, smem, s, p)
 #define DUALIP_LAUNCH_BOX(B, W, X) \
   e = launch_pdl(dualgrad_pass_kernel<B, W, false, X, false, true>, grid, block, smem, s, p)
   if (P.box) {
@@ -1631,6 +1891,7 @@ cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, in
                               DeviceStatus* status, int grid, int lean80, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   PassParams p{};
+  p.grab = DUALIP_GRAB;  // (the batched pass takes contiguous ranges)
   p.lean80 = lean80;
   p.ntiles = ntiles;
   p.jt = jt;

@@ -264,6 +264,23 @@ def add_families(inst: Instance, m: int, seed: int = 77, a_range=(0.5, 1.5),
                     meta=dict(inst.meta, families=m))
 
 
+def with_hubs(base: Instance, n_hubs: int = 100, deg_range=(100_000, 1_000_000),
+              J: int = 1_000_000, seed: int = 1007) -> Instance:
+    """The base instance plus n_hubs sources of log-uniform degree in deg_range,
+    each linked to distinct destinations drawn uniformly from J >= base.J (the
+    base keeps its destination ids), c and a by the base laws; greedy-load
+    budgets on the whole."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    deg = np.round(np.exp(rng.uniform(np.log(deg_range[0]), np.log(deg_range[1]),
+                                      n_hubs))).astype(np.int64)
+    hubs = from_degrees(deg, J, seed, DST_UNIFORM)
+    off = np.concatenate([base.off, base.off[-1] + hubs.off[1:]]).astype(np.int64)
+    inst = Instance(off, np.concatenate([base.dst, hubs.dst]), np.concatenate([base.c, hubs.c]),
+                    np.concatenate([base.a, hubs.a]), np.zeros(J, np.float32), J,
+                    name=f"{base.name}+{n_hubs}hubs", meta=dict(base.meta, hubs=n_hubs))
+    return greedy_budgets(inst, seed=seed)
+
+
 def batch_shapes(n: int = 256, seed: int = CONFIG_SEEDS["c4"], i_range=(1_000, 2_000_000),
                  j_range=(10, 50_000)):
     """(I, J, seed) of each instance of the batched workload c4."""

@@ -127,6 +127,20 @@ def test_adversarial_degrees(dl):
             P, Po, _, _ = check_eval(dl, inst, lam, gamma, P=P, Po=Po)  # reuse: scratch reset
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+def test_block_class_hub_sources(dl, weighted):
+    """Sources far larger than a stage (the block class: all consumer warps of
+    a CTA on one source, from global memory) among ordinary ones, up to a
+    million edges, at a slack, a moderate and a tiny gamma."""
+    degs = np.array([1_000_000, 5, 250_000, 40, 3_201, 0, 60_000, 2])
+    inst = synth.from_degrees(degs, 1_100_000, 19, synth.DST_UNIFORM, b_frac=0.3)
+    rng = np.random.default_rng(44)
+    P = Po = None
+    for gamma in (50.0, 1e-2, 1e-5):
+        for lam in (np.zeros(inst.J), rng.uniform(0, 1, inst.J)):
+            P, Po, _, _ = check_eval(dl, inst, lam, gamma, weighted, P=P, Po=Po)
+
+
 def test_many_tiny_sources_and_all_hot(dl):
     # degree-1 sources (tile capped by the source count) into 3 destinations
     inst = synth.from_degrees(np.ones(50_000, dtype=np.int64), 3, 12, synth.DST_UNIFORM,
