@@ -330,8 +330,35 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   std::vector<int64_t> tiles, tile_e;
   build_tiles(off_s, tiles, tile_e, tile_edges_for(P.storage), kTileSources);
   P.ntiles = (int64_t)tiles.size() - 1;
-  for (int64_t t = 0; t < P.ntiles && !P.has_big; ++t)
-    P.has_big = tile_e[t + 1] - tile_e[t] > tile_edges_for(P.storage) ? 1 : 0;
+  // Segment classes of the sources larger than a stage: the block class up
+  // to kMultiBlockStages stages, the multi-block class (hub sources) from
+  // there (not for the unit box, whose edges are independent, and not for a
+  // source past the hub kernel's 32-bit edge indices).
+  const int64_t stage_e = tile_edges_for(P.storage);
+  std::vector<HubDesc> hubs;
+  std::vector<int32_t> chunk_hub;
+  int64_t hub_edges = 0;
+  P.mb_min = kMultiBlockStages > 0 && !P.box ? (int64_t)kMultiBlockStages * stage_e : INT64_MAX;
+  for (int64_t t = 0; t < P.ntiles; ++t)
+    if (tile_e[t + 1] - tile_e[t] >= (int64_t)INT32_MAX - kHubChunk) P.mb_min = INT64_MAX;
+  for (int64_t t = 0; t < P.ntiles; ++t) {
+    const int64_t ne = tile_e[t + 1] - tile_e[t];
+    if (ne >= P.mb_min) {
+      HubDesc hd{};
+      hd.e0 = tile_e[t];
+      hd.cand0 = hub_edges;
+      hd.deg = (int32_t)ne;
+      hd.c0 = (int32_t)chunk_hub.size();
+      hd.nch = (int32_t)((ne + kHubChunk - 1) / kHubChunk);
+      chunk_hub.insert(chunk_hub.end(), (size_t)hd.nch, (int32_t)hubs.size());
+      hubs.push_back(hd);
+      hub_edges += ne;
+    } else if (ne > stage_e) {
+      P.has_big = 1;
+    }
+  }
+  P.nhub = (int)hubs.size();
+  P.nchunks = (int64_t)chunk_hub.size();
   P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P.num_sms, P.ntiles));
   P.h_mu = std::min(J, kMaxCachedDests);
   P.h_y = std::min(J, kMaxPrivDests);
@@ -347,11 +374,25 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
       (e = dev_alloc(P, &P.b_r, J)) || (e = dev_alloc(P, &P.orig_of, J)) ||
       (e = dev_alloc(P, &P.new_of, J)) || (e = dev_alloc(P, &P.mu_r, J)) ||
       (e = dev_alloc(P, &P.y, J)) ||
-      (e = dev_alloc(P, &P.part, (size_t)P.grid)) ||
+      (e = dev_alloc(P, &P.part, (size_t)P.grid + P.nhub)) ||
       (e = dev_alloc(P, &P.epi_part, (size_t)P.epi_blocks)) ||
       (e = dev_alloc(P, &P.eval_dev, 8)) || (e = dev_alloc(P, &P.lam_stage, J)) ||
       (e = dev_alloc(P, &P.grad_stage, J)) || (e = dev_alloc(P, &P.status, 1)))
     return bail(cuda_fail(e, "allocating problem memory"));
+  if (P.nhub > 0) {
+    if ((e = dev_alloc(P, &P.hubs, hubs.size())) ||
+        (e = dev_alloc(P, &P.chunk_hub, chunk_hub.size())) ||
+        (e = dev_alloc(P, &P.hub_stat, chunk_hub.size() * (kHubThreads / 32))) ||
+        (e = dev_alloc(P, &P.hub_cand, (size_t)hub_edges)) ||
+        (e = dev_alloc(P, &P.hub_cnt, 2 * hubs.size())))
+      return bail(cuda_fail(e, "allocating hub-source memory"));
+    if ((e = cudaMemcpyAsync(P.hubs, hubs.data(), hubs.size() * sizeof(HubDesc),
+                             cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(P.chunk_hub, chunk_hub.data(), chunk_hub.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemsetAsync(P.hub_cnt, 0, 2 * hubs.size() * sizeof(unsigned), s)))
+      return bail(cuda_fail(e, "uploading hub sources"));
+  }
   if (P.storage == DUALIP_EDGE_F32) {
     if ((e = dev_alloc(P, &P.ca2, e_pad))) return bail(cuda_fail(e, "allocating edge memory"));
   } else {

@@ -75,6 +75,15 @@ constexpr int kCandRounds = 16;  // Michelot rounds before the multi-pass path t
 constexpr bool kBlockClass = DUALIP_BLOCK_CLASS != 0;
 constexpr int kBlockUnroll = 4;  // edges in flight per consumer thread in the block class
 constexpr int kBlockCand = 4;    // candidate edges a consumer thread keeps in registers
+// Sources of at least DUALIP_MB_STAGES stages' edges are projected by the
+// multi-block class (the hub kernel, over the whole grid, before the pass,
+// which skips them); 0 leaves them to the block class.
+#ifndef DUALIP_MB_STAGES
+#define DUALIP_MB_STAGES 16
+#endif
+constexpr int kMultiBlockStages = DUALIP_MB_STAGES;
+constexpr int kHubChunk = 4096;    // edges of a hub source per chunk (one CTA, one read)
+constexpr int kHubThreads = 512;   // threads of a hub-kernel CTA
 // Problems with at most 16 edges per source on average take the pass variant
 // with 32-source batches and one-lane groups (1), or the standard one (0).
 #ifndef DUALIP_TINY_BATCHES
@@ -101,6 +110,20 @@ struct alignas(128) DeviceStatus {
   int pad;
   // the dynamic schedule's counter takes every CTA's atomics: a line of its own
   alignas(128) unsigned long long tile_next;
+};
+
+// A source of the multi-block class: its stored edges [e0, e0 + deg), its
+// chunks [c0, c0 + nch) of kHubChunk edges, its candidate list at cand0.
+struct HubDesc {
+  int64_t e0;
+  int64_t cand0;
+  int32_t deg, c0, nch, pad;
+};
+// Statistics of one warp's unit of a hub-source chunk: the saturation sum
+// sum_{r > 0} alpha r, r_max and max (r - gamma w).
+struct alignas(16) HubUnitStat {
+  double s0;
+  float rmax, mb;
 };
 
 // Kernel parameters of the J-length epilogue.
@@ -207,6 +230,7 @@ struct PassParams {
   long long* slot_part;   // per-slot fixed-point (sum c x, sum w x^2) (slot scales)
   int lean80;  // 4-lane lean groups may take spans up to 80 (else 64)
   int grab;    // tiles per grab of the single-problem schedule (1..31)
+  int64_t mb_min;  // a tile of at least this many edges is a hub source (skipped)
 };
 
 struct Problem {
@@ -217,6 +241,15 @@ struct Problem {
   int box = 0;  // projection onto the unit box [0, 1]^E instead of per-source simplices
   int tiny = 0;  // small mean degree: the pass claims 32 sources at a time (1-lane groups)
   int has_big = 0;  // some source is larger than a stage: tiles are grabbed one at a time
+  // multi-block class: sources of at least mb_min edges (INT64_MAX: none)
+  int64_t mb_min = INT64_MAX;
+  int nhub = 0;
+  int64_t nchunks = 0;
+  HubDesc* hubs = nullptr;           // [nhub]
+  int32_t* chunk_hub = nullptr;      // [nchunks] hub of each chunk
+  HubUnitStat* hub_stat = nullptr;   // [nchunks * units per chunk]
+  float4* hub_cand = nullptr;        // [sum of hub degrees] candidate lists
+  unsigned* hub_cnt = nullptr;       // [2 nhub] candidates so far, chunks done
   // constraint families (Definition 1): with m > 1, J counts rows (m Jd, row
   // k Jd + j), the edges keep the caller's order and destination ids, and c,
   // a (family-major, a[k E + e]) live in cm, am; the pass is multi.cu's
@@ -245,7 +278,7 @@ struct Problem {
   // sum_e w_e x_e^2 are bounded by I max|c| and I max w (sum_e x_e <= 1 per
   // source), kept below 2^61
   int exp_c = 0, exp_w = 0;
-  longlong2* part = nullptr;
+  longlong2* part = nullptr;  // [grid + nhub] fixed-point partials of the pass and hubs
   int epi_blocks = 0;
   float4* epi_part = nullptr;
   double* eval_dev = nullptr;

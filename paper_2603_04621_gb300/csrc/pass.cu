@@ -154,6 +154,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Per-thread asynchronous copies global -> shared (4 or 8 bytes, naturally
+// aligned), in commit groups that a thread waits for.
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1105,6 +1120,409 @@ __device__ __forceinline__ void flush_sums(const Sums& acc, long long* dst, int 
   }
 }
 
+// ------------------------------------- multi-block class (hub sources) ----
+// A source of at least mb_min edges is projected by the whole grid before the
+// pass (whose producer skips its tile).  Its edges are cut into chunks of
+// kHubChunk, each CTA takes a contiguous range of chunks, and each warp of it
+// a unit of kHubUnit edges of the chunk.  Reading its unit once, a warp
+//   * finds the unit's r_max, saturation sum s0 = sum_{r > 0} alpha r and
+//     m_u = max (r - gamma w);
+//   * appends the unit's candidates (hi, lo, alpha, k) to the source's list:
+//     the edges with r > m_u less a rounding margin.  With the sum constraint
+//     binding, every active edge has r_e > tau* >= r - gamma w for every edge
+//     of the source (x <= 1 in Eq. 5), so r_e > m_u; where the unit alone
+//     leaves the constraint slack, every r > 0 joins (the whole source may be
+//     slack, and then every edge with r > 0 is active).
+// Warps never wait for one another inside a source.  At the end of its run of
+// a source's chunks a CTA takes a ticket for them; the CTA whose ticket
+// completes the source combines the unit statistics in unit order, runs
+// Michelot's rounds on the candidate list and accounts x for the active edges.
+// The rounds' sums are 64-bit fixed point, exact in any order, so the result
+// does not depend on the order in which the warps appended their candidates.
+// No CTA waits for another.
+constexpr int kHubWarps = kHubThreads / 32;
+constexpr int kHubUnit = kHubChunk / kHubWarps;  // edges of a warp's unit
+constexpr int kHubU = kHubUnit / 32;             // edges per lane
+static_assert(kHubU * 32 * kHubWarps == kHubChunk, "a chunk is one unit per warp");
+
+struct HubParams {
+  const int32_t* dst;
+  const float2* ca2;
+  const uint32_t* ca;
+  const float* mu_r;
+  const float* gamma_dev;
+  float gamma;
+  unsigned long long* y;
+  int ey, ec, ew;
+  float* x_out;
+  const HubDesc* hubs;
+  const int32_t* chunk_hub;
+  int64_t nchunks;
+  HubUnitStat* stat;  // [nchunks * kHubWarps]
+  float4* cand;
+  unsigned* cnt;    // [2 nhub]: candidates appended, chunks completed
+  longlong2* part;  // [nhub] fixed-point objective partials
+  DeviceStatus* status;
+};
+
+// Shared scratch of the solve's fixed-order block reductions.
+struct HubRed {
+  float f[2][kHubWarps];
+  double d[kHubWarps];
+  long long q[3][kHubWarps];
+  int last;
+};
+
+// Scale exponent s with n * m * 2^s < 2^61: n terms of magnitude at most m
+// then sum exactly in a 64-bit integer.
+__device__ __forceinline__ int hub_fixed_exp(unsigned n, float m) {
+  if (n == 0u || !(m > 0.f)) return 0;
+  int ex;
+  frexp((double)n * (double)m, &ex);
+  const int s = 61 - ex;
+  return s > 100 ? 100 : (s < -100 ? -100 : s);
+}
+
+template <bool BF16, bool W, bool WX>
+__device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc hd, const Ctx& cx,
+                                       HubRed& r) {
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const GlobalView<BF16> gv{p.dst, p.ca2, p.ca};
+  // the unit statistics, in unit order
+  float rmax = -CUDART_INF_F, mb = -CUDART_INF_F;
+  double s0 = 0.0;
+  const int nu = hd.nch * kHubWarps;
+  const HubUnitStat* st = p.stat + (int64_t)hd.c0 * kHubWarps;
+  for (int q = tid; q < nu; q += kHubThreads) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(st + q));
+    const long long bits = __double_as_longlong(v.y);
+    rmax = fmaxf(rmax, __int_as_float((int)(bits & 0xffffffffll)));
+    mb = fmaxf(mb, __int_as_float((int)(bits >> 32)));
+    s0 += v.x;
+  }
+  rmax = warp_max(rmax);
+  mb = warp_max(mb);
+  s0 = warp_dsum(s0);
+  if (lane == 0) {
+    r.f[0][w] = rmax;
+    r.f[1][w] = mb;
+    r.d[w] = s0;
+  }
+  __syncthreads();
+  rmax = r.f[0][0];
+  mb = r.f[1][0];
+  s0 = r.d[0];
+  for (int k = 1; k < kHubWarps; ++k) {
+    rmax = fmaxf(rmax, r.f[0][k]);
+    mb = fmaxf(mb, r.f[1][k]);
+    s0 += r.d[k];
+  }
+  __syncthreads();
+  const unsigned N = __ldcg(p.cnt + 2 * h);
+  const float4* L = p.cand + hd.cand0;
+  const int mode = rmax <= 0.f ? 0 : (s0 <= 1.0 ? 1 : 2);
+  float t = 0.f;
+  if (mode == 2) {
+    // as in the block class: shifted scores d = (hi - r_max) + lo, and a lower
+    // bound of the threshold lowered by the FP32 rounding of the scores
+    const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
+    const float lb = W ? __fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack)
+                       : __fsub_rn(-cx.gamma, slack);
+    // magnitudes of the summed terms, for the fixed-point scales
+    float m1 = 0.f, m2 = 0.f;
+    for (unsigned q = tid; q < N; q += kHubThreads) {
+      const float4 v = __ldcg(L + q);
+      const float dk = __fadd_rn(__fsub_rn(v.x, rmax), v.y);
+      if (dk > lb) {
+        m1 = fmaxf(m1, fabsf(W ? __fmul_rn(v.z, dk) : dk));
+        m2 = fmaxf(m2, v.z);
+      }
+    }
+    m1 = warp_max(m1);
+    m2 = warp_max(m2);
+    if (lane == 0) {
+      r.f[0][w] = m1;
+      r.f[1][w] = m2;
+    }
+    __syncthreads();
+    m1 = r.f[0][0];
+    m2 = r.f[1][0];
+    for (int k = 1; k < kHubWarps; ++k) {
+      m1 = fmaxf(m1, r.f[0][k]);
+      m2 = fmaxf(m2, r.f[1][k]);
+    }
+    __syncthreads();
+    const int s1 = hub_fixed_exp(N, m1), s2 = hub_fixed_exp(N, m2);
+    const float sc1 = ldexpf(1.f, s1), sc2 = ldexpf(1.f, s2);
+    float theta = lb;
+    long long nprev = -1;
+    t = lb;
+    for (unsigned it = 0; it <= N; ++it) {
+      long long sa = 0, sb = 0, nn = 0;
+      for (unsigned q = tid; q < N; q += kHubThreads) {
+        const float4 v = __ldcg(L + q);
+        const float dk = __fadd_rn(__fsub_rn(v.x, rmax), v.y);
+        if (dk > theta) {
+          sa += to_fixed(W ? __fmul_rn(v.z, dk) : dk, sc1);
+          if (W) sb += to_fixed(v.z, sc2);
+          ++nn;
+        }
+      }
+      sa = warp_isum64(sa);
+      sb = warp_isum64(sb);
+      nn = warp_isum64(nn);
+      if (lane == 0) {
+        r.q[0][w] = sa;
+        r.q[1][w] = sb;
+        r.q[2][w] = nn;
+      }
+      __syncthreads();
+      sa = sb = nn = 0;
+      for (int k = 0; k < kHubWarps; ++k) {
+        sa += r.q[0][k];
+        sb += r.q[1][k];
+        nn += r.q[2][k];
+      }
+      __syncthreads();
+      if (nn == nprev || nn == 0) break;
+      const double A = ldexp((double)sa, -s1);
+      const double tt = W ? (A - 1.0) / ldexp((double)sb, -s2)
+                          : (A - (double)cx.gamma) / (double)nn;
+      t = (float)tt;
+      nprev = nn;
+      theta = fmaxf(theta, t);
+    }
+  }
+  // x of the candidates (every other edge of the source has x = 0)
+  Sums acc;
+  for (unsigned q = tid; q < N; q += kHubThreads) {
+    const float4 v = __ldcg(L + q);
+    const int64_t e = hd.e0 + __float_as_int(v.w);
+    float x = 0.f;
+    if (mode == 1) {
+      const float rf = __fadd_rn(v.x, v.y);
+      x = rf > 0.f ? __fmul_rn(v.z, rf) : 0.f;
+    } else if (mode == 2) {
+      const float dk = __fadd_rn(__fsub_rn(v.x, rmax), v.y);
+      x = dk > t ? __fmul_rn(v.z, __fsub_rn(dk, t)) : 0.f;
+    }
+    if (x > 0.f) {
+      int j;
+      float c, a;
+      gv.edge(e, j, c, a);
+      acc.account(cx, j, c, a, edge_w<W>(a), x);
+    }
+    if (WX) p.x_out[e] = x;
+  }
+  const long long cs = warp_isum64(acc.cx), ws = warp_isum64(acc.wxx);
+  if (lane == 0) {
+    r.q[0][w] = cs;
+    r.q[1][w] = ws;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    longlong2 tot = make_longlong2(0, 0);
+    for (int k = 0; k < kHubWarps; ++k) {
+      tot.x += r.q[0][k];
+      tot.y += r.q[1][k];
+    }
+    p.part[h] = tot;
+    // rewind the source's counters for the next evaluation
+    p.cnt[2 * h] = 0u;
+    p.cnt[2 * h + 1] = 0u;
+  }
+  __syncthreads();
+}
+
+// Shared staging of the hub kernel: two buffers per warp, each one unit's
+// destinations (4 B) and (c, a) (8 B FP32 pair or 4 B packed BF16).
+template <bool BF16>
+struct HubStage {
+  static constexpr int kCa = BF16 ? 4 : 8;
+  static constexpr int kBuf = kHubUnit * (4 + kCa);
+  static constexpr size_t kBytes = (size_t)2 * kHubWarps * kBuf;
+};
+
+template <bool BF16, bool W, bool WX>
+__global__ void __launch_bounds__(kHubThreads, 2) hub_kernel(HubParams p) {
+  using S = HubStage<BF16>;
+  extern __shared__ __align__(16) unsigned char hub_smem[];
+  __shared__ HubRed r;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  Ctx cx;
+  cx.mu_a = 0u;
+  cx.mu_g = p.mu_r;
+  cx.h_mu = 0;  // no shared caches: mu and A x go through L2
+  cx.y_a = 0u;
+  cx.h_y = 0;
+  cx.y = p.y;
+  cx.sy = ldexpf(1.f, p.ey);
+  cx.sc = ldexpf(1.f, p.ec);
+  cx.sw = ldexpf(1.f, p.ew);
+  cx.one_w = p.ew >= 0 && p.ew <= 62 ? (1ll << p.ew) : 0ll;
+  cx.x_out = WX ? p.x_out : nullptr;
+  cx.dst_g = p.dst;
+  cx.ca2_g = p.ca2;
+  cx.ca_g = p.ca;
+  const GlobalView<BF16> gv{p.dst, p.ca2, p.ca};
+  const int64_t c_begin = (int64_t)blockIdx.x * p.nchunks / gridDim.x;
+  const int64_t c_end = (int64_t)(blockIdx.x + 1) * p.nchunks / gridDim.x;
+  const uint32_t buf0 = smem_u32(hub_smem) + (uint32_t)(w * S::kBuf);
+  constexpr uint32_t kBufStride = (uint32_t)(kHubWarps * S::kBuf);
+  // this warp's unit of chunk c into buffer b (edges only: the problem's arrays
+  // are immutable, so the copies may start before the preceding kernel ends)
+  auto stage = [&](int64_t c, int b) {
+    if (c < c_end) {
+      const HubDesc hd = p.hubs[__ldg(p.chunk_hub + c)];
+      const int k0 = (int)(c - hd.c0) * kHubChunk + w * kHubUnit;
+      const int n = hd.deg - k0 < 0 ? 0 : (hd.deg - k0 < kHubUnit ? hd.deg - k0 : kHubUnit);
+      const uint32_t sb = buf0 + (uint32_t)b * kBufStride;
+      const int64_t eb = hd.e0 + k0;
+#pragma unroll
+      for (int u = 0; u < kHubU; ++u) {
+        const int k = u * 32 + lane;
+        if (k < n) {
+          cp_async4(sb + 4u * k, p.dst + eb + k);
+          if (BF16) {
+            cp_async4(sb + 4u * kHubUnit + 4u * k, p.ca + eb + k);
+          } else {
+            cp_async8(sb + 4u * kHubUnit + 8u * k, p.ca2 + eb + k);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  stage(c_begin, 0);
+  stage(c_begin + 1, 1);
+  pdl_wait();  // mu of this evaluation; A x rewound by the last epilogue
+  pdl_trigger();
+  cx.gamma = p.gamma_dev ? *p.gamma_dev : p.gamma;
+  cx.inv_gamma = __frcp_rn(cx.gamma);
+  unsigned run = 0u;  // chunks of the current source since the last ticket
+  int h = c_begin < c_end ? __ldg(p.chunk_hub + c_begin) : 0;
+  int b = 0;
+  for (int64_t c = c_begin; c < c_end; ++c, b ^= 1) {
+    const HubDesc hd = p.hubs[h];
+    const int k0 = (int)(c - hd.c0) * kHubChunk + w * kHubUnit;  // this warp's unit
+    const int n = hd.deg - k0 < 0 ? 0 : (hd.deg - k0 < kHubUnit ? hd.deg - k0 : kHubUnit);
+    cp_async_wait<1>();  // this unit's copies (the next unit's may be in flight)
+    __syncwarp();
+    const uint32_t sb = buf0 + (uint32_t)b * kBufStride;
+    float hi[kHubU], lo[kHubU], al[kHubU];
+    float rmax = -CUDART_INF_F, mb = -CUDART_INF_F, s0 = 0.f;
+    {
+      int j[kHubU];
+      float mv[kHubU];
+#pragma unroll
+      for (int u = 0; u < kHubU; ++u) {
+        const int k = u * 32 + lane;
+        j[u] = k < n ? lds_s32(sb + 4u * k) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kHubU; ++u) mv[u] = __ldg(p.mu_r + j[u]);  // every gather in flight
+#pragma unroll
+      for (int u = 0; u < kHubU; ++u) {
+        const int k = u * 32 + lane;
+        hi[u] = -CUDART_INF_F;
+        lo[u] = 0.f;
+        al[u] = 0.f;
+        if (k < n) {
+          float cv, av;
+          if (BF16) {
+            const uint32_t q = lds_u32(sb + 4u * kHubUnit + 4u * k);
+            cv = __uint_as_float(q << 16);
+            av = __uint_as_float(q & 0xffff0000u);
+          } else {
+            const float2 q = lds_f32x2(sb + 4u * kHubUnit + 8u * k);
+            cv = q.x;
+            av = q.y;
+          }
+          score(cv, av, mv[u], hi[u], lo[u]);
+          const float wv = edge_w<W>(av);
+          al[u] = edge_alpha<W>(cx, wv);
+          const float rf = __fadd_rn(hi[u], lo[u]);
+          rmax = fmaxf(rmax, rf);
+          if (rf > 0.f) s0 += __fmul_rn(al[u], rf);
+          mb = fmaxf(mb, __fsub_rn(rf, __fmul_rn(cx.gamma, wv)));
+        }
+      }
+    }
+    __syncwarp();  // the buffer is read: refill it with the unit after next
+    stage(c + 2, b);
+    rmax = warp_max(rmax);
+    mb = warp_max(mb);
+    float sh = s0, sl = 0.f;
+    warp_pair_sum(sh, sl);
+    // the unit's saturation sum as it is stored, and whether it alone exceeds 1
+    int slack_unit = 0;
+    double s0d = 0.0;
+    if (lane == 0) {
+      s0d = (double)sh + (double)sl;
+      slack_unit = s0d > 1.0 ? 0 : 1;
+    }
+    slack_unit = __shfl_sync(0xffffffffu, slack_unit, 0);
+    // candidate threshold: m_u less a margin that covers the rounding of the
+    // FP32 scores and of m_u itself (both below 2^-21 (|r_max| + |m_u|))
+    float thr = __fsub_rn(mb, __fmul_rn(__fadd_rn(fabsf(rmax), fabsf(mb)), 0x1p-19f));
+    if (slack_unit) thr = fminf(thr, 0.f);
+    unsigned total = 0u;
+    unsigned bal[kHubU];
+#pragma unroll
+    for (int u = 0; u < kHubU; ++u) {
+      bal[u] = __ballot_sync(0xffffffffu, __fadd_rn(hi[u], lo[u]) > thr);
+      total += __popc(bal[u]);
+    }
+    unsigned base = 0u;
+    if (lane == 0 && total) base = atomicAdd(p.cnt + 2 * h, total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const bool fits = (uint64_t)base + total <= (uint64_t)hd.deg;
+    if (lane == 0 && !fits) atomicOr(&p.status->err, kErrBounds);
+    // candidate u of this lane goes after every candidate of u' < u, then the
+    // lanes below it
+    unsigned pos = base;
+#pragma unroll
+    for (int u = 0; u < kHubU; ++u) {
+      const int k = u * 32 + lane;
+      if ((bal[u] >> lane) & 1u) {
+        const unsigned q = pos + __popc(bal[u] & ((1u << lane) - 1u));
+        if (fits)
+          p.cand[hd.cand0 + q] =
+              make_float4(hi[u], lo[u], W ? al[u] : cx.inv_gamma, __int_as_float(k0 + k));
+      } else if (WX && k < n) {
+        p.x_out[hd.e0 + k0 + k] = 0.f;
+      }
+      pos += __popc(bal[u]);
+    }
+    if (lane == 0) {
+      HubUnitStat su;
+      su.s0 = s0d;
+      su.rmax = rmax;
+      su.mb = mb;
+      p.stat[c * kHubWarps + w] = su;
+    }
+    ++run;
+    // the end of this CTA's run of the source: a ticket for its chunks; the
+    // ticket that completes the source projects it
+    const int hn = c + 1 < c_end ? __ldg(p.chunk_hub + c + 1) : -1;
+    if (hn != h) {
+      __syncthreads();  // every warp's candidates and statistics of the run are written
+      if (tid == 0) {
+        __threadfence();
+        r.last = atomicAdd(p.cnt + 2 * h + 1, run) + run == (unsigned)hd.nch;
+      }
+      __syncthreads();
+      if (r.last) {
+        __threadfence();
+        hub_solve<BF16, W, WX>(p, h, hd, cx, r);
+      }
+      run = 0u;
+      h = hn;
+    }
+  }
+  cp_async_wait<0>();  // no copy outlives the CTA
+}
+
 // ----------------------------------------------------------- the pass ----
 // MU_SMEM: every destination's mu is cached in shared memory (J <= the cache).
 // WRITE_X: the primal x is written for every edge (dualip_get_primal); every
@@ -1235,13 +1653,16 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         atomicOr(&p.status->err, kErrBounds);
         si.s1 = s0;  // skip the tile; results are flagged invalid
       }
-      si.big = done ? 2 : ((!bad && e1 - e0 > L::kTile) ? 1 : 0);
+      // a hub source: the multi-block class has projected it before the pass
+      const bool hub = !done && !bad && e1 - e0 >= p.mb_min;
+      if (hub) si.s1 = s0;
+      si.big = done ? 2 : ((!bad && !hub && e1 - e0 > L::kTile) ? 1 : 0);
       si.slot = slot;
       si.a0 = e0 & ~int64_t(3);
       si.o0 = s0 & ~int64_t(1);
       info[s] = si;
       ++it;
-      if (bad || si.big) {
+      if (bad || hub || si.big) {
         mbar_arrive(&full[s]);
         return;
       }
@@ -1734,6 +2155,12 @@ static cudaError_t set_smem() {
                               (int)Layout<BF16>::kTotal);
 }
 
+template <bool BF16, bool W, bool WX>
+static cudaError_t set_hub_smem() {
+  return cudaFuncSetAttribute(hub_kernel<BF16, W, WX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)HubStage<BF16>::kBytes);
+}
+
 cudaError_t configure_pass_kernels() {
   const cudaError_t es[] = {
       set_smem<false, false, false, false>(), set_smem<false, false, true, false>(),
@@ -1768,6 +2195,12 @@ cudaError_t configure_pass_kernels() {
       set_smem<true, false, true, false, false, false, false, true>(),
       set_smem<true, true, false, false, false, false, false, true>(),
       set_smem<true, true, true, false, false, false, false, true>()};
+  const cudaError_t hs[] = {set_hub_smem<false, false, false>(), set_hub_smem<false, false, true>(),
+                            set_hub_smem<false, true, false>(),  set_hub_smem<false, true, true>(),
+                            set_hub_smem<true, false, false>(),  set_hub_smem<true, false, true>(),
+                            set_hub_smem<true, true, false>(),   set_hub_smem<true, true, true>()};
+  for (cudaError_t e : hs)
+    if (e != cudaSuccess) return e;
   for (cudaError_t e : es)
     if (e != cudaSuccess) return e;
   return cudaSuccess;
@@ -1811,15 +2244,54 @@ static PassParams pass_params(const Problem& P, const float* gamma_dev, float ga
   // a tile holding a source larger than a stage takes a whole CTA for a
   // while: one tile per grab keeps two of them off the same CTA
   p.grab = P.has_big ? 1 : DUALIP_GRAB;
+  p.mb_min = P.nhub > 0 ? P.mb_min : INT64_MAX;
   return p;
 }
 
 static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_out,
                                  cudaStream_t s);
 
+// The multi-block class: every hub source, over the whole grid.
+static cudaError_t launch_hubs(const Problem& P, const float* gamma_dev, float gamma,
+                               float* x_out, cudaStream_t s) {
+  HubParams h;
+  h.dst = P.dst;
+  h.ca2 = P.ca2;
+  h.ca = P.ca;
+  h.mu_r = P.mu_r;
+  h.gamma_dev = gamma_dev;
+  h.gamma = gamma;
+  h.y = P.y;
+  h.ey = P.exp_y;
+  h.ec = P.exp_c;
+  h.ew = P.exp_w;
+  h.x_out = x_out;
+  h.hubs = P.hubs;
+  h.chunk_hub = P.chunk_hub;
+  h.nchunks = P.nchunks;
+  h.stat = P.hub_stat;
+  h.cand = P.hub_cand;
+  h.cnt = P.hub_cnt;
+  h.part = P.part + P.grid;
+  h.status = P.status;
+  const int64_t g64 = P.nchunks < 2 * (int64_t)P.num_sms ? P.nchunks : 2 * (int64_t)P.num_sms;
+  const dim3 grid((unsigned)(g64 > 0 ? g64 : 1)), block(kHubThreads);
+  const bool bf16 = P.storage == DUALIP_EDGE_BF16;
+#define DUALIP_HUB(B, W)                                                                 \
+  (x_out ? launch_pdl(hub_kernel<B, W, true>, grid, block, HubStage<B>::kBytes, s, h)  \
+         : launch_pdl(hub_kernel<B, W, false>, grid, block, HubStage<B>::kBytes, s, h))
+  if (bf16) return P.weighted ? DUALIP_HUB(true, true) : DUALIP_HUB(true, false);
+  return P.weighted ? DUALIP_HUB(false, true) : DUALIP_HUB(false, false);
+#undef DUALIP_HUB
+}
+
 cudaError_t launch_pass(const Problem& P, const float* gamma_dev, float gamma, float* x_out,
                         cudaStream_t s) {
   if (P.m > 1) return launch_pass_multi(P, gamma_dev, gamma, x_out, s);
+  if (P.nhub > 0) {
+    const cudaError_t e = launch_hubs(P, gamma_dev, gamma, x_out, s);
+    if (e != cudaSuccess) return e;
+  }
   return dispatch_pass(P, pass_params(P, gamma_dev, gamma, x_out), x_out != nullptr, s);
 }
 
@@ -1899,6 +2371,7 @@ cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, in
   p.gamma_of = gamma_of;
   p.slot_part = slot_part;
   p.status = status;
+  p.mb_min = INT64_MAX;  // hub sources of a batch stay in the pass
   const bool bf16 = storage == DUALIP_EDGE_BF16;
   const size_t smem = pass_smem_bytes(storage);
   const int g = (int)(ntiles < grid ? ntiles : grid);
@@ -1925,7 +2398,7 @@ cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const
   q.part = P.part;
   q.ec = P.exp_c;
   q.ew = P.exp_w;
-  q.npart = P.grid;
+  q.npart = P.grid + P.nhub;
   q.epi_part = P.epi_part;
   q.gamma_dev = gamma_dev;
   q.gamma = gamma;

@@ -129,16 +129,47 @@ def test_adversarial_degrees(dl):
 
 @pytest.mark.parametrize("weighted", [False, True])
 def test_block_class_hub_sources(dl, weighted):
-    """Sources far larger than a stage (the block class: all consumer warps of
-    a CTA on one source, from global memory) among ordinary ones, up to a
-    million edges, at a slack, a moderate and a tiny gamma."""
-    degs = np.array([1_000_000, 5, 250_000, 40, 3_201, 0, 60_000, 2])
+    """Sources far larger than a stage among ordinary ones, up to a million
+    edges, at a slack, a moderate and a tiny gamma: the block class (all
+    consumer warps of a CTA on one source, from global memory) up to 16
+    stages, the multi-block class (chunks over the whole grid, the last CTA
+    of a source finds its threshold) from there, with chunk-ragged degrees."""
+    degs = np.array([1_000_000, 5, 250_000, 40, 3_201, 0, 60_000, 2, 20_000, 45_000, 51_200,
+                     65_537, 4_801, 4_096])
     inst = synth.from_degrees(degs, 1_100_000, 19, synth.DST_UNIFORM, b_frac=0.3)
     rng = np.random.default_rng(44)
     P = Po = None
     for gamma in (50.0, 1e-2, 1e-5):
         for lam in (np.zeros(inst.J), rng.uniform(0, 1, inst.J)):
             P, Po, _, _ = check_eval(dl, inst, lam, gamma, weighted, P=P, Po=Po)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_hub_sources_bf16_primal_and_repeat(dl, weighted):
+    """Hub sources with BF16 storage against the oracle on the decoded data,
+    the primal x edge by edge, and repeated evaluations bit for bit (the
+    candidate lists fill in whatever order the chunks finish)."""
+    import torch
+
+    degs = np.array([400_000, 3, 90_000, 0, 77, 300_000, 12_345])
+    inst = synth.from_degrees(degs, 500_000, 23, synth.DST_UNIFORM, b_frac=0.3)
+    rng = np.random.default_rng(45)
+    P = Po = None
+    for gamma in (1.0, 3e-3):
+        lam = rng.uniform(0, 1, inst.J)
+        P, Po, _, _ = check_eval(dl, inst, lam, gamma, weighted, storage="bf16", P=P, Po=Po)
+    lam = torch.from_numpy(rng.uniform(0, 1, inst.J).astype(np.float32)).cuda()
+    for gamma in (1.0, 3e-3):
+        g0, e0 = P.dual_grad(lam, gamma)
+        for _ in range(3):
+            g1, e1 = P.dual_grad(lam, gamma)
+            assert torch.equal(g1, g0) and e1 == e0
+        x = P.primal(lam, gamma).cpu().numpy().astype(np.float64)
+        xo = Po.eval(lam.cpu().numpy().astype(np.float64), gamma, want_x=True).x
+        assert np.all(np.abs(x - xo) <= 2e-5 * np.maximum(1.0, np.abs(xo)) + 1e-6)
+        per_src = np.add.reduceat(x, inst.off[:-1][degs > 0])
+        assert per_src.max() <= 1.0 + 1e-5
+    P.close()
 
 
 def test_many_tiny_sources_and_all_hot(dl):
