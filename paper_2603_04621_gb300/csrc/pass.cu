@@ -154,21 +154,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// Per-thread asynchronous copies global -> shared (4 or 8 bytes, naturally
-// aligned), in commit groups that a thread waits for.
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1143,6 +1128,7 @@ __device__ __forceinline__ void flush_sums(const Sums& acc, long long* dst, int 
 constexpr int kHubWarps = kHubThreads / 32;
 constexpr int kHubUnit = kHubChunk / kHubWarps;  // edges of a warp's unit
 constexpr int kHubU = kHubUnit / 32;             // edges per lane
+constexpr int kHubCtasPerSm = 2;                 // resident hub CTAs per SM (registers, staging)
 static_assert(kHubU * 32 * kHubWarps == kHubChunk, "a chunk is one unit per warp");
 
 struct HubParams {
@@ -1334,19 +1320,8 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
   __syncthreads();
 }
 
-// Shared staging of the hub kernel: two buffers per warp, each one unit's
-// destinations (4 B) and (c, a) (8 B FP32 pair or 4 B packed BF16).
-template <bool BF16>
-struct HubStage {
-  static constexpr int kCa = BF16 ? 4 : 8;
-  static constexpr int kBuf = kHubUnit * (4 + kCa);
-  static constexpr size_t kBytes = (size_t)2 * kHubWarps * kBuf;
-};
-
 template <bool BF16, bool W, bool WX>
-__global__ void __launch_bounds__(kHubThreads, 2) hub_kernel(HubParams p) {
-  using S = HubStage<BF16>;
-  extern __shared__ __align__(16) unsigned char hub_smem[];
+__global__ void __launch_bounds__(kHubThreads, kHubCtasPerSm) hub_kernel(HubParams p) {
   __shared__ HubRed r;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   Ctx cx;
@@ -1367,110 +1342,67 @@ __global__ void __launch_bounds__(kHubThreads, 2) hub_kernel(HubParams p) {
   const GlobalView<BF16> gv{p.dst, p.ca2, p.ca};
   const int64_t c_begin = (int64_t)blockIdx.x * p.nchunks / gridDim.x;
   const int64_t c_end = (int64_t)(blockIdx.x + 1) * p.nchunks / gridDim.x;
-  const uint32_t buf0 = smem_u32(hub_smem) + (uint32_t)(w * S::kBuf);
-  constexpr uint32_t kBufStride = (uint32_t)(kHubWarps * S::kBuf);
-  // this warp's unit of chunk c into buffer b (edges only: the problem's arrays
-  // are immutable, so the copies may start before the preceding kernel ends)
-  auto stage = [&](int64_t c, int b) {
-    if (c < c_end) {
-      const HubDesc hd = p.hubs[__ldg(p.chunk_hub + c)];
-      const int k0 = (int)(c - hd.c0) * kHubChunk + w * kHubUnit;
-      const int n = hd.deg - k0 < 0 ? 0 : (hd.deg - k0 < kHubUnit ? hd.deg - k0 : kHubUnit);
-      const uint32_t sb = buf0 + (uint32_t)b * kBufStride;
-      const int64_t eb = hd.e0 + k0;
-#pragma unroll
-      for (int u = 0; u < kHubU; ++u) {
-        const int k = u * 32 + lane;
-        if (k < n) {
-          cp_async4(sb + 4u * k, p.dst + eb + k);
-          if (BF16) {
-            cp_async4(sb + 4u * kHubUnit + 4u * k, p.ca + eb + k);
-          } else {
-            cp_async8(sb + 4u * kHubUnit + 8u * k, p.ca2 + eb + k);
-          }
-        }
-      }
-    }
-    cp_async_commit();
-  };
-  stage(c_begin, 0);
-  stage(c_begin + 1, 1);
   pdl_wait();  // mu of this evaluation; A x rewound by the last epilogue
   pdl_trigger();
   cx.gamma = p.gamma_dev ? *p.gamma_dev : p.gamma;
   cx.inv_gamma = __frcp_rn(cx.gamma);
   unsigned run = 0u;  // chunks of the current source since the last ticket
   int h = c_begin < c_end ? __ldg(p.chunk_hub + c_begin) : 0;
-  int b = 0;
-  for (int64_t c = c_begin; c < c_end; ++c, b ^= 1) {
-    const HubDesc hd = p.hubs[h];
+  HubDesc hd = p.hubs[h];
+  for (int64_t c = c_begin; c < c_end; ++c) {
     const int k0 = (int)(c - hd.c0) * kHubChunk + w * kHubUnit;  // this warp's unit
     const int n = hd.deg - k0 < 0 ? 0 : (hd.deg - k0 < kHubUnit ? hd.deg - k0 : kHubUnit);
-    cp_async_wait<1>();  // this unit's copies (the next unit's may be in flight)
-    __syncwarp();
-    const uint32_t sb = buf0 + (uint32_t)b * kBufStride;
-    float hi[kHubU], lo[kHubU], al[kHubU];
+    const int64_t eb = hd.e0 + k0;
+    // r = -(c + a mu) rounded once (one FMA): the high word of the exact pair
+    // that the candidates carry
+    float rr[kHubU], mv[kHubU];
     float rmax = -CUDART_INF_F, mb = -CUDART_INF_F, s0 = 0.f;
     {
       int j[kHubU];
-      float mv[kHubU];
+      float cv[kHubU], av[kHubU];
 #pragma unroll
-      for (int u = 0; u < kHubU; ++u) {
+      for (int u = 0; u < kHubU; ++u) {  // the loads first
         const int k = u * 32 + lane;
-        j[u] = k < n ? lds_s32(sb + 4u * k) : 0;
+        j[u] = 0;
+        cv[u] = av[u] = 0.f;
+        if (k < n) gv.edge(eb + k, j[u], cv[u], av[u]);
       }
 #pragma unroll
       for (int u = 0; u < kHubU; ++u) mv[u] = __ldg(p.mu_r + j[u]);  // every gather in flight
 #pragma unroll
       for (int u = 0; u < kHubU; ++u) {
-        const int k = u * 32 + lane;
-        hi[u] = -CUDART_INF_F;
-        lo[u] = 0.f;
-        al[u] = 0.f;
-        if (k < n) {
-          float cv, av;
-          if (BF16) {
-            const uint32_t q = lds_u32(sb + 4u * kHubUnit + 4u * k);
-            cv = __uint_as_float(q << 16);
-            av = __uint_as_float(q & 0xffff0000u);
+        const float rv = -__fmaf_rn(av[u], mv[u], cv[u]);
+        const bool in = u * 32 + lane < n;
+        rr[u] = in ? rv : -CUDART_INF_F;
+        if (in) {
+          rmax = fmaxf(rmax, rv);
+          if (W) {
+            // the saturation sum only sorts units into slack and saturated
+            // (the projection is continuous where the two meet), so alpha r
+            // may be rounded loosely here
+            const float gw = __fmul_rn(cx.gamma, edge_w<W>(av[u]));
+            if (rv > 0.f) s0 += __fdividef(rv, gw);
+            mb = fmaxf(mb, __fsub_rn(rv, gw));
           } else {
-            const float2 q = lds_f32x2(sb + 4u * kHubUnit + 8u * k);
-            cv = q.x;
-            av = q.y;
+            s0 += fmaxf(rv, 0.f);
           }
-          score(cv, av, mv[u], hi[u], lo[u]);
-          const float wv = edge_w<W>(av);
-          al[u] = edge_alpha<W>(cx, wv);
-          const float rf = __fadd_rn(hi[u], lo[u]);
-          rmax = fmaxf(rmax, rf);
-          if (rf > 0.f) s0 += __fmul_rn(al[u], rf);
-          mb = fmaxf(mb, __fsub_rn(rf, __fmul_rn(cx.gamma, wv)));
         }
       }
     }
-    __syncwarp();  // the buffer is read: refill it with the unit after next
-    stage(c + 2, b);
     rmax = warp_max(rmax);
-    mb = warp_max(mb);
-    float sh = s0, sl = 0.f;
-    warp_pair_sum(sh, sl);
-    // the unit's saturation sum as it is stored, and whether it alone exceeds 1
-    int slack_unit = 0;
-    double s0d = 0.0;
-    if (lane == 0) {
-      s0d = (double)sh + (double)sl;
-      slack_unit = s0d > 1.0 ? 0 : 1;
-    }
-    slack_unit = __shfl_sync(0xffffffffu, slack_unit, 0);
+    mb = W ? warp_max(mb) : __fsub_rn(rmax, cx.gamma);
+    s0 = warp_sum(s0);
+    if (!W) s0 = __fmul_rn(s0, cx.inv_gamma);
     // candidate threshold: m_u less a margin that covers the rounding of the
-    // FP32 scores and of m_u itself (both below 2^-21 (|r_max| + |m_u|))
+    // FP32 scores and of m_u itself (both below 2^-21 (|r_max| + |m_u|));
+    // every r > 0 joins where the unit alone leaves the constraint slack
     float thr = __fsub_rn(mb, __fmul_rn(__fadd_rn(fabsf(rmax), fabsf(mb)), 0x1p-19f));
-    if (slack_unit) thr = fminf(thr, 0.f);
+    if (!(s0 > 1.f)) thr = fminf(thr, 0.f);
     unsigned total = 0u;
     unsigned bal[kHubU];
 #pragma unroll
     for (int u = 0; u < kHubU; ++u) {
-      bal[u] = __ballot_sync(0xffffffffu, __fadd_rn(hi[u], lo[u]) > thr);
+      bal[u] = __ballot_sync(0xffffffffu, rr[u] > thr);
       total += __popc(bal[u]);
     }
     unsigned base = 0u;
@@ -1479,24 +1411,27 @@ __global__ void __launch_bounds__(kHubThreads, 2) hub_kernel(HubParams p) {
     const bool fits = (uint64_t)base + total <= (uint64_t)hd.deg;
     if (lane == 0 && !fits) atomicOr(&p.status->err, kErrBounds);
     // candidate u of this lane goes after every candidate of u' < u, then the
-    // lanes below it
+    // lanes below it; it carries the exact score pair and alpha
     unsigned pos = base;
 #pragma unroll
     for (int u = 0; u < kHubU; ++u) {
       const int k = u * 32 + lane;
       if ((bal[u] >> lane) & 1u) {
         const unsigned q = pos + __popc(bal[u] & ((1u << lane) - 1u));
-        if (fits)
-          p.cand[hd.cand0 + q] =
-              make_float4(hi[u], lo[u], W ? al[u] : cx.inv_gamma, __int_as_float(k0 + k));
+        int j;
+        float cv, av, hi, lo;
+        gv.edge(eb + k, j, cv, av);
+        score(cv, av, mv[u], hi, lo);
+        const float al = edge_alpha<W>(cx, edge_w<W>(av));
+        if (fits) p.cand[hd.cand0 + q] = make_float4(hi, lo, al, __int_as_float(k0 + k));
       } else if (WX && k < n) {
-        p.x_out[hd.e0 + k0 + k] = 0.f;
+        p.x_out[eb + k] = 0.f;
       }
       pos += __popc(bal[u]);
     }
     if (lane == 0) {
       HubUnitStat su;
-      su.s0 = s0d;
+      su.s0 = (double)s0;
       su.rmax = rmax;
       su.mb = mb;
       p.stat[c * kHubWarps + w] = su;
@@ -1518,9 +1453,9 @@ __global__ void __launch_bounds__(kHubThreads, 2) hub_kernel(HubParams p) {
       }
       run = 0u;
       h = hn;
+      if (hn >= 0) hd = p.hubs[hn];
     }
   }
-  cp_async_wait<0>();  // no copy outlives the CTA
 }
 
 // ----------------------------------------------------------- the pass ----
@@ -2155,12 +2090,6 @@ static cudaError_t set_smem() {
                               (int)Layout<BF16>::kTotal);
 }
 
-template <bool BF16, bool W, bool WX>
-static cudaError_t set_hub_smem() {
-  return cudaFuncSetAttribute(hub_kernel<BF16, W, WX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)HubStage<BF16>::kBytes);
-}
-
 cudaError_t configure_pass_kernels() {
   const cudaError_t es[] = {
       set_smem<false, false, false, false>(), set_smem<false, false, true, false>(),
@@ -2195,12 +2124,6 @@ cudaError_t configure_pass_kernels() {
       set_smem<true, false, true, false, false, false, false, true>(),
       set_smem<true, true, false, false, false, false, false, true>(),
       set_smem<true, true, true, false, false, false, false, true>()};
-  const cudaError_t hs[] = {set_hub_smem<false, false, false>(), set_hub_smem<false, false, true>(),
-                            set_hub_smem<false, true, false>(),  set_hub_smem<false, true, true>(),
-                            set_hub_smem<true, false, false>(),  set_hub_smem<true, false, true>(),
-                            set_hub_smem<true, true, false>(),   set_hub_smem<true, true, true>()};
-  for (cudaError_t e : hs)
-    if (e != cudaSuccess) return e;
   for (cudaError_t e : es)
     if (e != cudaSuccess) return e;
   return cudaSuccess;
@@ -2274,12 +2197,13 @@ static cudaError_t launch_hubs(const Problem& P, const float* gamma_dev, float g
   h.cnt = P.hub_cnt;
   h.part = P.part + P.grid;
   h.status = P.status;
-  const int64_t g64 = P.nchunks < 2 * (int64_t)P.num_sms ? P.nchunks : 2 * (int64_t)P.num_sms;
+  const int64_t slots = (int64_t)kHubCtasPerSm * P.num_sms;  // one wave of resident CTAs
+  const int64_t g64 = P.nchunks < slots ? P.nchunks : slots;
   const dim3 grid((unsigned)(g64 > 0 ? g64 : 1)), block(kHubThreads);
   const bool bf16 = P.storage == DUALIP_EDGE_BF16;
-#define DUALIP_HUB(B, W)                                                                 \
-  (x_out ? launch_pdl(hub_kernel<B, W, true>, grid, block, HubStage<B>::kBytes, s, h)  \
-         : launch_pdl(hub_kernel<B, W, false>, grid, block, HubStage<B>::kBytes, s, h))
+#define DUALIP_HUB(B, W) \
+  (x_out ? launch_pdl(hub_kernel<B, W, true>, grid, block, 0, s, h) \
+         : launch_pdl(hub_kernel<B, W, false>, grid, block, 0, s, h))
   if (bf16) return P.weighted ? DUALIP_HUB(true, true) : DUALIP_HUB(true, false);
   return P.weighted ? DUALIP_HUB(false, true) : DUALIP_HUB(false, false);
 #undef DUALIP_HUB
