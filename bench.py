@@ -182,9 +182,9 @@ def pass_traffic(E, J, name, storage, tile_shape=None):
 
 def algorithmic_bytes(inst, storage="f32"):
     # what one pass must move: 12 B/edge (dst, c, a; 8 B with (c, a) in BF16),
-    # 8 B per source offset, and per destination: mu read, the A x
-    # accumulator written and read
-    return edge_bytes(storage) * inst.E + 8 * (inst.I + 1) + 12 * inst.J
+    # a 4 B source offset (the pass streams their low 32 bits), and per
+    # destination: mu read, the A x accumulator written and read
+    return edge_bytes(storage) * inst.E + 4 * (inst.I + 1) + 12 * inst.J
 
 
 class ClockSampler:

@@ -397,7 +397,7 @@ dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* 
  * alone: its gradients are exact whatever shares the launch, and its step,
  * momentum and stopping test use its own quantities only.
  *
- * Footprint estimate (bytes): E (4 + bytes(c, a)) + 8 (I + 4) + 16 tiles
+ * Footprint estimate (bytes): E (4 + bytes(c, a)) + 12 (I + 4) + 16 tiles
  * + 56 J, plus 12 E while host inputs are staged at creation.  A request
  * stored in degree order (see dualip_create) also holds 16 (I + 1) bytes of
  * source map during its creation; the estimate leaves that out.

@@ -369,7 +369,10 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   std::vector<int64_t> off_pad(i_pad, E);
   std::copy(off_s.begin(), off_s.end(), off_pad.begin());
 
-  if ((e = dev_alloc(P, &P.off, i_pad)) || (e = dev_alloc(P, &P.dst, e_pad)) ||
+  std::vector<uint32_t> off32_pad(i_pad);
+  for (size_t i = 0; i < i_pad; ++i) off32_pad[i] = (uint32_t)off_pad[i];
+  if ((e = dev_alloc(P, &P.off, i_pad)) || (e = dev_alloc(P, &P.off32, i_pad)) ||
+      (e = dev_alloc(P, &P.dst, e_pad)) ||
       (e = dev_alloc(P, &P.tiles, tiles.size())) || (e = dev_alloc(P, &P.tile_e, tiles.size())) ||
       (e = dev_alloc(P, &P.b_r, J)) || (e = dev_alloc(P, &P.orig_of, J)) ||
       (e = dev_alloc(P, &P.new_of, J)) || (e = dev_alloc(P, &P.mu_r, J)) ||
@@ -410,6 +413,7 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   if (P.ca && (e = cudaMemsetAsync(P.ca, 0, e_pad * 4, s)))
     return bail(cuda_fail(e, "clearing edge memory"));
   if ((e = cudaMemcpyAsync(P.off, off_pad.data(), i_pad * 8, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(P.off32, off32_pad.data(), i_pad * 4, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(P.tiles, tiles.data(), tiles.size() * 8, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(P.tile_e, tile_e.data(), tile_e.size() * 8, cudaMemcpyHostToDevice, s)))
     return bail(cuda_fail(e, "uploading offsets"));

@@ -578,7 +578,7 @@ cudaError_t batch_alloc(Batch& B, int capacity, int storage, int weighted, int n
 
 SlotDesc slot_desc(Problem& P, int64_t joff) {
   SlotDesc d{};
-  d.off = P.off;
+  d.off = P.off32;
   d.dst = P.dst;
   d.ca2 = P.ca2;
   d.ca = P.ca;

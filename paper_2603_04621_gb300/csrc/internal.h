@@ -95,7 +95,7 @@ constexpr int kMaxCachedDests = 10240; // hot destinations whose mu lives in sme
 constexpr int kMaxPrivDests = DUALIP_PRIV_DESTS;  // hot destinations accumulated in smem
 constexpr int kStageSlack = 8;                      // 16-byte alignment slack of a stage
 constexpr int kDstPad = 512;                         // widest group window (32 lanes x 16)
-constexpr int kStageOffSlots = kTileSources + 4;
+constexpr int kStageOffSlots = kTileSources + 8;  // a tile's offsets, from a 16-byte boundary
 
 // device error word bits
 constexpr int kErrTimeout = 1;
@@ -169,7 +169,7 @@ struct RowChunk {
 // Per-slot arrays and scalars (device table).
 struct SlotDesc {
   // the problem's own device arrays
-  const int64_t* off;
+  const uint32_t* off;        // low 32 bits of the stored source offsets
   const int32_t* dst;
   const float2* ca2;
   const uint32_t* ca;
@@ -198,7 +198,9 @@ struct SlotSolve {
 // Kernel parameters of one pass (one dual evaluation).
 struct PassParams {
   // edges
-  const int64_t* off;     // [I+1 (+ padding)]
+  // low 32 bits of the stored source offsets [I+1 (+ padding)]: a tile spans
+  // fewer than 2^32 edges, so differences within it are exact modulo 2^32
+  const uint32_t* off;
   const int32_t* dst;     // [E_pad] renumbered destinations
   const float2* ca2;      // [E_pad] (c, a) pairs (f32 storage)
   const uint32_t* ca;     // [E_pad] packed bf16 (c | a << 16) (bf16 storage)
@@ -262,7 +264,8 @@ struct Problem {
   int num_sms = 0, grid = 0;
   int device = 0;
   // device buffers (owned)
-  int64_t* off = nullptr;
+  int64_t* off = nullptr;     // stored source offsets (create, the primal's source map)
+  uint32_t* off32 = nullptr;  // their low 32 bits, padded (the pass streams these)
   int32_t* dst = nullptr;
   float2* ca2 = nullptr;  // (c, a) pairs, FP32 storage
   uint32_t* ca = nullptr;

@@ -72,11 +72,6 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
   return v;
 }
-__device__ __forceinline__ int64_t lds_s64(uint32_t a) {
-  int64_t v;
-  asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(a));
-  return v;
-}
 __device__ __forceinline__ float2 lds_f32x2(uint32_t a) {
   float2 v;
   asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
@@ -223,14 +218,14 @@ struct alignas(16) StageInfo {
   int64_t s0, s1;  // sources [s0, s1)
   int64_t e0, e1;  // edges [e0, e1)
   int64_t a0;      // first staged edge (multiple of 4)
-  int64_t o0;      // first staged offset (even)
+  int64_t o0;      // first staged offset (a multiple of 4)
   int32_t big;     // single source larger than a stage: read from global
   int32_t slot;    // batched pass: the slot whose problem the tile belongs to
 };
 
 template <bool BF16>
 struct Layout {
-  static constexpr size_t kOffBytes = sizeof(int64_t) * kStageOffSlots;
+  static constexpr size_t kOffBytes = sizeof(uint32_t) * kStageOffSlots;
   static constexpr int kTile = BF16 ? kTileEdgesBF16 : kTileEdges;  // edges of a tile
   static constexpr int kSlots = kTile + kStageSlack;
   static constexpr size_t kEdgeArr = sizeof(uint32_t) * kSlots;
@@ -260,7 +255,8 @@ struct Layout {
 template <bool BF16>
 struct StageView {
   uint32_t off_a, dst_a, ca_a;
-  __device__ __forceinline__ int64_t off(int k) const { return lds_s64(off_a + 8u * k); }
+  // low 32 bits of a staged source offset (differences within a tile are exact)
+  __device__ __forceinline__ uint32_t off(int k) const { return lds_u32(off_a + 4u * k); }
   __device__ __forceinline__ void edge(int k, int& j, float& cv, float& av) const {
     j = lds_s32(dst_a + 4u * k);
     if (BF16) {
@@ -1553,7 +1549,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
     int64_t it = 0;
     bool stop = false;
     int pslot = -1;  // batched pass: slot of the edge pointers below
-    const int64_t* offp = p.off;
+    const uint32_t* offp = p.off;
     const int32_t* dstp = p.dst;
     const float2* ca2p = p.ca2;
     const uint32_t* cap = p.ca;
@@ -1594,7 +1590,7 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
       si.big = done ? 2 : ((!bad && !hub && e1 - e0 > L::kTile) ? 1 : 0);
       si.slot = slot;
       si.a0 = e0 & ~int64_t(3);
-      si.o0 = s0 & ~int64_t(1);
+      si.o0 = s0 & ~int64_t(3);
       info[s] = si;
       ++it;
       if (bad || hub || si.big) {
@@ -1602,12 +1598,12 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
         return;
       }
       const int64_t a1 = (e1 + 3) & ~int64_t(3);
-      const int64_t o1 = (s1 + 2) & ~int64_t(1);
+      const int64_t o1 = (s1 + 4) & ~int64_t(3);
       const uint32_t ne = (uint32_t)(a1 - si.a0), no = (uint32_t)(o1 - si.o0);
-      const uint32_t bytes = no * 8u + ne * (BF16 ? 8u : 12u);
+      const uint32_t bytes = no * 4u + ne * (BF16 ? 8u : 12u);
       mbar_arrive_expect_tx(&full[s], bytes);
       unsigned char* base = smem + (size_t)s * L::kStageBytes;
-      bulk_g2s(base, offp + si.o0, no * 8u, &full[s]);
+      bulk_g2s(base, offp + si.o0, no * 4u, &full[s]);
       if (ne) {
         bulk_g2s(base + L::kOffBytes, dstp + si.a0, ne * 4u, &full[s]);
         if (BF16) {
@@ -1789,7 +1785,8 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
             if (bi >= nb) break;
             const int li = li0 + 8 * (int)bi;
             const int n8 = nsrc - 8 * (int)bi < 8 ? nsrc - 8 * (int)bi : 8;
-            const int e_lo = (int)(sv.off(li) - si.a0), e_hi = (int)(sv.off(li + n8) - si.a0);
+            const uint32_t a0 = (uint32_t)si.a0;
+            const int e_lo = (int)(sv.off(li) - a0), e_hi = (int)(sv.off(li + n8) - a0);
             project_box<BF16, W, WRITE_X>(sv, e_lo, e_hi, si.a0 + e_lo, lane, 32, cx, acc);
           }
         }
@@ -1830,11 +1827,11 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
           if (bi >= nb) break;
           const int li = li0 + NB * (int)bi;
           const int n8 = nsrc - NB * (int)bi < NB ? nsrc - NB * (int)bi : NB;
-          const int64_t oq = sv.off(li + (lane <= n8 ? lane : n8));
-          int64_t on = __shfl_down_sync(0xffffffffu, oq, 1);
+          const uint32_t oq = sv.off(li + (lane <= n8 ? lane : n8));
+          uint32_t on = __shfl_down_sync(0xffffffffu, oq, 1);
           if (TINY && lane == 31) on = sv.off(li + n8);  // the batch's end offset
           const int dq = lane < n8 ? (int)(on - oq) : 0;
-          const int bq = (int)(oq - si.a0);
+          const int bq = (int)(oq - (uint32_t)si.a0);
           const int spq = dq > 0 ? (bq & 3) + dq : 0;
           unsigned needm, needm_tiny = 0u;
           if (WRITE_X) {
@@ -2138,7 +2135,7 @@ cudaError_t launch_prep(const Problem& P, const float* lambda, const float* D, c
 static PassParams pass_params(const Problem& P, const float* gamma_dev, float gamma,
                               float* x_out) {
   PassParams p;
-  p.off = P.off;
+  p.off = P.off32;
   p.dst = P.dst;
   p.ca2 = P.ca2;
   p.ca = P.ca;

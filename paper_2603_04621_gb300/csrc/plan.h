@@ -181,11 +181,12 @@ inline std::vector<int> prune_shapes(const int64_t hist[32], int64_t nsrc, int64
 }
 
 // Serving admission.  Resident footprint of a request (bytes): its edges
-// (4 bytes of dst plus the stored c and a), offsets, tiles and J-length
-// arrays; the transient is the staging of host inputs during creation.
+// (4 bytes of dst plus the stored c and a), offsets (8 bytes and their 4-byte
+// low words), tiles and J-length arrays; the transient is the staging of host
+// inputs during creation.
 inline int64_t request_resident_bytes(int64_t I, int64_t E, int64_t J, bool bf16) {
   const int64_t eb = bf16 ? 8 : 12;
-  return eb * (E + 8) + 8 * (I + 4) + 16 * (E / 1024 + I / 256 + 2) + 56 * J;
+  return eb * (E + 8) + 12 * (I + 4) + 16 * (E / 1024 + I / 256 + 2) + 56 * J;
 }
 inline int64_t request_transient_bytes(int64_t E, bool inputs_on_device) {
   return inputs_on_device ? 0 : 12 * E;

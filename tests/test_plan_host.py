@@ -278,9 +278,10 @@ def test_shape_pruning_rule(plan, law):
 def test_request_footprint_estimate(plan):
     I, E, J = 800_000, 32_000_000, 26_000
     tiles = E // 1024 + I // 256 + 2
-    # E (4 + bytes of c and a) + 8 (I + 4) + 16 tiles + 56 J, with 8 edges of padding
-    assert plan.plan_resident(I, E, J, 0) == 12 * (E + 8) + 8 * (I + 4) + 16 * tiles + 56 * J
-    assert plan.plan_resident(I, E, J, 1) == 8 * (E + 8) + 8 * (I + 4) + 16 * tiles + 56 * J
+    # E (4 + bytes of c and a) + 12 (I + 4) (offsets and their low words) + 16 tiles + 56 J,
+    # with 8 edges of padding
+    assert plan.plan_resident(I, E, J, 0) == 12 * (E + 8) + 12 * (I + 4) + 16 * tiles + 56 * J
+    assert plan.plan_resident(I, E, J, 1) == 8 * (E + 8) + 12 * (I + 4) + 16 * tiles + 56 * J
     assert plan.plan_transient(E, 0) == 12 * E and plan.plan_transient(E, 1) == 0
 
 
