@@ -673,7 +673,7 @@ def run_serve(args):
     return 0
 
 
-def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0):
+def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0, solves=True):
     """The paper's two ablations on its own generator (Appendix B), at 1/25 of
     the Section 7 size (10k resources, 10 edges per request):
     * Jacobi row normalisation (Section 5.1) on and off, at a fixed gamma of
@@ -703,7 +703,7 @@ def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0):
         "row_normalize_off": dict(row_normalize=0, **fixed),
         "continuation_0.16_to_0.01": dict(gamma0=0.16, gamma_final=0.01, halve_every=25,
                                           max_iters=3000),
-    }
+    } if solves else {}
     res, traces = {}, {}
     for name, o in runs.items():
         P.solve(max_iters=20, **{kk: v for kk, v in o.items() if kk != "max_iters"})  # warm
@@ -719,14 +719,15 @@ def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0):
     # distance of g to the best value any run reached there, at a few iteration
     # counts (the paper's Fig. 4 plots this log-gap for the row normalisation)
     at_final = {n: tr[:, 1][tr[:, 0] == 0.01] for n, tr in traces.items()}
-    g_star = max(float(np.max(g)) for g in at_final.values() if len(g))
+    g_star = max((float(np.max(g)) for g in at_final.values() if len(g)), default=0.0)
     for name, tr in traces.items():
         g = tr[:, 1]
         res[name]["log10_gap_to_best"] = {
             str(it): float(np.log10(max(g_star - g[min(it, len(g)) - 1], 1e-300)))
             for it in (10, 25, 50, 100, 200, 500, 1000, 3000)
             if tr[min(it, len(g)) - 1, 0] == 0.01}
-    res["fixed_gamma_0.01"] = res["row_normalize_on"]
+    if solves:
+        res["fixed_gamma_0.01"] = res["row_normalize_on"]
     P.close()
     rown = np.sqrt(np.bincount(inst.dst, weights=inst.a.astype(np.float64) ** 2,
                                minlength=inst.J))
@@ -797,7 +798,8 @@ def run_appb(args):
     import paper_2603_04621_gb300 as d
 
     peak, note = load_peak()
-    f = appb_ablations(d, torch, peak, note, I=max(1, int(1_000_000 * args.scale)))
+    f = appb_ablations(d, torch, peak, note, I=max(1, int(1_000_000 * args.scale)),
+                       solves=not args.no_solve)
     ms = f["pass"]["kernel_ms"]
     out = {"metric": METRIC, "value": f["pass"]["edges_per_s"], "unit": UNIT, "n_gpus": 1,
            "steps": 50, "warmup": 5, "ms_per_step": ms, "higher_is_better": True,

@@ -1856,8 +1856,16 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
             const unsigned m512 = __ballot_sync(0xffffffffu, spq > 256 && spq <= 512);
             needm = __ballot_sync(0xffffffffu, spq > 512);
             if (m4) {
+              // batched problems are stored in degree order, so a batch's
+              // spans are alike: their 4-lane window is sized to the batch's
+              // largest span (32, 48, 64 or 80 slots)
+              const int mx4 = BATCH ? __reduce_max_sync(0xffffffffu, in4 ? spq : 0) : 64;
               if (p.lean80 && __any_sync(0xffffffffu, in4 && spq > 64))
                 needm |= lean_over<4, 5, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
+              else if (BATCH && mx4 <= 32)
+                needm |= lean_over<4, 2, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
+              else if (BATCH && mx4 <= 48)
+                needm |= lean_over<4, 3, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
               else
                 needm |= lean_over<4, 4, BF16, W, MU_SMEM, BATCH>(sv, m4, bq, dq, lane, cx, acc);
             }
