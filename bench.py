@@ -742,6 +742,48 @@ def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0, solves=
             "solves": res}
 
 
+def variant_forms(d, torch, peak, note, steps=20, warmup=3):
+    """The pass of two variants on the c2 graph, against its plain FP32 pass:
+    the unit-box projection (Section 6's clamp map: every edge in [0, 1], no
+    sum constraint) and two constraint families (Definition 1, m = 2; one
+    warp per source, m duals gathered and m rows scattered per edge)."""
+    import synth
+
+    base = synth.config("c2")
+    out = {}
+    for name, inst, kw in (("unit_box_c2", base, dict(projection="box")),
+                           ("two_families_c2", synth.add_families(base, 2), {})):
+        m = 1 if inst.a.ndim == 1 else inst.a.shape[0]
+        P = d.Problem.from_instance(inst, **kw)
+        lam = torch.from_numpy(np.random.default_rng(LAM_SEED).uniform(
+            0.0, 1.0, m * inst.J).astype(np.float32)).cuda()
+        grad = torch.empty(m * inst.J, dtype=torch.float32, device="cuda")
+        out_dev = torch.empty(8, dtype=torch.float64, device="cuda")
+        sp = int(torch.cuda.current_stream().cuda_stream)
+
+        def step():
+            d.dualip_dual_grad_async(P.h, lam.data_ptr(), GAMMA, grad.data_ptr(),
+                                     out_dev.data_ptr(), sp)
+
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for _ in range(warmup):
+                step()
+            k = profiled(d, P.h, steps, step)
+        d.dualip_check_device_status(P.h, sp)
+        P.close()
+        # per edge: dst, c and m coefficients; per source: the offset (the
+        # families pass reads 8-byte offsets); per row: mu, A x written and read
+        alg = (edge_bytes("f32") * inst.E + 4 * (inst.I + 1) + 12 * inst.J if m == 1 else
+               (8 + 4 * m) * inst.E + 8 * (inst.I + 1) + 12 * m * inst.J)
+        out[name] = {"m": m, "E": inst.E, "rows": m * inst.J, "gamma": GAMMA,
+                     "pass_ms": k["pass"], "edges_per_s": inst.E / (k["pass"] / 1e3),
+                     "roofline": roofline(alg, k["pass"], peak, note, None,
+                                          "multi_pass_kernel" if m > 1 else
+                                          "dualgrad_pass_kernel (unit box)"),
+                     "clocks": clk.summary()}
+    return out
+
+
 def hub_form(d, torch, peak, note, steps=20, warmup=3):
     """Sources far larger than a stage: c2 plus 100 sources of 100k-1M edges
     (log-uniform) over 1M destinations, against the c2 sources alone in the
@@ -784,6 +826,7 @@ def forms(d, torch, args, plain, peak, note):
     out["serving_c5"] = serve_form(d, torch, args.form_requests, args.budget_gib)
     out["appendix_b_ablations"] = appb_ablations(d, torch, peak, note)
     out["hubs_c2"] = hub_form(d, torch, peak, note)
+    out.update(variant_forms(d, torch, peak, note))
     return out
 
 
