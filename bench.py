@@ -54,10 +54,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "appb"],
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "c3", "c4", "c5", "appb", "hubs"],
                     help="c2: 1M x 10k, ~50M edges (default); c3: 25M x 1M, ~2.0B edges; "
                          "c4: 256 problems in one batched pass, ~3.4B edges; "
-                         "c5: a Poisson stream of solve requests through the server")
+                         "c5: a Poisson stream of solve requests through the server; "
+                         "appb: the Appendix B generator; hubs: c2 plus 100 hub sources")
     ap.add_argument("--requests", type=int, default=60,
                     help="c5: the first N requests of the seeded trace")
     ap.add_argument("--budget-gib", type=float, default=160.0, help="c5: HBM budget")
@@ -145,16 +147,18 @@ def config_dict(inst, name, scale, storage):
 # written and read: 12 B each) do not grow with the sources; the rest is scaled
 # by the edges processed.  It is reported only while the kernel's code (the
 # source without comments and blank lines) is unchanged and, for the batched
-# pass, while the autotuner picks the tile shape it was taken at.  A capture
-# holds only for the storage layout it ran on: the batched recipe's problems
-# are now stored in degree order, so its capture (on the caller's order) is
-# not listed.
-PASS_CODE_SHA256 = "3ea3d6867baf3da372a60475a050b477fa958945f6a2371c48f8d345ea8c9d8e"
+# pass, while the autotuner picks the tile shape it was taken at.
+PASS_CODE_SHA256 = "6abe8f9aca739d72e8eed8cc3638d2d9db4daa9ed178b3e716084ac918164663"
 PASS_TRAFFIC = {
     # c2 recipe at 0.3 of the sources, FP32
-    ("c2", "f32"): {"bytes": 182_655_488 + 3_568_128, "edges": 14_995_720, "J": 10_000},
+    ("c2", "f32"): {"bytes": 181_433_856 + 3_639_040, "edges": 14_995_720, "J": 10_000},
     # c3 recipe at 0.01 of the sources, BF16 (c, a)
-    ("c3", "bf16"): {"bytes": 168_000_512 + 4_269_824, "edges": 20_001_134, "J": 1_000_000},
+    ("c3", "bf16"): {"bytes": 167_032_576 + 3_985_408, "edges": 20_001_134, "J": 1_000_000},
+    # c4 recipe at 0.05 of the sources (degree order), FP32, tiles of 3200 x 128
+    ("c4", "f32"): {"bytes": 2_018_495_000 + 11_967_232, "edges": 164_807_481, "J": 1_665_819,
+                    "tile_shape": [3200, 128]},
+    # the Appendix B generator at 2M requests, FP32 (the small-degree variant)
+    ("appb", "f32"): {"bytes": 248_333_568 + 3_109_120, "edges": 20_000_112, "J": 10_000},
 }
 
 
@@ -738,7 +742,8 @@ def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0, solves=
             "row_norm_p1_p50_p99": [float(x) for x in np.percentile(rown[rown > 0],
                                                                     [1, 50, 99])],
             "pass": {"kernel_ms": k["pass"], "edges_per_s": inst.E / (k["pass"] / 1e3),
-                     "roofline": roofline(algorithmic_bytes(inst), k["pass"], peak, note)},
+                     "roofline": roofline(algorithmic_bytes(inst), k["pass"], peak, note,
+                                          pass_traffic(inst.E, inst.J, "appb", "f32"))},
             "solves": res}
 
 
@@ -855,7 +860,35 @@ def run_appb(args):
     return 0
 
 
+def run_hubs(args):
+    """c2 plus 100 sources of 100k-1M edges (the multi-block class) against the
+    c2 sources alone."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2603_04621_gb300 import build
+
+    build.build()
+    import paper_2603_04621_gb300 as d
+
+    peak, note = load_peak()
+    f = hub_form(d, torch, peak, note, steps=args.steps, warmup=args.warmup)
+    h = f["with_hubs"]
+    out = {"metric": METRIC, "value": h["edges_per_s"], "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["pass_ms"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": {"workload": f["workload"], "E": h["E"],
+                                           "hub_edges": f["hub_edges"], "gamma": GAMMA,
+                                           "parallelism": "replicas"},
+           "roofline": h["roofline"], "c2_sources_alone": f["c2_sources_alone"],
+           "edges_per_s_ratio_hubs_vs_alone": f["edges_per_s_ratio_hubs_vs_alone"]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
+    if args.workload == "hubs":
+        return run_hubs(args)
     if args.workload == "c4":
         return run_batch(args)
     if args.workload == "c5":
