@@ -22,6 +22,7 @@ namespace dualip {
 namespace {
 
 constexpr int kMultiThreads = 256;
+constexpr int kMultiRegs = 4;  // edges per lane held in registers (sources of up to 128 edges)
 
 struct MultiParams {
   const int64_t* off;
@@ -89,9 +90,97 @@ __global__ void __launch_bounds__(kMultiThreads) multi_pass_kernel(MultiParams p
   const float sy = ldexpf(1.f, p.ey), sc = ldexpf(1.f, p.ec), sw = ldexpf(1.f, p.ew);
   long long acx = 0, awxx = 0;
   const int64_t nw = (int64_t)gridDim.x * (kMultiThreads / 32);
-  for (int64_t src = (int64_t)blockIdx.x * (kMultiThreads / 32) + warp; src < p.I; src += nw) {
-    const int64_t e0 = __ldg(p.off + src), d = __ldg(p.off + src + 1) - e0;
-    auto alpha = [&](float w) { return __frcp_rn(__fmul_rn(gamma, w)); };
+  auto alpha = [&](float w) { return __frcp_rn(__fmul_rn(gamma, w)); };
+  // x of one edge, its scatter into every family's row and its objective terms
+  auto emit = [&](int64_t e, int j, float w, float x) {
+    if (x > 0.f) {
+      for (int f = 0; f < p.m; ++f) {
+        const float a = __ldg(p.a + (int64_t)f * p.E + e);
+        const long long q = __float2ll_rn(__fmul_rn(__fmul_rn(a, x), sy));
+        if (q) atomicAdd(p.y + (int64_t)f * p.Jd + j, (unsigned long long)q);
+      }
+      acx += __float2ll_rn(__fmul_rn(__fmul_rn(__ldg(p.c + e), x), sc));
+      awxx += __float2ll_rn(__fmul_rn(__fmul_rn(w, __fmul_rn(x, x)), sw));
+    }
+    if (p.x_out) p.x_out[e] = x;
+  };
+  // one source by the whole warp
+  auto warp_source = [&](int64_t e0, int64_t d) {
+    if (d <= 32 * kMultiRegs) {
+      // the source's scores stay in registers (kMultiRegs per lane): one read
+      // of its edges, every gather in flight at once, Michelot's rounds and x
+      // from the registers
+      int jj[kMultiRegs];
+      float hi[kMultiRegs], lo[kMultiRegs], wv[kMultiRegs];
+#pragma unroll
+      for (int u = 0; u < kMultiRegs; ++u) {
+        const int64_t k = lane + 32 * u;
+        jj[u] = k < d ? __ldg(p.dst + e0 + k) : 0;
+      }
+      float rmax = -INFINITY, s0 = 0.f, mb = -INFINITY;
+#pragma unroll
+      for (int u = 0; u < kMultiRegs; ++u) {
+        const int64_t k = lane + 32 * u;
+        hi[u] = -INFINITY;
+        lo[u] = 0.f;
+        wv[u] = 1.f;
+        if (k < d) {
+          m_score(p, e0 + k, jj[u], hi[u], lo[u], wv[u]);
+          const float rf = __fadd_rn(hi[u], lo[u]);
+          rmax = fmaxf(rmax, rf);
+          if (rf > 0.f) s0 += __fmul_rn(alpha(wv[u]), rf);
+          mb = fmaxf(mb, __fsub_rn(rf, __fmul_rn(gamma, wv[u])));
+        }
+      }
+      rmax = m_wmax(rmax);
+      s0 = m_wsum(s0);
+      mb = m_wmax(mb);
+      const int mode = p.box ? 3 : (rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2));
+      float t = 0.f;
+      if (mode == 2) {
+        const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
+        float theta = __fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack), nprev = -1.f;
+        t = theta;
+        for (int64_t it = 0; it <= d; ++it) {
+          float sr = 0.f, sa = 0.f, n = 0.f;
+#pragma unroll
+          for (int u = 0; u < kMultiRegs; ++u) {
+            const float dk = __fadd_rn(__fsub_rn(hi[u], rmax), lo[u]);
+            if (lane + 32 * u < d && dk > theta) {
+              const float al = alpha(wv[u]);
+              sr += __fmul_rn(al, dk);
+              sa += al;
+              n += 1.f;
+            }
+          }
+          sr = m_wsum(sr);
+          sa = m_wsum(sa);
+          n = m_wsum(n);
+          if (n == nprev) break;
+          t = __fdiv_rn(sr - 1.f, sa);
+          nprev = n;
+          theta = fmaxf(theta, t);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kMultiRegs; ++u) {
+        const int64_t k = lane + 32 * u;
+        if (k >= d) continue;
+        const float al = alpha(wv[u]);
+        float x = 0.f;
+        if (mode == 1) {
+          const float rf = __fadd_rn(hi[u], lo[u]);
+          x = rf > 0.f ? __fmul_rn(al, rf) : 0.f;
+        } else if (mode == 2) {
+          const float dk = __fadd_rn(__fsub_rn(hi[u], rmax), lo[u]);
+          x = dk > t ? __fmul_rn(al, __fsub_rn(dk, t)) : 0.f;
+        } else if (mode == 3) {
+          x = fminf(fmaxf(__fmul_rn(al, __fadd_rn(hi[u], lo[u])), 0.f), 1.f);
+        }
+        emit(e0 + k, jj[u], wv[u], x);
+      }
+      return;
+    }
     // pass 1: maximum score, saturation sum, and the bound max(r - gamma w)
     float rmax = -INFINITY, s0 = 0.f, mb = -INFINITY;
     for (int64_t k = lane; k < d; k += 32) {
@@ -152,18 +241,11 @@ __global__ void __launch_bounds__(kMultiThreads) multi_pass_kernel(MultiParams p
       } else if (mode == 3) {  // unit box
         x = fminf(fmaxf(__fmul_rn(al, __fadd_rn(hi, lo)), 0.f), 1.f);
       }
-      if (x > 0.f) {
-        for (int f = 0; f < p.m; ++f) {
-          const float a = __ldg(p.a + (int64_t)f * p.E + e);
-          const long long q = __float2ll_rn(__fmul_rn(__fmul_rn(a, x), sy));
-          if (q) atomicAdd(p.y + (int64_t)f * p.Jd + j, (unsigned long long)q);
-        }
-        acx += __float2ll_rn(__fmul_rn(__fmul_rn(__ldg(p.c + e), x), sc));
-        awxx += __float2ll_rn(__fmul_rn(__fmul_rn(w, __fmul_rn(x, x)), sw));
-      }
-      if (p.x_out) p.x_out[e] = x;
+      emit(e, j, w, x);
     }
-  }
+  };
+  for (int64_t src = (int64_t)blockIdx.x * (kMultiThreads / 32) + warp; src < p.I; src += nw)
+    warp_source(__ldg(p.off + src), __ldg(p.off + src + 1) - __ldg(p.off + src));
   // per-block partials: exact integer sums
   __shared__ longlong2 red[kMultiThreads / 32];
   acx = m_isum(acx);
