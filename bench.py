@@ -708,13 +708,15 @@ def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0, solves=
         "continuation_0.16_to_0.01": dict(gamma0=0.16, gamma_final=0.01, halve_every=25,
                                           max_iters=3000),
     } if solves else {}
-    res, traces = {}, {}
+    res, traces, lam_end = {}, {}, None
     for name, o in runs.items():
         P.solve(max_iters=20, **{kk: v for kk, v in o.items() if kk != "max_iters"})  # warm
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, r, tr = P.solve(trace=True, **o)
+        lam_k, r, tr = P.solve(trace=True, **o)
         torch.cuda.synchronize()
+        if name == "row_normalize_on":
+            lam_end = lam_k
         res[name] = {"seconds": time.perf_counter() - t0, "iters": r["iters"],
                      "converged": r["converged"], "gap_rel": r["gap_rel"],
                      "infeas_rel": r["infeas_rel"], "dual_obj": r["dual_obj"]}
@@ -732,6 +734,15 @@ def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0, solves=
             if tr[min(it, len(g)) - 1, 0] == 0.01}
     if solves:
         res["fixed_gamma_0.01"] = res["row_normalize_on"]
+    # the pass where the ascent is: at the dual point the row-normalised run
+    # ends on (many sources there have near-ties or a slack sum; lambda = 0
+    # gives every source a single candidate)
+    k_end = None
+    if lam_end is not None:
+        lam.copy_(lam_end)
+        for _ in range(3):
+            step()
+        k_end = profiled(d, P.h, 50, step)
     P.close()
     rown = np.sqrt(np.bincount(inst.dst, weights=inst.a.astype(np.float64) ** 2,
                                minlength=inst.J))
@@ -742,8 +753,13 @@ def appb_ablations(d, torch, peak, note, I=1_000_000, J=10_000, nu=10.0, solves=
             "row_norm_p1_p50_p99": [float(x) for x in np.percentile(rown[rown > 0],
                                                                     [1, 50, 99])],
             "pass": {"kernel_ms": k["pass"], "edges_per_s": inst.E / (k["pass"] / 1e3),
+                     "lambda": "0",
                      "roofline": roofline(algorithmic_bytes(inst), k["pass"], peak, note,
                                           pass_traffic(inst.E, inst.J, "appb", "f32"))},
+            "pass_at_ascent_end": None if k_end is None else {
+                "kernel_ms": k_end["pass"], "edges_per_s": inst.E / (k_end["pass"] / 1e3),
+                "lambda": "where the row-normalised ascent ends (3000 iterations, gamma 0.01)",
+                "roofline": roofline(algorithmic_bytes(inst), k_end["pass"], peak, note)},
             "solves": res}
 
 

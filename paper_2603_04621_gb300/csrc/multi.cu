@@ -55,6 +55,11 @@ __device__ __forceinline__ float m_wmax(float v) {
   for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+__device__ __forceinline__ double m_dsum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __device__ __forceinline__ long long m_isum(long long v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -82,7 +87,9 @@ __device__ __forceinline__ void m_score(const MultiParams& p, int64_t e, int j, 
   w = p.weighted ? (ww != 0.f ? ww : 1.f) : 1.f;
 }
 
-__global__ void __launch_bounds__(kMultiThreads) multi_pass_kernel(MultiParams p) {
+// WGT: primal scaling (p.weighted); its instance carries the FP64 rounds.
+template <bool WGT>
+__global__ void __launch_bounds__(kMultiThreads, WGT ? 3 : 4) multi_pass_kernel(MultiParams p) {
   pdl_wait();  // mu (and the reset accumulator) of the kernels before
   pdl_trigger();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -137,7 +144,35 @@ __global__ void __launch_bounds__(kMultiThreads) multi_pass_kernel(MultiParams p
       mb = m_wmax(mb);
       const int mode = p.box ? 3 : (rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2));
       float t = 0.f;
-      if (mode == 2) {
+      double td = 0.0;
+      if (mode == 2 && WGT) {
+        // FP64 d, sums, t and x: widely spread weights cancel in FP32
+        const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
+        double theta = (double)__fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack);
+        float nprev = -1.f;
+        td = theta;
+        for (int64_t it = 0; it <= d; ++it) {
+          double sr = 0.0, sa = 0.0;
+          float n = 0.f;
+#pragma unroll
+          for (int u = 0; u < kMultiRegs; ++u) {
+            const double dd = ((double)hi[u] - (double)rmax) + (double)lo[u];
+            if (lane + 32 * u < d && dd > theta) {
+              const double al = (double)alpha(wv[u]);
+              sr += al * dd;
+              sa += al;
+              n += 1.f;
+            }
+          }
+          sr = m_dsum(sr);
+          sa = m_dsum(sa);
+          n = m_wsum(n);
+          if (n == nprev) break;
+          td = (sr - 1.0) / sa;
+          nprev = n;
+          theta = theta > td ? theta : td;
+        }
+      } else if (mode == 2) {
         const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
         float theta = __fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack), nprev = -1.f;
         t = theta;
@@ -171,6 +206,9 @@ __global__ void __launch_bounds__(kMultiThreads) multi_pass_kernel(MultiParams p
         if (mode == 1) {
           const float rf = __fadd_rn(hi[u], lo[u]);
           x = rf > 0.f ? __fmul_rn(al, rf) : 0.f;
+        } else if (mode == 2 && WGT) {
+          const double dd = ((double)hi[u] - (double)rmax) + (double)lo[u];
+          x = dd > td ? (float)((double)al * (dd - td)) : 0.f;
         } else if (mode == 2) {
           const float dk = __fadd_rn(__fsub_rn(hi[u], rmax), lo[u]);
           x = dk > t ? __fmul_rn(al, __fsub_rn(dk, t)) : 0.f;
@@ -197,7 +235,36 @@ __global__ void __launch_bounds__(kMultiThreads) multi_pass_kernel(MultiParams p
     mb = m_wmax(mb);
     const int mode = p.box ? 3 : (rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2));
     float t = 0.f;
-    if (mode == 2) {  // Michelot's iteration from a set that holds the active set
+    double td = 0.0;
+    if (mode == 2 && WGT) {  // FP64, as in the register path
+      const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
+      double theta = (double)__fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack);
+      float nprev = -1.f;
+      td = theta;
+      for (int64_t it = 0; it <= d; ++it) {
+        double sr = 0.0, sa = 0.0;
+        float n = 0.f;
+        for (int64_t k = lane; k < d; k += 32) {
+          const int64_t e = e0 + k;
+          float hi, lo, w;
+          m_score(p, e, __ldg(p.dst + e), hi, lo, w);
+          const double dd = ((double)hi - (double)rmax) + (double)lo;
+          if (dd > theta) {
+            const double al = (double)alpha(w);
+            sr += al * dd;
+            sa += al;
+            n += 1.f;
+          }
+        }
+        sr = m_dsum(sr);
+        sa = m_dsum(sa);
+        n = m_wsum(n);
+        if (n == nprev) break;
+        td = (sr - 1.0) / sa;
+        nprev = n;
+        theta = theta > td ? theta : td;
+      }
+    } else if (mode == 2) {  // Michelot's iteration from a set that holds the active set
       const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
       float theta = __fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack), nprev = -1.f;
       t = theta;
@@ -235,6 +302,9 @@ __global__ void __launch_bounds__(kMultiThreads) multi_pass_kernel(MultiParams p
       if (mode == 1) {
         const float rf = __fadd_rn(hi, lo);
         x = rf > 0.f ? __fmul_rn(al, rf) : 0.f;
+      } else if (mode == 2 && WGT) {
+        const double dd = ((double)hi - (double)rmax) + (double)lo;
+        x = dd > td ? (float)((double)al * (dd - td)) : 0.f;
       } else if (mode == 2) {
         const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
         x = dk > t ? __fmul_rn(al, __fsub_rn(dk, t)) : 0.f;
@@ -306,7 +376,8 @@ cudaError_t launch_pass_multi(const Problem& P, const float* gamma_dev, float ga
   p.box = P.box;
   p.part = P.part;
   p.x_out = x_out;
-  return launch_pdl(multi_pass_kernel, dim3(P.grid), dim3(kMultiThreads), 0, s, p);
+  return P.weighted ? launch_pdl(multi_pass_kernel<true>, dim3(P.grid), dim3(kMultiThreads), 0, s, p)
+                    : launch_pdl(multi_pass_kernel<false>, dim3(P.grid), dim3(kMultiThreads), 0, s, p);
 }
 
 cudaError_t launch_row_norm_multi(const Problem& P, double* acc, cudaStream_t s) {

@@ -97,6 +97,14 @@ __device__ __forceinline__ float na_wmax(float v) {
   for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+__device__ __forceinline__ double na_dsum(double v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double na_dmax(double v) {
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
 __global__ void na_clear_kernel(NaParams p) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < p.J;
@@ -149,40 +157,45 @@ __global__ void __launch_bounds__(kNaThreads) na_pass_kernel(NaParams p) {
     s0 = na_wsum(s0);
     const int mode = rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2);
     if (mode == 0) continue;
-    float t = 0.f;
+    // shifted scores d, the sums, t and x in FP64: with primal scaling the
+    // weights of one source may spread widely, and x = alpha (d - t) then
+    // cancels in FP32
+    auto shifted = [&](float hi, float lo) { return ((double)hi - (double)rmax) + (double)lo; };
+    double t = 0.0;
     if (mode == 2) {
-      float lb = -CUDART_INF_F;
+      double lb = -CUDART_INF;
       for (int64_t k = lane; k < d; k += 32) {
         int j;
         float c, a, hi, lo;
         load(k, j, c, a, hi, lo);
-        const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
-        lb = fmaxf(lb, __fsub_rn(dk, __fmul_rn(p.gamma, wgt(a))));
+        lb = fmax(lb, shifted(hi, lo) - (double)__fmul_rn(p.gamma, wgt(a)));
       }
-      lb = na_wmax(lb);
-      float theta = lb, nprev = -1.f;
+      lb = na_dmax(lb);
+      double theta = lb;
+      float nprev = -1.f;
       t = lb;
       for (int64_t it = 0; it <= d; ++it) {
-        float sr = 0.f, sa = 0.f, n = 0.f;
+        double sr = 0.0, sa = 0.0;
+        float n = 0.f;
         for (int64_t k = lane; k < d; k += 32) {
           int j;
           float c, a, hi, lo;
           load(k, j, c, a, hi, lo);
-          const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
+          const double dk = shifted(hi, lo);
           if (dk > theta) {
-            const float al = alpha(wgt(a));
-            sr += __fmul_rn(al, dk);
+            const double al = (double)alpha(wgt(a));
+            sr += al * dk;
             sa += al;
             n += 1.f;
           }
         }
-        sr = na_wsum(sr);
-        sa = na_wsum(sa);
+        sr = na_dsum(sr);
+        sa = na_dsum(sa);
         n = na_wsum(n);
         if (n == nprev) break;
-        t = __fdiv_rn(sr - 1.f, sa);
+        t = (sr - 1.0) / sa;
         nprev = n;
-        theta = fmaxf(theta, t);
+        theta = theta > t ? theta : t;
       }
     }
     for (int64_t k = lane; k < d; k += 32) {
@@ -194,8 +207,8 @@ __global__ void __launch_bounds__(kNaThreads) na_pass_kernel(NaParams p) {
       if (mode == 1) {
         x = hi > 0.f ? __fmul_rn(al, __fadd_rn(hi, lo)) : 0.f;
       } else {
-        const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
-        x = dk > t ? __fmul_rn(al, __fsub_rn(dk, t)) : 0.f;
+        const double dk = shifted(hi, lo);
+        x = dk > t ? (float)((double)al * (dk - t)) : 0.f;
       }
       if (x > 0.f) {
         atomicAdd(p.y + j, (double)a * (double)x);

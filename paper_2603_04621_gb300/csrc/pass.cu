@@ -241,12 +241,14 @@ struct Layout {
   // full[kStages], empty[kStages], and two consumer barriers (batched pass)
   static constexpr size_t kInfo = kBars + sizeof(uint64_t) * (2 * kStages + 2);
   static constexpr size_t kMisc = kInfo + sizeof(StageInfo) * kStages;
-  static constexpr size_t kTotal = kMisc + 512;
+  // [kMisc + 512, kMisc + 1024): FP64 block reductions (weighted block class)
+  static constexpr size_t kTotal = kMisc + 1024;
   static_assert(kOffBytes % 16 == 0 && kEdgeArr % 16 == 0 && kDstArr % 16 == 0,
                 "16-byte staging");
   static_assert(kTotal <= 227 * 1024, "shared memory budget");
   static_assert(kMisc % 16 == 0, "float4 reduction slots at kMisc + 16");
   static_assert(16 + 16 * (kThreads / 32) <= 320, "reduction slots end before the claim counters");
+  static_assert(24 * kConsumerWarps <= 512, "FP64 reduction slots");
 };
 
 // Stage layout: offsets | dst (4 B per slot, padded) | c, a (8 B per slot:
@@ -400,6 +402,11 @@ __device__ __forceinline__ void warp_pair_sum(float& h, float& l) {
   }
 }
 __device__ __forceinline__ double pair_value(float h, float l) { return (double)h + (double)l; }
+__device__ __forceinline__ double warp_dmax(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 __device__ __forceinline__ double warp_dsum(double v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -572,6 +579,59 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
       acc.lone(cx, c);
     }
   }
+  if constexpr (G == 1 && !W) {
+    // One lane holds the whole source (at most 16 edges): it projects it
+    // exactly on its own, as the multi-pass path would (exact pair scores
+    // shifted by r_max, Michelot from the bound lb), instead of handing the
+    // source to a whole warp.  (Weighted sources take the multi-pass path,
+    // whose rounds are FP64.)
+    if (gvalid && (mode == 1 || (mode == 2 && !lone))) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int slot = ws + k;
+        float dk = -CUDART_INF_F;
+        if ((unsigned)(slot - base) < (unsigned)d) {
+          int j;
+          float c, a, hi, lo;
+          sv.edge(slot, j, c, a);
+          score(c, a, MU_SMEM ? cx.mu_smem(j) : cx.mu(j), hi, lo);
+          dk = mode == 2 ? __fadd_rn(__fsub_rn(hi, rmax), lo) : __fadd_rn(hi, lo);
+        }
+        rf[k] = dk;
+      }
+      float t = 0.f;
+      if (mode == 2) {
+        float theta = lb, nprev = -1.f;
+        t = lb;
+        for (int it = 0; it <= K; ++it) {
+          float sr = 0.f, n = 0.f;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            if (rf[k] > theta) {
+              sr += rf[k];
+              n += 1.f;
+            }
+          }
+          if (n == nprev) break;
+          t = __fdiv_rn(sr - cx.gamma, n);
+          nprev = n;
+          theta = fmaxf(theta, t);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float x = mode == 2 ? (rf[k] > t ? __fmul_rn(cx.inv_gamma, __fsub_rn(rf[k], t)) : 0.f)
+                                  : (rf[k] > 0.f ? __fmul_rn(cx.inv_gamma, rf[k]) : 0.f);
+        if (x > 0.f) {
+          int j;
+          float c, a;
+          sv.edge(ws + k, j, c, a);
+          acc.account(cx, j, c, a, 1.f, x);
+        }
+      }
+      return false;
+    }
+  }
   return gvalid && (mode == 1 || (mode == 2 && !lone));
 }
 
@@ -640,7 +700,41 @@ __device__ __forceinline__ void project_multipass(const View& v, int64_t base, i
   s0 = g.sum(s0);
   int mode = rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2);
   float t = 0.f;
-  if (mode == 2) {
+  double td = 0.0;
+  if (W && mode == 2) {
+    // Weighted: x = alpha (d - t) cancels when the weights of one source
+    // spread widely (an edge with a large alpha is active with d - t of order
+    // 1 / alpha, far below |t|), so d, the sums, t and x are formed in FP64
+    // from the exact pair; the bound is as below.
+    const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
+    const double lb = (double)__fsub_rn(fminf(__fsub_rn(g.max(mb), rmax), 0.f), slack);
+    double theta = lb;
+    float nprev = -1.f;
+    td = lb;
+    for (int64_t it = 0; it <= d; ++it) {
+      double sr = 0.0, sa = 0.0;
+      float n = 0.f;
+      for (int64_t k = g.rank(); k < d; k += g.size()) {
+        int j;
+        float c, a, hi, lo;
+        load(k, j, c, a, hi, lo);
+        const double dd = ((double)hi - (double)rmax) + (double)lo;
+        if (dd > theta) {
+          const double al = (double)edge_alpha<W>(cx, edge_w<W>(a));
+          sr += al * dd;
+          sa += al;
+          n += 1.f;
+        }
+      }
+      sr = warp_dsum(sr);
+      sa = warp_dsum(sa);
+      n = g.sum(n);
+      if (n == nprev) break;
+      td = (sr - 1.0) / sa;
+      nprev = n;
+      theta = theta > td ? theta : td;
+    }
+  } else if (mode == 2) {
     // a lower bound of max_e (d_e - gamma w_e), lowered by the FP32 rounding of
     // the scores, so that {d_e > lb} contains the active set (unweighted: the
     // top edge has d = 0, so the bound is -gamma)
@@ -682,6 +776,9 @@ __device__ __forceinline__ void project_multipass(const View& v, int64_t base, i
     if (mode == 1) {
       const float rf = __fadd_rn(hi, lo);
       x = rf > 0.f ? __fmul_rn(al, rf) : 0.f;
+    } else if (W && mode == 2) {
+      const double dd = ((double)hi - (double)rmax) + (double)lo;
+      x = dd > td ? (float)((double)al * (dd - td)) : 0.f;
     } else if (mode == 2) {
       const float dk = __fadd_rn(__fsub_rn(hi, rmax), lo);
       x = dk > t ? __fmul_rn(al, __fsub_rn(dk, t)) : 0.f;
@@ -721,6 +818,31 @@ __device__ __forceinline__ float3 block_reduce3(float a, float b, float c, float
   }
   consumer_bar();  // sm is free again
   return make_float3(ra, rb, rc);
+}
+
+// The same in FP64 for two sums and a count (the weighted block class); smd
+// holds 3 doubles per consumer warp.
+__device__ __forceinline__ void block_reduce_d(double& a, double& b, float& c, double* smd, int cw,
+                                               int lane) {
+  a = warp_dsum(a);
+  b = warp_dsum(b);
+  c = warp_sum(c);
+  if (lane == 0) {
+    smd[3 * cw] = a;
+    smd[3 * cw + 1] = b;
+    smd[3 * cw + 2] = (double)c;
+  }
+  consumer_bar();
+  double ra = 0.0, rb = 0.0, rc = 0.0;
+  for (int w = 0; w < kConsumerWarps; ++w) {
+    ra += smd[3 * w];
+    rb += smd[3 * w + 1];
+    rc += smd[3 * w + 2];
+  }
+  consumer_bar();  // smd is free again
+  a = ra;
+  b = rb;
+  c = (float)rc;
 }
 
 // The projection of a source larger than a stage by every consumer thread
@@ -786,6 +908,47 @@ __device__ __forceinline__ void project_block_body(const GlobalView<BF16>& v, in
   s0 = r1.y;
   const int mode = rmax <= 0.f ? 0 : (s0 <= 1.f ? 1 : 2);
   if (mode == 0 && cx.x_out == nullptr) return;  // every x is 0
+  if (W && mode == 2) {
+    // weighted, sum constraint binding: full passes with d, the sums, t and x
+    // in FP64 (see the multi-pass path: widely spread weights cancel in FP32)
+    double* smd = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(sm) + 496);
+    const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
+    const double lb = (double)__fsub_rn(fminf(__fsub_rn(r1.z, rmax), 0.f), slack);
+    double theta = lb, td = lb;
+    float nprev = -1.f;
+    for (int64_t it = 0; it <= d; ++it) {
+      double sr = 0.0, sa = 0.0;
+      float n = 0.f;
+      for (int64_t k = ct; k < d; k += NT) {
+        int j;
+        float c, a, hi, lo;
+        load(k, j, c, a, hi, lo);
+        const double dd = ((double)hi - (double)rmax) + (double)lo;
+        if (dd > theta) {
+          const double al = (double)edge_alpha<W>(cx, edge_w<W>(a));
+          sr += al * dd;
+          sa += al;
+          n += 1.f;
+        }
+      }
+      block_reduce_d(sr, sa, n, smd, cw, lane);
+      if (n == nprev) break;
+      td = (sr - 1.0) / sa;
+      nprev = n;
+      theta = theta > td ? theta : td;
+    }
+    for (int64_t k = ct; k < d; k += NT) {
+      int j;
+      float c, a, hi, lo;
+      load(k, j, c, a, hi, lo);
+      const float w = edge_w<W>(a);
+      const double dd = ((double)hi - (double)rmax) + (double)lo;
+      const float x = dd > td ? (float)((double)edge_alpha<W>(cx, w) * (dd - td)) : 0.f;
+      if (x > 0.f) acc.account(cx, j, c, a, w, x);
+      if (cx.x_out != nullptr) cx.x_out[e_glob + k] = x;
+    }
+    return;
+  }
   float t = 0.f;
   if (mode == 2) {
     const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
@@ -1150,17 +1313,17 @@ struct HubParams {
 // Shared scratch of the solve's fixed-order block reductions.
 struct HubRed {
   float f[2][kHubWarps];
-  double d[kHubWarps];
+  double d[kHubWarps], e[kHubWarps];
   long long q[3][kHubWarps];
   int last;
 };
 
 // Scale exponent s with n * m * 2^s < 2^61: n terms of magnitude at most m
 // then sum exactly in a 64-bit integer.
-__device__ __forceinline__ int hub_fixed_exp(unsigned n, float m) {
-  if (n == 0u || !(m > 0.f)) return 0;
+__device__ __forceinline__ int hub_fixed_exp(unsigned n, double m) {
+  if (n == 0u || !(m > 0.0)) return 0;
   int ex;
-  frexp((double)n * (double)m, &ex);
+  frexp((double)n * m, &ex);
   const int s = 61 - ex;
   return s > 100 ? 100 : (s < -100 ? -100 : s);
 }
@@ -1203,50 +1366,55 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
   const unsigned N = __ldcg(p.cnt + 2 * h);
   const float4* L = p.cand + hd.cand0;
   const int mode = rmax <= 0.f ? 0 : (s0 <= 1.0 ? 1 : 2);
-  float t = 0.f;
+  // Shifted scores d = (hi - r_max) + lo, as in the block class: FP32 for
+  // unweighted sources, FP64 with primal scaling (widely spread weights make
+  // x = alpha (d - t) cancel in FP32; see the multi-pass path).
+  auto shifted = [&](const float4& v) -> double {
+    return W ? ((double)v.x - (double)rmax) + (double)v.y
+             : (double)__fadd_rn(__fsub_rn(v.x, rmax), v.y);
+  };
+  double t = 0.0;
   if (mode == 2) {
-    // as in the block class: shifted scores d = (hi - r_max) + lo, and a lower
-    // bound of the threshold lowered by the FP32 rounding of the scores
+    // a lower bound of the threshold lowered by the FP32 rounding of the scores
     const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
-    const float lb = W ? __fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack)
-                       : __fsub_rn(-cx.gamma, slack);
+    const double lb = W ? (double)__fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack)
+                        : (double)__fsub_rn(-cx.gamma, slack);
     // magnitudes of the summed terms, for the fixed-point scales
-    float m1 = 0.f, m2 = 0.f;
+    double m1 = 0.0, m2 = 0.0;
     for (unsigned q = tid; q < N; q += kHubThreads) {
       const float4 v = __ldcg(L + q);
-      const float dk = __fadd_rn(__fsub_rn(v.x, rmax), v.y);
+      const double dk = shifted(v);
       if (dk > lb) {
-        m1 = fmaxf(m1, fabsf(W ? __fmul_rn(v.z, dk) : dk));
-        m2 = fmaxf(m2, v.z);
+        m1 = fmax(m1, fabs(W ? (double)v.z * dk : dk));
+        m2 = fmax(m2, (double)v.z);
       }
     }
-    m1 = warp_max(m1);
-    m2 = warp_max(m2);
+    m1 = warp_dmax(m1);
+    m2 = warp_dmax(m2);
     if (lane == 0) {
-      r.f[0][w] = m1;
-      r.f[1][w] = m2;
+      r.d[w] = m1;
+      r.e[w] = m2;
     }
     __syncthreads();
-    m1 = r.f[0][0];
-    m2 = r.f[1][0];
+    m1 = r.d[0];
+    m2 = r.e[0];
     for (int k = 1; k < kHubWarps; ++k) {
-      m1 = fmaxf(m1, r.f[0][k]);
-      m2 = fmaxf(m2, r.f[1][k]);
+      m1 = fmax(m1, r.d[k]);
+      m2 = fmax(m2, r.e[k]);
     }
     __syncthreads();
     const int s1 = hub_fixed_exp(N, m1), s2 = hub_fixed_exp(N, m2);
-    const float sc1 = ldexpf(1.f, s1), sc2 = ldexpf(1.f, s2);
-    float theta = lb;
+    double theta = lb;
     long long nprev = -1;
     t = lb;
     for (unsigned it = 0; it <= N; ++it) {
       long long sa = 0, sb = 0, nn = 0;
       for (unsigned q = tid; q < N; q += kHubThreads) {
         const float4 v = __ldcg(L + q);
-        const float dk = __fadd_rn(__fsub_rn(v.x, rmax), v.y);
+        const double dk = shifted(v);
         if (dk > theta) {
-          sa += to_fixed(W ? __fmul_rn(v.z, dk) : dk, sc1);
-          if (W) sb += to_fixed(v.z, sc2);
+          sa += __double2ll_rn(ldexp(W ? (double)v.z * dk : dk, s1));
+          if (W) sb += __double2ll_rn(ldexp((double)v.z, s2));
           ++nn;
         }
       }
@@ -1270,9 +1438,10 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
       const double A = ldexp((double)sa, -s1);
       const double tt = W ? (A - 1.0) / ldexp((double)sb, -s2)
                           : (A - (double)cx.gamma) / (double)nn;
-      t = (float)tt;
+      // unweighted: the threshold in FP32, as the other classes take it
+      t = W ? tt : (double)(float)tt;
       nprev = nn;
-      theta = fmaxf(theta, t);
+      theta = theta > t ? theta : t;
     }
   }
   // x of the candidates (every other edge of the source has x = 0)
@@ -1285,8 +1454,10 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
       const float rf = __fadd_rn(v.x, v.y);
       x = rf > 0.f ? __fmul_rn(v.z, rf) : 0.f;
     } else if (mode == 2) {
-      const float dk = __fadd_rn(__fsub_rn(v.x, rmax), v.y);
-      x = dk > t ? __fmul_rn(v.z, __fsub_rn(dk, t)) : 0.f;
+      const double dk = shifted(v);
+      if (dk > t)
+        x = W ? (float)((double)v.z * (dk - t))
+              : __fmul_rn(v.z, __fsub_rn((float)dk, (float)t));
     }
     if (x > 0.f) {
       int j;

@@ -38,6 +38,17 @@ def test_families_parity(dl, m, weighted):
     assert P.m == m and P.J == m * inst.J
 
 
+def test_families_widely_spread_weights(dl):
+    """Two families with coefficients over four orders of magnitude and primal
+    scaling (w = sum_k a_k^2): the weighted rounds are FP64."""
+    base = synth.greedy_budgets(synth.config("c2", scale=0.005))
+    inst = synth.add_families(base, 2, seed=8, a_range=(0.01, 100.0))
+    rng = np.random.default_rng(48)
+    P = Po = None
+    for gamma in (0.1, 1e-3):
+        P, Po, _, _ = check_eval(dl, inst, rng.uniform(0, 1, 2 * inst.J), gamma, True, P=P, Po=Po)
+
+
 def test_families_edge_cases_box_and_primal(dl):
     import torch
 

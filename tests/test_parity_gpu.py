@@ -172,6 +172,46 @@ def test_hub_sources_bf16_primal_and_repeat(dl, weighted):
     P.close()
 
 
+@pytest.mark.parametrize("storage,weighted", [("f32", False), ("f32", True), ("bf16", False)])
+def test_small_degree_sources_at_solver_points(dl, storage, weighted):
+    """The small-degree variant (mean degree at most 16: one lane per source of
+    span <= 16, which projects a source with near-ties or a slack sum exactly
+    on its own) on the Appendix B generator, at dual points of an actual ascent
+    (where many sources leave the single-candidate exit) and at random ones."""
+    inst = synth.appb(30_000, 400, 8.0)
+    assert inst.E <= 16 * inst.I  # (with primal scaling: weights over eight orders)
+    ref = decoded(inst) if storage == "bf16" else inst
+    Po = oracle.Problem(ref, weighted=weighted)
+    pts = [Po.solve(gamma0=0.01, gamma_final=0.01, halve_every=0, max_iters=n,
+                    stop_on_tol=False)["mu"] for n in (30, 300)]
+    pts.append(np.random.default_rng(46).uniform(0, 2, inst.J))
+    P = None
+    for lam in pts:
+        for gamma in (0.1, 0.01, 1e-3):
+            P, Po, _, _ = check_eval(dl, inst, lam, gamma, weighted, storage, P=P, Po=Po)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_widely_spread_weights_every_class(dl, storage):
+    """Primal scaling with coefficients spread over four orders of magnitude
+    (weights a^2 over eight): an active edge with a large alpha = 1/(gamma w)
+    has x = alpha (d - t) with d - t far below |t|, which the weighted exact
+    paths form in FP64.  Sources for the warp (degrees up to 500), block (a
+    few stages) and multi-block (over 16 stages) classes, at dual points of a
+    short ascent and at random ones."""
+    degs = np.array([3, 40, 300, 5_000, 60_000, 12, 0, 90])
+    inst = synth.greedy_budgets(synth.from_degrees(degs, 70_000, 29, synth.DST_UNIFORM,
+                                                   a_lo=0.01, a_hi=100.0))
+    ref = decoded(inst) if storage == "bf16" else inst
+    Po = oracle.Problem(ref, weighted=True)
+    pts = [Po.solve(gamma0=0.01, gamma_final=0.01, halve_every=0, max_iters=20,
+                    stop_on_tol=False)["mu"], np.random.default_rng(47).uniform(0, 1, inst.J)]
+    P = None
+    for lam in pts:
+        for gamma in (0.1, 1e-3):
+            P, Po, _, _ = check_eval(dl, inst, lam, gamma, True, storage, P=P, Po=Po)
+
+
 def test_many_tiny_sources_and_all_hot(dl):
     # degree-1 sources (tile capped by the source count) into 3 destinations
     inst = synth.from_degrees(np.ones(50_000, dtype=np.int64), 3, 12, synth.DST_UNIFORM,

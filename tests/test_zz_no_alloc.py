@@ -117,6 +117,23 @@ def test_noalloc_matches_oracle_and_handle_path(dl, weighted):
         assert np.any((sums > 0) & (sums < 1 - 1e-9))
 
 
+def test_noalloc_widely_spread_weights(dl):
+    """Primal scaling with coefficients over four orders of magnitude: the
+    allocation-free threshold is formed in FP64 too."""
+    import torch
+
+    degs = np.array([3, 40, 300, 2_000, 12, 0, 90])
+    inst = synth.greedy_budgets(synth.from_degrees(degs, 5_000, 31, synth.DST_UNIFORM,
+                                                   a_lo=0.01, a_hi=100.0))
+    dev = to_dev(inst)
+    Po = oracle.Problem(inst, weighted=True)
+    rng = np.random.default_rng(49)
+    for gamma in (0.1, 1e-3):
+        lam_h = rng.uniform(0, 1, inst.J).astype(np.float32)
+        g, o = noalloc(dl, inst, dev, torch.from_numpy(lam_h).cuda(), gamma, True)
+        check_oracle(inst, g, o, Po.eval(lam_h.astype(np.float64), gamma), lam_h)
+
+
 def test_noalloc_no_sources_and_empty_sources(dl):
     import torch
 
