@@ -586,29 +586,29 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
     // source to a whole warp.  (Weighted sources take the multi-pass path,
     // whose rounds are FP64.)
     if (gvalid && (mode == 1 || (mode == 2 && !lone))) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int slot = ws + k;
-        float dk = -CUDART_INF_F;
-        if ((unsigned)(slot - base) < (unsigned)d) {
-          int j;
-          float c, a, hi, lo;
-          sv.edge(slot, j, c, a);
-          score(c, a, MU_SMEM ? cx.mu_smem(j) : cx.mu(j), hi, lo);
-          dk = mode == 2 ? __fadd_rn(__fsub_rn(hi, rmax), lo) : __fadd_rn(hi, lo);
-        }
-        rf[k] = dk;
+      // rolled loops over a per-lane array (local memory): the path is rare,
+      // and its code must stay small beside the hot loop's
+      float dl[K];
+      const int k0 = base - ws, k1 = k0 + d;
+#pragma unroll 4
+      for (int k = k0; k < k1; ++k) {
+        int j;
+        float c, a, hi, lo;
+        sv.edge(ws + k, j, c, a);
+        score(c, a, MU_SMEM ? cx.mu_smem(j) : cx.mu(j), hi, lo);
+        dl[k] = mode == 2 ? __fadd_rn(__fsub_rn(hi, rmax), lo) : __fadd_rn(hi, lo);
       }
       float t = 0.f;
       if (mode == 2) {
         float theta = lb, nprev = -1.f;
         t = lb;
+#pragma unroll 1
         for (int it = 0; it <= K; ++it) {
           float sr = 0.f, n = 0.f;
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            if (rf[k] > theta) {
-              sr += rf[k];
+#pragma unroll 4
+          for (int k = k0; k < k1; ++k) {
+            if (dl[k] > theta) {
+              sr += dl[k];
               n += 1.f;
             }
           }
@@ -618,10 +618,10 @@ __device__ __forceinline__ bool project_lean(const StageView<BF16>& sv, int base
           theta = fmaxf(theta, t);
         }
       }
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float x = mode == 2 ? (rf[k] > t ? __fmul_rn(cx.inv_gamma, __fsub_rn(rf[k], t)) : 0.f)
-                                  : (rf[k] > 0.f ? __fmul_rn(cx.inv_gamma, rf[k]) : 0.f);
+#pragma unroll 1
+      for (int k = k0; k < k1; ++k) {
+        const float x = mode == 2 ? (dl[k] > t ? __fmul_rn(cx.inv_gamma, __fsub_rn(dl[k], t)) : 0.f)
+                                  : (dl[k] > 0.f ? __fmul_rn(cx.inv_gamma, dl[k]) : 0.f);
         if (x > 0.f) {
           int j;
           float c, a;
