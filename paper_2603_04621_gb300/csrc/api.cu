@@ -335,27 +335,22 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   // there (not for the unit box, whose edges are independent, and not for a
   // source past the hub kernel's 32-bit edge indices).
   const int64_t stage_e = tile_edges_for(P.storage);
-  std::vector<HubDesc> hubs;
+  std::vector<HubPlan> hub_plan;
   std::vector<int32_t> chunk_hub;
+  bool big = false;
+  plan_hubs(tile_e, stage_e, kMultiBlockStages, P.box != 0, kHubChunk, P.mb_min, hub_plan,
+            chunk_hub, big);
+  P.has_big = big ? 1 : 0;
+  std::vector<HubDesc> hubs(hub_plan.size());
   int64_t hub_edges = 0;
-  P.mb_min = kMultiBlockStages > 0 && !P.box ? (int64_t)kMultiBlockStages * stage_e : INT64_MAX;
-  for (int64_t t = 0; t < P.ntiles; ++t)
-    if (tile_e[t + 1] - tile_e[t] >= (int64_t)INT32_MAX - kHubChunk) P.mb_min = INT64_MAX;
-  for (int64_t t = 0; t < P.ntiles; ++t) {
-    const int64_t ne = tile_e[t + 1] - tile_e[t];
-    if (ne >= P.mb_min) {
-      HubDesc hd{};
-      hd.e0 = tile_e[t];
-      hd.cand0 = hub_edges;
-      hd.deg = (int32_t)ne;
-      hd.c0 = (int32_t)chunk_hub.size();
-      hd.nch = (int32_t)((ne + kHubChunk - 1) / kHubChunk);
-      chunk_hub.insert(chunk_hub.end(), (size_t)hd.nch, (int32_t)hubs.size());
-      hubs.push_back(hd);
-      hub_edges += ne;
-    } else if (ne > stage_e) {
-      P.has_big = 1;
-    }
+  for (size_t h = 0; h < hub_plan.size(); ++h) {
+    hubs[h] = HubDesc{};
+    hubs[h].e0 = hub_plan[h].e0;
+    hubs[h].cand0 = hub_plan[h].cand0;
+    hubs[h].deg = hub_plan[h].deg;
+    hubs[h].c0 = hub_plan[h].c0;
+    hubs[h].nch = hub_plan[h].nch;
+    hub_edges += hub_plan[h].deg;
   }
   P.nhub = (int)hubs.size();
   P.nchunks = (int64_t)chunk_hub.size();

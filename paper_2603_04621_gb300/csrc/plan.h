@@ -180,6 +180,47 @@ inline std::vector<int> prune_shapes(const int64_t hist[32], int64_t nsrc, int64
   return keep;
 }
 
+// Segment classes of the sources larger than a stage (stage_e edges): the
+// block class below mb_stages stages, the multi-block class (hub sources)
+// from there.  A hub source is cut into chunks of `chunk` edges; hub h's
+// candidate list starts at cand0 (the hub degrees before it).  The
+// multi-block class is off (mb_min = INT64_MAX, no hubs) when mb_stages is 0,
+// for the unit box, or when a tile reaches 2^31 - chunk edges (the hub
+// kernel's edge indices are 32-bit).  big: some tile is larger than a stage
+// and below mb_min (the block class's pass variant is needed).
+struct HubPlan {
+  int64_t e0, cand0;
+  int32_t deg, c0, nch;
+};
+inline void plan_hubs(const std::vector<int64_t>& tile_e, int64_t stage_e, int mb_stages,
+                      bool box, int64_t chunk, int64_t& mb_min, std::vector<HubPlan>& hubs,
+                      std::vector<int32_t>& chunk_hub, bool& big) {
+  const int64_t nt = (int64_t)tile_e.size() - 1;
+  mb_min = mb_stages > 0 && !box ? (int64_t)mb_stages * stage_e : INT64_MAX;
+  for (int64_t t = 0; t < nt; ++t)
+    if (tile_e[t + 1] - tile_e[t] >= (int64_t)INT32_MAX - chunk) mb_min = INT64_MAX;
+  hubs.clear();
+  chunk_hub.clear();
+  big = false;
+  int64_t cand = 0;
+  for (int64_t t = 0; t < nt; ++t) {
+    const int64_t ne = tile_e[t + 1] - tile_e[t];
+    if (ne >= mb_min) {
+      HubPlan h;
+      h.e0 = tile_e[t];
+      h.cand0 = cand;
+      h.deg = (int32_t)ne;
+      h.c0 = (int32_t)chunk_hub.size();
+      h.nch = (int32_t)((ne + chunk - 1) / chunk);
+      chunk_hub.insert(chunk_hub.end(), (size_t)h.nch, (int32_t)hubs.size());
+      hubs.push_back(h);
+      cand += ne;
+    } else if (ne > stage_e) {
+      big = true;
+    }
+  }
+}
+
 // Serving admission.  Resident footprint of a request (bytes): its edges
 // (4 bytes of dst plus the stored c and a), offsets (8 bytes and their 4-byte
 // low words), tiles and J-length arrays; the transient is the staging of host

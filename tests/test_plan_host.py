@@ -16,6 +16,9 @@ order and the degree order.
   quarter of their edge budget.
 * Serving admission: the footprint estimate of the header, and the head of
   the queue admitted, kept waiting or rejected.
+* Segment classes of large sources: hub sources (at least 16 stages) and
+  their chunk table and candidate-list offsets; the block class's flag; the
+  multi-block class off for the unit box.
 """
 import ctypes
 import os
@@ -65,6 +68,24 @@ int plan_admission(int64_t resident, int64_t footprint, int64_t transient, int64
                    int slot_free) {
   return (int)dualip::admission(resident, footprint, transient, budget, slot_free != 0);
 }
+int64_t plan_hubs_c(const int64_t* tile_e, int64_t nt, int64_t stage_e, int mb_stages, int box,
+                    int64_t chunk, int64_t* mb_min, int64_t* hub_out, int64_t hub_cap,
+                    int32_t* chunk_hub, int64_t chunk_cap, int64_t* nchunks, int* big) {
+  std::vector<int64_t> te(tile_e, tile_e + nt + 1);
+  std::vector<dualip::HubPlan> hubs;
+  std::vector<int32_t> ch;
+  bool b = false;
+  dualip::plan_hubs(te, stage_e, mb_stages, box != 0, chunk, *mb_min, hubs, ch, b);
+  for (size_t h = 0; h < hubs.size() && (int64_t)h < hub_cap; ++h) {
+    hub_out[5 * h] = hubs[h].e0; hub_out[5 * h + 1] = hubs[h].cand0;
+    hub_out[5 * h + 2] = hubs[h].deg; hub_out[5 * h + 3] = hubs[h].c0;
+    hub_out[5 * h + 4] = hubs[h].nch;
+  }
+  for (size_t k = 0; k < ch.size() && (int64_t)k < chunk_cap; ++k) chunk_hub[k] = ch[k];
+  *nchunks = (int64_t)ch.size();
+  *big = b ? 1 : 0;
+  return (int64_t)hubs.size();
+}
 void plan_degree_order(const int64_t* off, int64_t I, int64_t* src_of, int64_t* off_st) {
   std::vector<int64_t> s, os;
   dualip::degree_order(std::vector<int64_t>(off, off + I + 1), s, os);
@@ -112,6 +133,10 @@ def plan(tmp_path_factory):
     L.plan_admission.argtypes = [i64, i64, i64, i64, ctypes.c_int]
     L.plan_admission.restype = ctypes.c_int
     L.plan_degree_order.argtypes = [p64, ctypes.c_int64, p64, p64]
+    vp = ctypes.c_void_p
+    L.plan_hubs_c.argtypes = [vp, i64, i64, ctypes.c_int, ctypes.c_int, i64, vp, vp, i64, vp,
+                              i64, vp, vp]
+    L.plan_hubs_c.restype = i64
     L.plan_degree_order.restype = None
     return L
 
@@ -296,3 +321,38 @@ def test_admission_rule(plan):
     assert a(20, 60, 30, 100, 1) == WAIT        # fits once something leaves
     assert a(10, 60, 30, 100, 0) == WAIT        # fits, but no slot of its kind is free
     assert a(10, 60, 30, 100, 1) == ADMIT       # exactly at the budget
+
+
+def hub_plan(plan, tile_e, stage_e=3200, mb_stages=16, box=0, chunk=4096):
+    te = np.ascontiguousarray(tile_e, dtype=np.int64)
+    mb = np.zeros(1, np.int64)
+    hubs = np.zeros(5 * 64, np.int64)
+    ch = np.zeros(100_000, np.int32)
+    nch = np.zeros(1, np.int64)
+    big = ctypes.c_int(0)
+    n = plan.plan_hubs_c(te.ctypes.data, len(te) - 1, stage_e, mb_stages, box, chunk,
+                         mb.ctypes.data, hubs.ctypes.data, 64, ch.ctypes.data, len(ch),
+                         nch.ctypes.data, ctypes.addressof(big))
+    return int(mb[0]), hubs[: 5 * n].reshape(n, 5), ch[: int(nch[0])], bool(big.value)
+
+
+def test_hub_sources_and_their_chunks(plan):
+    """Sources of at least 16 stages are hub sources (the multi-block class),
+    cut into 4096-edge chunks; those between a stage and 16 stages need the
+    block class; the unit box and mb_stages = 0 turn the multi-block class off."""
+    degs = [100, 3_201, 51_199, 51_200, 4_096 * 20 + 1, 7, 200_000]
+    tile_e = np.concatenate([[0], np.cumsum(degs)])
+    mb, hubs, ch, big = hub_plan(plan, tile_e)
+    assert mb == 16 * 3200 and big  # 3,201 and 51,199 edges: block class
+    assert hubs[:, 2].tolist() == [51_200, 81_921, 200_000]
+    assert hubs[:, 0].tolist() == [tile_e[3], tile_e[4], tile_e[6]]
+    assert hubs[:, 1].tolist() == [0, 51_200, 51_200 + 81_921]  # candidate lists back to back
+    nch = [-(-d // 4096) for d in (51_200, 81_921, 200_000)]
+    assert hubs[:, 4].tolist() == nch and hubs[:, 3].tolist() == [0, nch[0], nch[0] + nch[1]]
+    assert ch.tolist() == [0] * nch[0] + [1] * nch[1] + [2] * nch[2]
+    for kw in (dict(box=1), dict(mb_stages=0)):
+        mb, hubs, ch, big = hub_plan(plan, tile_e, **kw)
+        assert mb == 2**63 - 1 and len(hubs) == 0 and len(ch) == 0 and big
+    mb, hubs, ch, big = hub_plan(plan, [0, 10, 3_000])
+    assert len(hubs) == 0 and not big
+
