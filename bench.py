@@ -248,8 +248,10 @@ class ClockSampler:
                 "samples": len(self.rows), "samples_under_load": len(load)}
 
 
-def cpu_baseline(inst, seconds):
-    """The FP64 oracle as it stands, all host cores, on a bounded source sample."""
+def cpu_baseline(inst, seconds, d=None, torch=None):
+    """The FP64 oracle as it stands, all host cores, on a bounded source sample;
+    with the library given, also the error of the GPU evaluation of the same
+    sample against it (per result)."""
     import oracle
 
     n = max(1, min(inst.I, int(inst.I * 0.05)))
@@ -257,7 +259,27 @@ def cpu_baseline(inst, seconds):
     cores = oracle.set_threads(0)
     P = oracle.Problem(sub)
     lam = lam_for(inst).astype(np.float64)
-    P.eval(lam, GAMMA)  # warm
+    eo = P.eval(lam, GAMMA)  # warm
+    check = None
+    if d is not None:
+        G = d.Problem.from_instance(sub)
+        grad, ev = G.dual_grad(torch.from_numpy(lam.astype(np.float32)).cuda(), GAMMA)
+        grad = grad.cpu().numpy().astype(np.float64)
+        G.close()
+        b = sub.b.astype(np.float64)
+        size = np.abs(eo.ax) + np.abs(b)
+        err = np.abs(grad - eo.grad)
+        terms = float(np.sum(np.abs(lam) * size))
+        rel = lambda v, r: abs(v - r) / max(1.0, abs(r))
+        check = {"at": "the same lambda and gamma as the pass",
+                 "grad_max_err_over_bound": float(np.max(err / (1e-5 * size + 1e-6))),
+                 "grad_max_rel_to_scale": float(np.max(err[size > 0] / size[size > 0])),
+                 "dual_obj_rel": rel(ev["dual_obj"], eo.dual),
+                 "primal_obj_rel": rel(ev["primal_obj"], eo.primal_lin),
+                 "reg_rel": rel(ev["reg"], eo.reg),
+                 "infeas_l2_rel": rel(ev["infeas_l2"], eo.infeas),
+                 "lambda_dot_grad_rel_to_terms": abs(ev["lambda_dot_grad"] - eo.mu_dot_grad) /
+                 max(1.0, terms)}
     t0 = time.perf_counter()
     reps = 0
     while True:
@@ -266,9 +288,12 @@ def cpu_baseline(inst, seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": sub.E * reps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {n} of {inst.I} sources ({sub.E} edges), {reps} FP64 evaluations "
-                      f"in {dt:.1f} s"}
+    out = {"value": sub.E * reps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"first {n} of {inst.I} sources ({sub.E} edges), {reps} FP64 evaluations "
+                     f"in {dt:.1f} s"}
+    if check is not None:
+        out["gpu_error_vs_oracle"] = check
+    return out
 
 
 def run_reference(args):
@@ -587,7 +612,7 @@ def run_batch(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", **f}
     if not args.no_cpu_baseline and sample is not None:
-        out["cpu_baseline"] = cpu_baseline(sample, args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(sample, args.cpu_seconds, d, torch)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -1013,7 +1038,7 @@ def run_ours(args):
         "ascent_pass": asc,
     }
     if ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds, d, torch)
     if (ws == 1 and args.workload == "c2" and args.scale == 1.0 and not args.no_forms
             and not args.no_solve):
         del inst
