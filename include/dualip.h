@@ -120,12 +120,18 @@ typedef struct dualip_problem dualip_problem;
  * finiteness).  Work is queued on `stream` and finished before return.
  * Errors: DUALIP_EINVAL (bad desc or data), DUALIP_ENOMEM, DUALIP_ECUDA.
  * On success *out owns device memory of about E * (4 + bytes of c and a)
- * + 8 I + 40 J bytes; free it with dualip_destroy.
- * Degree order: when the source degrees spread widely (standard deviation
- * above 0.3 of the mean), the sources are stored in order of increasing
- * degree.  Results do not depend on it beyond rounding: gradients are exact
- * sums either way, the scalars' partial sums come in another order, and
- * dualip_get_primal returns x in the caller's edge order. */
+ * + 12 I + 40 J bytes, plus 16 bytes per edge of hub sources (below); free it
+ * with dualip_destroy.
+ * Degree order: when the pass's lane-group cost model predicts at least 5%
+ * fewer element slots for it, the sources are stored in order of increasing
+ * degree.  Results do not depend on the stored order: A x and the objective
+ * partials are exact fixed-point sums, and dualip_get_primal returns x in the
+ * caller's edge order.
+ * Segment classes: a source larger than a stage (3200 edges with FP32
+ * storage, 4800 with BF16) is projected by a whole CTA; one of at least 16
+ * stages (a hub source) by the whole grid, in a kernel of its own before
+ * each pass, which keeps a candidate list of up to 16 bytes per edge of the
+ * source in device memory (not for the unit box). */
 dualip_status dualip_create(const dualip_problem_desc* desc, void* stream, dualip_problem** out);
 
 /* Release a handle (NULL is ignored).  Synchronises the handle's last stream. */
@@ -400,7 +406,8 @@ dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* 
  * Footprint estimate (bytes): E (4 + bytes(c, a)) + 12 (I + 4) + 16 tiles
  * + 56 J, plus 12 E while host inputs are staged at creation.  A request
  * stored in degree order (see dualip_create) also holds 16 (I + 1) bytes of
- * source map during its creation; the estimate leaves that out.
+ * source map during its creation, and one with hub sources 16 bytes per hub
+ * edge; the estimate leaves both out.
  */
 typedef struct dualip_server dualip_server;
 
