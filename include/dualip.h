@@ -335,8 +335,9 @@ void dualip_batch_destroy(dualip_batch* b);
 
 /*
  * One evaluation of every problem, each at its own gamma, equal to what
- * dualip_dual_grad gives for it alone (the gradient bit for bit; the scalars
- * up to the order of their partial sums).
+ * dualip_dual_grad gives for it alone (the gradient, c^T x and the ridge
+ * term bit for bit; g, the infeasibility and lambda^T (A x - b) up to the
+ * order in which their per-row terms are summed).
  *   lambda [sum J] device joint, read; gammas [n] host; grad [sum J] device joint, written
  *   out [n] host (may be NULL): the scalars of each problem
  * Synchronises the stream.
