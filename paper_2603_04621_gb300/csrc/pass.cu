@@ -1083,10 +1083,9 @@ __device__ __forceinline__ void project_block_body(const GlobalView<BF16>& v, in
 // instruction footprint small.  Returns false, having accounted nothing, if
 // the rounds have not settled after kCandRounds (the multi-pass path then
 // projects the source).
-template <bool BF16, bool MU_SMEM>
+template <bool BF16, bool MU_SMEM, int K = 16>  // K: edges per lane (spans up to 32 K)
 __device__ __forceinline__ bool project_warp_cand(const StageView<BF16>& sv, int base, int d,
                                                   int lane, const Ctx& cx, Sums& acc) {
-  constexpr int K = 16;  // 512 / 32 edges per lane
   float rf[K];
   float rmax = -CUDART_INF_F, s0 = 0.f;
 #pragma unroll
@@ -2052,7 +2051,10 @@ __global__ void __launch_bounds__(kThreads, 1) dualgrad_pass_kernel(PassParams p
             const int dd = __shfl_sync(0xffffffffu, dq, q);
             // (the result is the same for every lane: it follows warp sums)
             const bool done = !W && !WRITE_X && kWarpCand && dd <= 512 &&
-                              project_warp_cand<BF16, MU_SMEM>(sv, b, dd, lane, cx, acc);
+                              (dd <= 32    ? project_warp_cand<BF16, MU_SMEM, 1>(sv, b, dd, lane, cx, acc)
+                               : dd <= 64  ? project_warp_cand<BF16, MU_SMEM, 2>(sv, b, dd, lane, cx, acc)
+                               : dd <= 128 ? project_warp_cand<BF16, MU_SMEM, 4>(sv, b, dd, lane, cx, acc)
+                                           : project_warp_cand<BF16, MU_SMEM, 16>(sv, b, dd, lane, cx, acc));
             if (!done)
               project_multipass<BF16, W>(sv, (int64_t)b, (int64_t)dd, si.a0 + b, lane, cx, acc);
           }
