@@ -337,7 +337,10 @@ void dualip_batch_destroy(dualip_batch* b);
  * One evaluation of every problem, each at its own gamma, equal to what
  * dualip_dual_grad gives for it alone (the gradient, c^T x and the ridge
  * term bit for bit; g, the infeasibility and lambda^T (A x - b) up to the
- * order in which their per-row terms are summed).
+ * order in which their per-row terms are summed).  Exception: a source of at
+ * least 16 stages' edges, which alone goes to the multi-block class, is
+ * projected in a batch by one CTA (the block class); its x then agrees
+ * within rounding, not bit for bit.
  *   lambda [sum J] device joint, read; gammas [n] host; grad [sum J] device joint, written
  *   out [n] host (may be NULL): the scalars of each problem
  * Synchronises the stream.

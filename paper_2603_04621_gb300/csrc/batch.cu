@@ -387,10 +387,13 @@ cudaError_t rebuild_lists(Batch& B) {
   B.rc_host.clear();
   B.act_host.clear();
   B.crange_host.assign(B.n, int2{0, 0});
+  B.has_big = false;
   for (int s = 0; s < B.n; ++s) {
     if (!B.active[s]) continue;
     B.act_host.push_back(s);
     B.jt_host.insert(B.jt_host.end(), B.tiles[s].begin(), B.tiles[s].end());
+    for (const JointTile& t : B.tiles[s])  // a source larger than a stage is read from memory
+      B.has_big = B.has_big || t.e1 - t.e0 > tile_edges_for(B.storage);
     const int c0 = (int)B.rc_host.size();
     for (int32_t r = 0; r < B.prob[s]->J; r += kChunkRows)
       B.rc_host.push_back(RowChunk{s, r, std::min<int32_t>(B.prob[s]->J, r + kChunkRows), 0});
@@ -460,7 +463,7 @@ cudaError_t enqueue_batch_eval(Batch& B, const float* lam, float* grad, int solv
   }
   if (ev && (e = cudaEventRecord(ev[1], s))) return e;
   if ((e = launch_pass_batch(B.storage, B.weighted, B.d_jt, B.ntiles, B.d_slots, B.d_gamma_f,
-                             B.d_slot_part, B.d_status, B.grid, B.lean80, s)))
+                             B.d_slot_part, B.d_status, B.grid, B.lean80, B.has_big, s)))
     return e;
   if (ev && (e = cudaEventRecord(ev[2], s))) return e;
   if ((e = launch_pdl(bepi_kernel, dim3(B.nchunks), dim3(256), 0, s, (const RowChunk*)B.d_rc,

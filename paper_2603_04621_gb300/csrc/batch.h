@@ -21,6 +21,7 @@ struct Batch {
   std::vector<char> active;       // slots in the joint lists
   int64_t tile_edges = kTileEdges, tile_sources = kTileSources;
   int lean80 = 0;  // lean-window policy of the pass (the autotuner may change it)
+  bool has_big = false;  // an active tile holds a source larger than a stage (block class)
   bool lean_auto = false;  // pick lean80 from the degrees of the active slots
   std::vector<int64_t> over76;  // per slot: sources with more than 76 edges
   // per-slot tile lists for the current tile shape (host), and their joint

@@ -345,7 +345,7 @@ cudaError_t launch_pdl(void (*k)(K...), dim3 grid, dim3 block, size_t smem, cuda
 // Batched pass over the joint tile list (ntiles entries) with the given grid.
 cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, int64_t ntiles,
                               const SlotDesc* slots, const float* gamma_of, long long* slot_part,
-                              DeviceStatus* status, int grid, int lean80, cudaStream_t s);
+                              DeviceStatus* status, int grid, int lean80, bool big, cudaStream_t s);
 cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const float* gamma_dev,
                             double gamma, double* eval_out, cudaStream_t s, bool identity = false);
 cudaError_t launch_renumber(const int32_t* dst_in, int32_t* dst_out, const int32_t* new_of,

@@ -2301,7 +2301,11 @@ cudaError_t configure_pass_kernels() {
       set_smem<true, false, false, false, false, false, false, true>(),
       set_smem<true, false, true, false, false, false, false, true>(),
       set_smem<true, true, false, false, false, false, false, true>(),
-      set_smem<true, true, true, false, false, false, false, true>()};
+      set_smem<true, true, true, false, false, false, false, true>(),
+      set_smem<false, false, false, false, true, false, false, true>(),
+      set_smem<false, true, false, false, true, false, false, true>(),
+      set_smem<true, false, false, false, true, false, false, true>(),
+      set_smem<true, true, false, false, true, false, false, true>()};
   for (cudaError_t e : es)
     if (e != cudaSuccess) return e;
   return cudaSuccess;
@@ -2462,7 +2466,8 @@ static cudaError_t dispatch_pass(const Problem& P, const PassParams& p, bool x_o
 
 cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, int64_t ntiles,
                               const SlotDesc* slots, const float* gamma_of, long long* slot_part,
-                              DeviceStatus* status, int grid, int lean80, cudaStream_t s) {
+                              DeviceStatus* status, int grid, int lean80, bool big,
+                              cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   PassParams p{};
   p.grab = DUALIP_GRAB;  // (the batched pass takes contiguous ranges)
@@ -2478,12 +2483,15 @@ cudaError_t launch_pass_batch(int storage, int weighted, const JointTile* jt, in
   const size_t smem = pass_smem_bytes(storage);
   const int g = (int)(ntiles < grid ? ntiles : grid);
   const dim3 gd(g), bd(kThreads);
-  if (bf16) {
-    if (weighted) return launch_pdl(dualgrad_pass_kernel<true, true, false, false, true>, gd, bd, smem, s, p);
-    return launch_pdl(dualgrad_pass_kernel<true, false, false, false, true>, gd, bd, smem, s, p);
-  }
-  if (weighted) return launch_pdl(dualgrad_pass_kernel<false, true, false, false, true>, gd, bd, smem, s, p);
-  return launch_pdl(dualgrad_pass_kernel<false, false, false, false, true>, gd, bd, smem, s, p);
+  // a batch holding a source larger than a tile takes the instance with the
+  // block class (all consumer warps on that source)
+#define DUALIP_LAUNCH_B(B_, W_)                                                                 \
+  (big ? launch_pdl(dualgrad_pass_kernel<B_, W_, false, false, true, false, false, true>, gd, bd, \
+                    smem, s, p)                                                                 \
+       : launch_pdl(dualgrad_pass_kernel<B_, W_, false, false, true>, gd, bd, smem, s, p))
+  if (bf16) return weighted ? DUALIP_LAUNCH_B(true, true) : DUALIP_LAUNCH_B(true, false);
+  return weighted ? DUALIP_LAUNCH_B(false, true) : DUALIP_LAUNCH_B(false, false);
+#undef DUALIP_LAUNCH_B
 }
 
 cudaError_t launch_epilogue(const Problem& P, const float* D, float* grad, const float* gamma_dev,

@@ -80,6 +80,40 @@ def test_batch_matches_lone_and_oracle(dl, storage, weighted):
     B.close()
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+def test_batch_with_sources_larger_than_a_stage(dl, weighted):
+    """A batch holding sources larger than a stage takes the pass instance with
+    the block class.  Sources up to 16 stages are projected by the same code as
+    alone (the gradient bit for bit); a larger one, which alone goes to the
+    multi-block class, agrees with the oracle within the parity bounds."""
+    import torch
+
+    blockish = synth.greedy_budgets(synth.from_degrees(np.array([5_000, 40, 3, 20_000, 0, 12]),
+                                                       30_000, 61, synth.DST_UNIFORM))
+    hubbish = synth.greedy_budgets(synth.from_degrees(np.array([70_000, 9, 300, 4_000]),
+                                                      80_000, 62, synth.DST_UNIFORM))
+    insts = [blockish, hubbish]
+    probs = [dl.Problem.from_instance(x, primal_scaling=weighted) for x in insts]
+    B = dl.Batch(probs)
+    lam = lam_joint(insts, 3)
+    lt = torch.from_numpy(lam).cuda()
+    for gammas in ([1e-3, 1e-3], [0.2, 0.05]):
+        grad, evs = B.dual_grad(lt, gammas)
+        g = grad.cpu().numpy()
+        for k, (x, P) in enumerate(zip(insts, probs)):
+            lk = lt[B.joff[k]:B.joff[k + 1]]
+            gk = g[B.joff[k]:B.joff[k + 1]]
+            g1, e1 = P.dual_grad(lk, gammas[k])
+            if k == 0:
+                assert np.array_equal(gk, g1.cpu().numpy())
+            eo = oracle.Problem(x, weighted=weighted).eval(
+                lam[B.joff[k]:B.joff[k + 1]].astype(np.float64), gammas[k])
+            tol = GRAD_RTOL * (np.abs(eo.ax) + np.abs(x.b.astype(np.float64))) + 1e-6
+            assert np.all(np.abs(gk - eo.grad) <= tol), k
+            assert abs(evs[k]["dual_obj"] - eo.dual) <= OBJ_RTOL * max(1.0, abs(eo.dual)), k
+    B.close()
+
+
 def test_batch_autotune_keeps_results(dl):
     import torch
 
