@@ -122,7 +122,7 @@ typedef struct dualip_problem dualip_problem;
  * On success *out owns device memory of about E * (4 + bytes of c and a)
  * + 12 I + 40 J bytes, plus 16 bytes per edge of hub sources (below); free it
  * with dualip_destroy.
- * Degree order: when the pass's lane-group cost model predicts at least 5%
+ * Degree order: when the pass's lane-group cost model predicts at least 2%
  * fewer element slots for it, the sources are stored in order of increasing
  * degree.  Results do not depend on the stored order: A x and the objective
  * partials are exact fixed-point sums, and dualip_get_primal returns x in the

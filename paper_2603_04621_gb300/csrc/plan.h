@@ -118,7 +118,7 @@ inline double lean_slots(const std::vector<int64_t>& off, int64_t max_edges, int
 }
 
 // The stored order of a problem: degree order (src_of, off_st filled) when the
-// cost model above gives it at least 5% fewer element slots than the caller's
+// cost model above gives it at least 2% fewer element slots than the caller's
 // order, for tiles of max_edges / max_sources; else the caller's order
 // (src_of, off_st left empty).  DUALIP_DEGREE_ORDER = 0 or 1 forces never or
 // always (for measurements).
@@ -135,7 +135,7 @@ inline bool choose_degree_order(const std::vector<int64_t>& off, int64_t max_edg
   degree_order(off, src_of, off_st);
   if (DUALIP_DEGREE_ORDER == 1) return true;
   if (lean_slots(off_st, max_edges, max_sources, true) <
-      0.95 * lean_slots(off, max_edges, max_sources, true))
+      0.98 * lean_slots(off, max_edges, max_sources, true))
     return true;
   src_of.clear();
   off_st.clear();

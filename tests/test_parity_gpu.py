@@ -335,7 +335,7 @@ def test_degree_order_storage(dl, storage, weighted):
     import torch
 
     inst = synth.matching(20_000, 3_000, 17, ("uniform", 5, 100), "zipf")
-    assert degree_cv(inst) > 0.3  # the documented threshold for degree order
+    assert degree_cv(inst) > 0.3  # widely spread degrees: the cost model picks degree order
     rng = np.random.default_rng(9)
     P = Po = None
     for gamma in (0.1, 1e-3):
