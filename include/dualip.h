@@ -120,7 +120,7 @@ typedef struct dualip_problem dualip_problem;
  * finiteness).  Work is queued on `stream` and finished before return.
  * Errors: DUALIP_EINVAL (bad desc or data), DUALIP_ENOMEM, DUALIP_ECUDA.
  * On success *out owns device memory of about E * (4 + bytes of c and a)
- * + 12 I + 40 J bytes, plus 16 bytes per edge of hub sources (below); free it
+ * + 12 I + 40 J bytes, plus 20 bytes per edge of hub sources (below); free it
  * with dualip_destroy.
  * Degree order: when the pass's lane-group cost model predicts at least 2%
  * fewer element slots for it, the sources are stored in order of increasing
@@ -131,7 +131,11 @@ typedef struct dualip_problem dualip_problem;
  * storage, 4800 with BF16) is projected by a whole CTA; one of at least 16
  * stages (a hub source) by the whole grid, in a kernel of its own before
  * each pass, which keeps a candidate list of up to 16 bytes per edge of the
- * source in device memory (not for the unit box). */
+ * source in device memory (not for the unit box).  A hub source's edges are
+ * stored in order of destination (4 bytes per edge keep the permutation;
+ * sorting them takes a stream-ordered temporary of 12 bytes per hub edge and
+ * a host pass over J per hub source), so that neighbouring lanes gather mu
+ * from shared sectors; results do not depend on that order either. */
 dualip_status dualip_create(const dualip_problem_desc* desc, void* stream, dualip_problem** out);
 
 /* Release a handle (NULL is ignored).  Synchronises the handle's last stream. */
@@ -168,7 +172,7 @@ dualip_status dualip_dual_grad_host(dualip_problem* p, const float* lambda_host,
  * caller's edge order:
  *   x  [E] float, device, written.  Other arguments as dualip_dual_grad.
  * For a problem stored in degree order it takes a stream-ordered temporary of
- * E floats and 16 bytes per source. */
+ * E floats and 16 bytes per source; with hub sources, one of E floats. */
 dualip_status dualip_get_primal(dualip_problem* p, const float* lambda, double gamma, float* x,
                                 void* stream);
 
@@ -410,8 +414,8 @@ dualip_status dualip_batch_get_info(const dualip_batch* b, int32_t* n, int64_t* 
  * Footprint estimate (bytes): E (4 + bytes(c, a)) + 12 (I + 4) + 16 tiles
  * + 56 J, plus 12 E while host inputs are staged at creation.  A request
  * stored in degree order (see dualip_create) also holds 16 (I + 1) bytes of
- * source map during its creation, and one with hub sources 16 bytes per hub
- * edge; the estimate leaves both out.
+ * source map during its creation, and one with hub sources 20 bytes per hub
+ * edge (and 12 more while it is built); the estimate leaves these out.
  */
 typedef struct dualip_server dualip_server;
 

@@ -123,6 +123,60 @@ static cudaError_t enqueue_eval(Problem& P, const float* lambda, double gamma, f
 // c and the m coefficient arrays stay separate FP32 arrays, and every J-length
 // array of the handle has m Jd rows in the caller's row order; the prologue,
 // epilogue and solver kernels then work unchanged on those rows.
+// Stores the edges of every hub source in order of destination: a stable
+// counting sort of its renumbered ids on the host, then a gather of its
+// (dst, c, a) on the device.  The source's simplex does not depend on the
+// order of its edges; sorted ids let the lanes of a warp gather mu from
+// shared sectors of L2 instead of one sector per edge.  The permutation stays
+// in P.hub_perm for dualip_get_primal.
+static cudaError_t sort_hub_edges(Problem& P, int64_t hub_edges, cudaStream_t s) {
+  const size_t ce = P.storage == DUALIP_EDGE_BF16 ? 4 : 8;  // bytes of a stored (c, a)
+  char* ca = P.storage == DUALIP_EDGE_BF16 ? reinterpret_cast<char*>(P.ca)
+                                            : reinterpret_cast<char*>(P.ca2);
+  std::vector<int32_t> dh((size_t)hub_edges);
+  cudaError_t e;
+  for (const HubDesc& hd : P.hub_host)
+    if ((e = cudaMemcpyAsync(dh.data() + hd.cand0, P.dst + hd.e0, 4 * (size_t)hd.deg,
+                             cudaMemcpyDeviceToHost, s)))
+      return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
+  std::vector<uint32_t> perm((size_t)hub_edges), start((size_t)P.J + 1);
+  for (const HubDesc& hd : P.hub_host) {
+    const int32_t* d = dh.data() + hd.cand0;
+    uint32_t* pm = perm.data() + hd.cand0;
+    std::fill(start.begin(), start.end(), 0u);
+    for (int32_t k = 0; k < hd.deg; ++k) ++start[(size_t)d[k] + 1];  // ids were checked
+    for (int32_t j = 0; j < P.J; ++j) start[(size_t)j + 1] += start[j];
+    for (int32_t k = 0; k < hd.deg; ++k) pm[start[d[k]]++] = (uint32_t)k;
+  }
+  int32_t* tdst = nullptr;
+  char* tca = nullptr;
+  if ((e = dev_alloc(P, &P.hub_perm, (size_t)hub_edges)) ||
+      (e = cudaMemcpyAsync(P.hub_perm, perm.data(), 4 * (size_t)hub_edges,
+                           cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMallocAsync(&tdst, 4 * (size_t)hub_edges, s)) ||
+      (e = cudaMallocAsync(&tca, ce * (size_t)hub_edges, s))) {
+    if (tdst) cudaFreeAsync(tdst, s);
+    cudaStreamSynchronize(s);
+    return e;
+  }
+  for (const HubDesc& hd : P.hub_host) {
+    if ((e = cudaMemcpyAsync(tdst + hd.cand0, P.dst + hd.e0, 4 * (size_t)hd.deg,
+                             cudaMemcpyDeviceToDevice, s)) ||
+        (e = cudaMemcpyAsync(tca + ce * hd.cand0, ca + ce * hd.e0, ce * (size_t)hd.deg,
+                             cudaMemcpyDeviceToDevice, s)) ||
+        (e = launch_gather_perm(tdst + hd.cand0, P.dst + hd.e0, P.hub_perm + hd.cand0, hd.deg,
+                                4, s)) ||
+        (e = launch_gather_perm(tca + ce * hd.cand0, ca + ce * hd.e0, P.hub_perm + hd.cand0,
+                                hd.deg, (int)ce, s)))
+      break;
+  }
+  cudaFreeAsync(tdst, s);
+  cudaFreeAsync(tca, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  return e ? e : e2;
+}
+
 dualip_status create_multi(const dualip_problem_desc* d, void* stream, dualip_problem** out) {
   const int64_t I = d->num_sources, E = d->num_edges;
   const int32_t Jd = d->num_dests, m = d->num_families;
@@ -580,6 +634,21 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
       (e = cudaStreamSynchronize(s)))
     return bail(cuda_fail(e, "reading the device status"));
   if (st.err) return bail(fail(DUALIP_EINVAL, "dst out of [0, J) or non-finite c / a"));
+  if (P.nhub > 0) {
+    P.hub_host = hubs;
+    P.hub_caller0.resize(hubs.size());
+    for (size_t k = 0; k < hubs.size(); ++k) {
+      int64_t g = hubs[k].e0;
+      if (seg) {  // the stored source whose segment starts at e0 (it is not empty)
+        const int64_t i = (int64_t)(std::upper_bound(off_s.begin(), off_s.end(), g) -
+                                    off_s.begin()) - 1;
+        g = off[src_of[i]];
+      }
+      P.hub_caller0[k] = g;
+    }
+    if ((e = sort_hub_edges(P, hub_edges, s)))
+      return bail(cuda_fail(e, "storing the hub sources in destination order"));
+  }
   if (seg) {
     P.off_host = std::move(off_st);
     P.orig_off_host = std::move(off);
@@ -667,24 +736,36 @@ dualip_status dualip_get_primal(dualip_problem* h, const float* lambda, double g
   cudaStream_t s = as_stream(stream);
   P.last_stream = s;
   cudaError_t e;
-  if (P.src_of_host.empty()) {
+  const bool seg = !P.src_of_host.empty();
+  if (!seg && P.nhub == 0) {
     e = enqueue_eval(P, lambda, gamma, P.grad_stage, P.eval_dev, x, s);
     return e ? cuda_fail(e, "launching the primal evaluation") : DUALIP_OK;
   }
   // degree order: x in stored order, then each source's segment back to the
-  // caller's place (stream-ordered temporaries)
+  // caller's place; hub sources: their edges back from destination order
+  // (stream-ordered temporaries)
   float* xs = nullptr;
   int64_t *src = nullptr, *orig = nullptr;
   const int64_t I = P.I;
   if (!(e = cudaMallocAsync(&xs, sizeof(float) * std::max<int64_t>(P.E, 1), s)) &&
-      !(e = cudaMallocAsync(&src, sizeof(int64_t) * I, s)) &&
-      !(e = cudaMallocAsync(&orig, sizeof(int64_t) * (I + 1), s)) &&
-      !(e = cudaMemcpyAsync(src, P.src_of_host.data(), sizeof(int64_t) * I,
-                            cudaMemcpyHostToDevice, s)) &&
-      !(e = cudaMemcpyAsync(orig, P.orig_off_host.data(), sizeof(int64_t) * (I + 1),
-                            cudaMemcpyHostToDevice, s)) &&
-      !(e = enqueue_eval(P, lambda, gamma, P.grad_stage, P.eval_dev, xs, s)))
-    e = launch_unpermute_seg(xs, x, SegMap{P.off, src, orig, I}, s);
+      !(e = enqueue_eval(P, lambda, gamma, P.grad_stage, P.eval_dev, xs, s))) {
+    if (seg) {
+      if (!(e = cudaMallocAsync(&src, sizeof(int64_t) * I, s)) &&
+          !(e = cudaMallocAsync(&orig, sizeof(int64_t) * (I + 1), s)) &&
+          !(e = cudaMemcpyAsync(src, P.src_of_host.data(), sizeof(int64_t) * I,
+                                cudaMemcpyHostToDevice, s)) &&
+          !(e = cudaMemcpyAsync(orig, P.orig_off_host.data(), sizeof(int64_t) * (I + 1),
+                                cudaMemcpyHostToDevice, s)))
+        e = launch_unpermute_seg(xs, x, SegMap{P.off, src, orig, I}, s);
+    } else if (P.E > 0) {
+      e = cudaMemcpyAsync(x, xs, sizeof(float) * P.E, cudaMemcpyDeviceToDevice, s);
+    }
+    for (size_t k = 0; !e && k < P.hub_host.size(); ++k) {
+      const HubDesc& hd = P.hub_host[k];
+      e = launch_scatter_perm(xs + hd.e0, x + P.hub_caller0[k], P.hub_perm + hd.cand0, hd.deg,
+                              s);
+    }
+  }
   if (xs) cudaFreeAsync(xs, s);
   if (src) cudaFreeAsync(src, s);
   if (orig) cudaFreeAsync(orig, s);

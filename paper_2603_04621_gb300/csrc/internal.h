@@ -252,6 +252,14 @@ struct Problem {
   HubUnitStat* hub_stat = nullptr;   // [nchunks * units per chunk]
   float4* hub_cand = nullptr;        // [sum of hub degrees] candidate lists
   unsigned* hub_cnt = nullptr;       // [2 nhub] candidates so far, chunks done
+  // A hub source's edges are stored in order of destination (renumbered id),
+  // so that the mu gathers of a warp read neighbouring ids.  hub_perm[cand0 +
+  // k] is the place, within the source's segment, that its stored edge k had
+  // in the caller's order; hub_host and hub_caller0 (the segment's start in
+  // the caller's edge order) serve dualip_get_primal.
+  uint32_t* hub_perm = nullptr;      // [sum of hub degrees]
+  std::vector<HubDesc> hub_host;
+  std::vector<int64_t> hub_caller0;
   // constraint families (Definition 1): with m > 1, J counts rows (m Jd, row
   // k Jd + j), the edges keep the caller's order and destination ids, and c,
   // a (family-major, a[k E + e]) live in cm, am; the pass is multi.cu's
@@ -371,6 +379,12 @@ cudaError_t launch_renumber_seg(const int32_t* dst_in, int32_t* dst_out, const i
 cudaError_t launch_pack_seg(const float* c, const float* a, int storage, void* out,
                             const SegMap& m, cudaStream_t s);
 cudaError_t launch_unpermute_seg(const float* in, float* out, const SegMap& m, cudaStream_t s);
+// out[k] = in[perm[k]] (elements of 4 or 8 bytes) and out[perm[k]] = in[k],
+// for k < n
+cudaError_t launch_gather_perm(const void* in, void* out, const uint32_t* perm, int64_t n,
+                               int elem_bytes, cudaStream_t s);
+cudaError_t launch_scatter_perm(const float* in, float* out, const uint32_t* perm, int64_t n,
+                                cudaStream_t s);
 cudaError_t launch_absmax(const float* v, int64_t n, unsigned* out, cudaStream_t s);
 
 // solve.cu

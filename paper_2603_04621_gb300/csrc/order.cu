@@ -1,4 +1,5 @@
-// Degree order of the stored sources (dualip_create, dualip_get_primal).
+// Degree order of the stored sources and destination order of the hub sources'
+// edges (dualip_create, dualip_get_primal).
 //
 // A problem whose source degrees spread widely is stored with its sources in
 // order of increasing degree.  The pass takes sources in batches of eight
@@ -7,6 +8,10 @@
 // separable by source (Section 3.1: the projection is one simplex per
 // source), so the order changes no per-source result: A x is summed exactly,
 // and only the order of the objective's partial sums moves.
+//
+// Hub sources (the multi-block class) are, besides, stored with their edges
+// in order of destination: a source's simplex is the same in any order of
+// its edges, and sorted ids let a warp's mu gathers share sectors.
 //
 // These kernels move whole source segments between the caller's edge order
 // and the stored one: one warp per stored source, its lanes over the
@@ -79,7 +84,52 @@ __global__ void unpermute_seg_kernel(const float* __restrict__ in, float* __rest
   }
 }
 
+// A permutation within one segment (the destination order of a hub source):
+// out[k] = in[perm[k]], and its inverse for the primal x.
+template <typename T>
+__global__ void gather_perm_kernel(const T* __restrict__ in, T* __restrict__ out,
+                                   const uint32_t* __restrict__ perm, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride)
+    out[k] = in[perm[k]];
+}
+
+__global__ void scatter_perm_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                    const uint32_t* __restrict__ perm, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride)
+    out[perm[k]] = in[k];
+}
+
+int elems_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 8192) g = 8192;
+  return (int)g;
+}
+
 }  // namespace
+
+cudaError_t launch_gather_perm(const void* in, void* out, const uint32_t* perm, int64_t n,
+                               int elem_bytes, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (elem_bytes == 8)
+    gather_perm_kernel<uint2><<<elems_grid(n), 256, 0, s>>>(static_cast<const uint2*>(in),
+                                                            static_cast<uint2*>(out), perm, n);
+  else if (elem_bytes == 4)
+    gather_perm_kernel<uint32_t><<<elems_grid(n), 256, 0, s>>>(
+        static_cast<const uint32_t*>(in), static_cast<uint32_t*>(out), perm, n);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_perm(const float* in, float* out, const uint32_t* perm, int64_t n,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  scatter_perm_kernel<<<elems_grid(n), 256, 0, s>>>(in, out, perm, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_renumber_seg(const int32_t* dst_in, int32_t* dst_out, const int32_t* new_of,
                                 const SegMap& m, int32_t J, DeviceStatus* st, cudaStream_t s) {

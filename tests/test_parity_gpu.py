@@ -172,6 +172,38 @@ def test_hub_sources_bf16_primal_and_repeat(dl, weighted):
     P.close()
 
 
+@pytest.mark.parametrize("order", ["caller", "degree"])
+def test_hub_edges_in_destination_order(dl, order):
+    """Hub sources are stored with their edges sorted by destination.  The
+    primal comes back in the caller's edge order, with repeated destinations
+    in a hub (ties of the sort) and hubs among sources kept in the caller's
+    order (ascending degrees) or stored in degree order (widely spread small
+    degrees around them)."""
+    import torch
+
+    rng = np.random.default_rng(47)
+    if order == "caller":
+        degs = np.array([3, 10, 40, 300, 70_000, 200_000])
+    else:
+        degs = np.concatenate([[200_000], rng.integers(5, 101, 6_000), [70_000],
+                               rng.integers(5, 101, 6_000)])
+    inst = synth.from_degrees(degs, 400_000, 29, synth.DST_UNIFORM, b_frac=0.3)
+    hub = int(np.argmax(degs))
+    e0 = int(inst.off[hub])
+    # repeated (i, j) pairs inside the largest hub: separate variables with the
+    # same destination, at places far apart in the caller's order
+    inst.dst[e0 + 1000:e0 + 1100] = inst.dst[e0 + 150_000:e0 + 150_100]
+    inst.dst[e0 + 7] = inst.dst[e0 + 199_990]
+    for gamma, lam in ((1e-3, rng.uniform(0, 1, inst.J)), (5.0, np.zeros(inst.J))):
+        P, Po, _, _ = check_eval(dl, inst, lam, gamma)
+        lam32 = torch.from_numpy(lam.astype(np.float32)).cuda()
+        x = P.primal(lam32, gamma).cpu().numpy().astype(np.float64)
+        xo = Po.eval(lam.astype(np.float32).astype(np.float64), gamma, want_x=True).x
+        assert np.all(np.abs(x - xo) <= 2e-5 * np.maximum(1.0, np.abs(xo)) + 1e-6), (
+            np.abs(x - xo).max())
+        P.close()
+
+
 @pytest.mark.parametrize("storage,weighted", [("f32", False), ("f32", True), ("bf16", False)])
 def test_small_degree_sources_at_solver_points(dl, storage, weighted):
     """The small-degree variant (mean degree at most 16: one lane per source of

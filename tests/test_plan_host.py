@@ -226,6 +226,13 @@ def test_degree_order_is_chosen_by_the_slot_model(plan):
     # Poisson(80) in [1, 2000] with 4800-edge BF16 tiles (the precision workload):
     # about half the spans exceed 80, so unsorted batches mix 4- and 8-lane rounds
     assert choose(np.clip(rng.poisson(80, 50_000), 1, 2000), max_e=4800) == 1
+    # hub sources among the others (the two mixes of the GPU test of hub edges
+    # in destination order): ascending degrees stay in the caller's order,
+    # hubs among Uniform[5, 100] degrees are stored in degree order
+    assert choose(np.array([3, 10, 40, 300, 70_000, 200_000])) == 0
+    r47 = np.random.default_rng(47)
+    assert choose(np.concatenate([[200_000], r47.integers(5, 101, 6_000), [70_000],
+                                  r47.integers(5, 101, 6_000)])) == 1
     # whatever it picks, the model never prefers an order it scores higher
     for deg in (rng.poisson(50, 20_000), rng.poisson(40, 20_000), rng.integers(1, 300, 20_000)):
         off = offsets(deg)
