@@ -1283,31 +1283,11 @@ __device__ __forceinline__ void flush_sums(const Sums& acc, long long* dst, int 
 // The rounds' sums are 64-bit fixed point, exact in any order, so the result
 // does not depend on the order in which the warps appended their candidates.
 // No CTA waits for another.
-// A warp's units reach shared memory by bulk asynchronous copies that its
-// lane 0 issues one chunk ahead (two slots per warp, one mbarrier each), so
-// the HBM latency of the next unit hides behind the work on this one.  The
-// edges of a hub source are stored in order of destination, and the mu
-// gathers of a warp's lanes then share L2 sectors.
 constexpr int kHubWarps = kHubThreads / 32;
 constexpr int kHubUnit = kHubChunk / kHubWarps;  // edges of a warp's unit
 constexpr int kHubU = kHubUnit / 32;             // edges per lane
 constexpr int kHubCtasPerSm = 2;                 // resident hub CTAs per SM (registers, staging)
 static_assert(kHubU * 32 * kHubWarps == kHubChunk, "a chunk is one unit per warp");
-
-// Shared staging of the hub kernel: per warp two slots, each the unit's ids
-// and its (c, a), copied from windows widened to 16-byte boundaries (ids from
-// a multiple of 4 edges; (c, a) from a multiple of 2 edges in FP32, 4 in
-// BF16), so a slot holds up to kHubUnit + 4 edges of each.
-template <bool BF16>
-struct HubStage {
-  static constexpr int kCaB = BF16 ? 4 : 8;            // bytes of a stored (c, a)
-  static constexpr int kCaAlign = BF16 ? 4 : 2;        // edges per 16 bytes of (c, a)
-  static constexpr int kDst = (kHubUnit + 4) * 4;      // ids of a slot
-  static constexpr int kSlot = kDst + (kHubUnit + 4) * kCaB;
-  static constexpr int kBars = 2 * kHubWarps * kSlot;  // the mbarriers follow the slots
-  static constexpr int kBytes = kBars + 2 * kHubWarps * 8;
-  static_assert(kDst % 16 == 0 && kSlot % 16 == 0, "slots start on 16-byte boundaries");
-};
 
 struct HubParams {
   const int32_t* dst;
@@ -1335,7 +1315,6 @@ struct HubRed {
   double d[kHubWarps], e[kHubWarps];
   long long q[3][kHubWarps];
   int last;
-  int abort;  // a staging wait gave up (every later wait returns at once)
 };
 
 // Scale exponent s with n * m * 2^s < 2^61: n terms of magnitude at most m
@@ -1351,7 +1330,6 @@ __device__ __forceinline__ int hub_fixed_exp(unsigned n, double m) {
 template <bool BF16, bool W, bool WX>
 __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc hd, const Ctx& cx,
                                        HubRed& r) {
-  constexpr int kU = 4;  // loads in flight per thread in each sweep
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const GlobalView<BF16> gv{p.dst, p.ca2, p.ca};
   // the unit statistics, in unit order
@@ -1359,22 +1337,12 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
   double s0 = 0.0;
   const int nu = hd.nch * kHubWarps;
   const HubUnitStat* st = p.stat + (int64_t)hd.c0 * kHubWarps;
-  for (int q0 = tid; q0 < nu; q0 += kU * kHubThreads) {
-    double2 v[kU];
-#pragma unroll
-    for (int i = 0; i < kU; ++i) {
-      const int q = q0 + i * kHubThreads;
-      v[i] = q < nu ? __ldcg(reinterpret_cast<const double2*>(st + q)) : make_double2(0.0, 0.0);
-    }
-#pragma unroll
-    for (int i = 0; i < kU; ++i) {
-      if (q0 + i * kHubThreads < nu) {
-        const long long bits = __double_as_longlong(v[i].y);
-        rmax = fmaxf(rmax, __int_as_float((int)(bits & 0xffffffffll)));
-        mb = fmaxf(mb, __int_as_float((int)(bits >> 32)));
-        s0 += v[i].x;
-      }
-    }
+  for (int q = tid; q < nu; q += kHubThreads) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(st + q));
+    const long long bits = __double_as_longlong(v.y);
+    rmax = fmaxf(rmax, __int_as_float((int)(bits & 0xffffffffll)));
+    mb = fmaxf(mb, __int_as_float((int)(bits >> 32)));
+    s0 += v.x;
   }
   rmax = warp_max(rmax);
   mb = warp_max(mb);
@@ -1404,59 +1372,29 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
     return W ? ((double)v.x - (double)rmax) + (double)v.y
              : (double)__fadd_rn(__fsub_rn(v.x, rmax), v.y);
   };
-  // f(v) for every candidate, kU independent loads per thread at a time
-  auto sweep = [&](auto&& f) {
-    for (unsigned q0 = tid; q0 < N; q0 += kU * kHubThreads) {
-      float4 v[kU];
-#pragma unroll
-      for (int i = 0; i < kU; ++i) {
-        const unsigned q = q0 + i * kHubThreads;
-        v[i] = q < N ? __ldcg(L + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int i = 0; i < kU; ++i)
-        if (q0 + i * kHubThreads < N) f(v[i]);
-    }
-  };
-  // The candidates above the lower bound lb (the only ones the rounds count,
-  // as their threshold never falls below lb) are few: when no thread meets
-  // more than two, each keeps its own in registers and the rounds read no
-  // memory.
-  double d0 = 0.0, d1 = 0.0, lb = 0.0, t = 0.0;
-  float a0 = 0.f, a1 = 0.f;
-  int k0 = 0, k1 = 0, ns = 0;
-  bool keep = false;
+  double t = 0.0;
   if (mode == 2) {
     // a lower bound of the threshold lowered by the FP32 rounding of the scores
     const float slack = __fmul_rn(fabsf(rmax), 0x1p-20f);
-    lb = W ? (double)__fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack)
-           : (double)__fsub_rn(-cx.gamma, slack);
+    const double lb = W ? (double)__fsub_rn(fminf(__fsub_rn(mb, rmax), 0.f), slack)
+                        : (double)__fsub_rn(-cx.gamma, slack);
     // magnitudes of the summed terms, for the fixed-point scales
     double m1 = 0.0, m2 = 0.0;
-    sweep([&](const float4& v) {
+    for (unsigned q = tid; q < N; q += kHubThreads) {
+      const float4 v = __ldcg(L + q);
       const double dk = shifted(v);
       if (dk > lb) {
         m1 = fmax(m1, fabs(W ? (double)v.z * dk : dk));
         m2 = fmax(m2, (double)v.z);
-        if (ns == 0) {
-          d0 = dk;
-          a0 = v.z;
-          k0 = __float_as_int(v.w);
-        } else if (ns == 1) {
-          d1 = dk;
-          a1 = v.z;
-          k1 = __float_as_int(v.w);
-        }
-        ++ns;
       }
-    });
+    }
     m1 = warp_dmax(m1);
     m2 = warp_dmax(m2);
     if (lane == 0) {
       r.d[w] = m1;
       r.e[w] = m2;
     }
-    keep = __syncthreads_and(ns <= 2) != 0;
+    __syncthreads();
     m1 = r.d[0];
     m2 = r.e[0];
     for (int k = 1; k < kHubWarps; ++k) {
@@ -1470,18 +1408,14 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
     t = lb;
     for (unsigned it = 0; it <= N; ++it) {
       long long sa = 0, sb = 0, nn = 0;
-      auto add = [&](double dk, float al) {
+      for (unsigned q = tid; q < N; q += kHubThreads) {
+        const float4 v = __ldcg(L + q);
+        const double dk = shifted(v);
         if (dk > theta) {
-          sa += __double2ll_rn(ldexp(W ? (double)al * dk : dk, s1));
-          if (W) sb += __double2ll_rn(ldexp((double)al, s2));
+          sa += __double2ll_rn(ldexp(W ? (double)v.z * dk : dk, s1));
+          if (W) sb += __double2ll_rn(ldexp((double)v.z, s2));
           ++nn;
         }
-      };
-      if (keep) {
-        if (ns > 0) add(d0, a0);
-        if (ns > 1) add(d1, a1);
-      } else {
-        sweep([&](const float4& v) { add(shifted(v), v.z); });
       }
       sa = warp_isum64(sa);
       sb = warp_isum64(sb);
@@ -1511,12 +1445,19 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
   }
   // x of the candidates (every other edge of the source has x = 0)
   Sums acc;
-  auto x_of = [&](double dk, float al) -> float {
-    if (!(dk > t)) return 0.f;
-    return W ? (float)((double)al * (dk - t)) : __fmul_rn(al, __fsub_rn((float)dk, (float)t));
-  };
-  auto emit = [&](int k, float x) {
-    const int64_t e = hd.e0 + k;
+  for (unsigned q = tid; q < N; q += kHubThreads) {
+    const float4 v = __ldcg(L + q);
+    const int64_t e = hd.e0 + __float_as_int(v.w);
+    float x = 0.f;
+    if (mode == 1) {
+      const float rf = __fadd_rn(v.x, v.y);
+      x = rf > 0.f ? __fmul_rn(v.z, rf) : 0.f;
+    } else if (mode == 2) {
+      const double dk = shifted(v);
+      if (dk > t)
+        x = W ? (float)((double)v.z * (dk - t))
+              : __fmul_rn(v.z, __fsub_rn((float)dk, (float)t));
+    }
     if (x > 0.f) {
       int j;
       float c, a;
@@ -1524,22 +1465,6 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
       acc.account(cx, j, c, a, edge_w<W>(a), x);
     }
     if (WX) p.x_out[e] = x;
-  };
-  if (!WX && keep && t >= lb) {
-    // every other candidate has d <= lb <= t
-    if (ns > 0) emit(k0, x_of(d0, a0));
-    if (ns > 1) emit(k1, x_of(d1, a1));
-  } else if (WX || mode != 0) {
-    sweep([&](const float4& v) {
-      float x = 0.f;
-      if (mode == 1) {
-        const float rf = __fadd_rn(v.x, v.y);
-        x = rf > 0.f ? __fmul_rn(v.z, rf) : 0.f;
-      } else if (mode == 2) {
-        x = x_of(shifted(v), v.z);
-      }
-      emit(__float_as_int(v.w), x);
-    });
   }
   const long long cs = warp_isum64(acc.cx), ws = warp_isum64(acc.wxx);
   if (lane == 0) {
@@ -1563,19 +1488,8 @@ __device__ __noinline__ void hub_solve(const HubParams& p, int h, const HubDesc 
 
 template <bool BF16, bool W, bool WX>
 __global__ void __launch_bounds__(kHubThreads, kHubCtasPerSm) hub_kernel(HubParams p) {
-  using HS = HubStage<BF16>;
   __shared__ HubRed r;
-  extern __shared__ __align__(128) unsigned char hsm[];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  unsigned char* slot_base = hsm + (size_t)w * 2 * HS::kSlot;  // this warp's two slots
-  uint64_t* bar = reinterpret_cast<uint64_t*>(hsm + HS::kBars) + 2 * w;
-  if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  if (tid == 0) r.abort = 0;
-  __syncthreads();
   Ctx cx;
   cx.mu_a = 0u;
   cx.mu_g = p.mu_r;
@@ -1591,90 +1505,25 @@ __global__ void __launch_bounds__(kHubThreads, kHubCtasPerSm) hub_kernel(HubPara
   cx.dst_g = p.dst;
   cx.ca2_g = p.ca2;
   cx.ca_g = p.ca;
-  const unsigned char* ca_g = BF16 ? reinterpret_cast<const unsigned char*>(p.ca)
-                                   : reinterpret_cast<const unsigned char*>(p.ca2);
+  const GlobalView<BF16> gv{p.dst, p.ca2, p.ca};
   const int64_t c_begin = (int64_t)blockIdx.x * p.nchunks / gridDim.x;
   const int64_t c_end = (int64_t)(blockIdx.x + 1) * p.nchunks / gridDim.x;
-  // this warp's unit of chunk c of hub source hd: first edge eb, n edges
-  auto unit_of = [&](int64_t c, const HubDesc& hd, int& k0, int& n) {
-    k0 = (int)(c - hd.c0) * kHubChunk + w * kHubUnit;
-    n = hd.deg - k0 < 0 ? 0 : (hd.deg - k0 < kHubUnit ? hd.deg - k0 : kHubUnit);
-  };
-  // lane 0: the bulk copies of a unit into slot sl (windows on 16-byte
-  // boundaries; every padded edge array extends to a multiple of 4 edges)
-  auto issue = [&](int sl, int64_t eb, int n) {
-    const int64_t d0 = eb & ~3ll, d1 = (eb + n + 3) & ~3ll;
-    const int64_t a0 = eb & ~(int64_t)(HS::kCaAlign - 1);
-    const int64_t a1 = (eb + n + HS::kCaAlign - 1) & ~(int64_t)(HS::kCaAlign - 1);
-    const uint32_t bd = (uint32_t)(d1 - d0) * 4u, ba = (uint32_t)(a1 - a0) * HS::kCaB;
-    unsigned char* sb = slot_base + sl * HS::kSlot;
-    // the slot's previous reads (generic proxy) come before the copies' writes
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(&bar[sl], bd + ba);
-    bulk_g2s(sb, p.dst + d0, bd, &bar[sl]);
-    bulk_g2s(sb + HS::kDst, ca_g + a0 * HS::kCaB, ba, &bar[sl]);
-  };
-  // slot state, the same in every lane: bit s = parity of slot s's next
-  // phase, bit 2 + s = slot s has a copy in flight
-  unsigned sst = 0u;
-  int h = c_begin < c_end ? __ldg(p.chunk_hub + c_begin) : 0;
-  HubDesc hd = p.hubs[h];
-  int k0, n;
-  unit_of(c_begin, hd, k0, n);
-  // the edges do not depend on the previous kernel: the first copy goes out
-  // before the wait for it
-  if (c_begin < c_end && n > 0) {
-    if (lane == 0) issue(0, hd.e0 + k0, n);
-    sst |= 4u;
-  }
   pdl_wait();  // mu of this evaluation; A x rewound by the last epilogue
   pdl_trigger();
   cx.gamma = p.gamma_dev ? *p.gamma_dev : p.gamma;
   cx.inv_gamma = __frcp_rn(cx.gamma);
   unsigned run = 0u;  // chunks of the current source since the last ticket
+  int h = c_begin < c_end ? __ldg(p.chunk_hub + c_begin) : 0;
+  HubDesc hd = p.hubs[h];
   for (int64_t c = c_begin; c < c_end; ++c) {
-    const int sl = (int)((c - c_begin) & 1);
-    // the next chunk's unit goes out before this one is read
-    const int hn = c + 1 < c_end ? __ldg(p.chunk_hub + c + 1) : -1;
-    const HubDesc hdn = hn == h || hn < 0 ? hd : p.hubs[hn];
-    int k0n = 0, nn = 0;
-    if (hn >= 0) unit_of(c + 1, hdn, k0n, nn);
-    const bool bad =  // lane 0's view, so that every lane keeps the same slot state
-        __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&r.abort), 0) != 0;
-    if (nn > 0 && !bad) {
-      if (lane == 0) issue(sl ^ 1, hdn.e0 + k0n, nn);
-      sst |= 4u << (sl ^ 1);
-    }
+    const int k0 = (int)(c - hd.c0) * kHubChunk + w * kHubUnit;  // this warp's unit
+    const int n = hd.deg - k0 < 0 ? 0 : (hd.deg - k0 < kHubUnit ? hd.deg - k0 : kHubUnit);
     const int64_t eb = hd.e0 + k0;
-    bool have = false;
-    if (n > 0 && (sst & (4u << sl))) {
-      have = __all_sync(0xffffffffu, wait_phase(&bar[sl], (sst >> sl) & 1u,
-                                                reinterpret_cast<volatile int*>(&r.abort),
-                                                p.status, 20));
-      if (have) sst = (sst ^ (1u << sl)) & ~(4u << sl);
-    }
+    // r = -(c + a mu) rounded once (one FMA): the high word of the exact pair
+    // that the candidates carry
     float rr[kHubU], mv[kHubU];
     float rmax = -CUDART_INF_F, mb = -CUDART_INF_F, s0 = 0.f;
-    const uint32_t sd = smem_u32(slot_base + sl * HS::kSlot) + 4u * (uint32_t)(eb & 3);
-    const uint32_t sa = smem_u32(slot_base + sl * HS::kSlot + HS::kDst) +
-                        (uint32_t)HS::kCaB * (uint32_t)(eb & (HS::kCaAlign - 1));
-    // edge k of the unit from the slot
-    auto staged = [&](int k, int& j, float& cv, float& av) {
-      j = lds_s32(sd + 4u * k);
-      if (BF16) {
-        const uint32_t u = lds_u32(sa + 4u * k);
-        cv = __uint_as_float(u << 16);
-        av = __uint_as_float(u & 0xffff0000u);
-      } else {
-        const float2 v = lds_f32x2(sa + 8u * k);
-        cv = v.x;
-        av = v.y;
-      }
-    };
-    const int nv = have ? n : 0;  // a unit whose copy did not land is skipped
     {
-      // r = -(c + a mu) rounded once (one FMA): the high word of the exact
-      // pair that the candidates carry
       int j[kHubU];
       float cv[kHubU], av[kHubU];
 #pragma unroll
@@ -1682,14 +1531,14 @@ __global__ void __launch_bounds__(kHubThreads, kHubCtasPerSm) hub_kernel(HubPara
         const int k = u * 32 + lane;
         j[u] = 0;
         cv[u] = av[u] = 0.f;
-        if (k < nv) staged(k, j[u], cv[u], av[u]);
+        if (k < n) gv.edge(eb + k, j[u], cv[u], av[u]);
       }
 #pragma unroll
       for (int u = 0; u < kHubU; ++u) mv[u] = __ldg(p.mu_r + j[u]);  // every gather in flight
 #pragma unroll
       for (int u = 0; u < kHubU; ++u) {
         const float rv = -__fmaf_rn(av[u], mv[u], cv[u]);
-        const bool in = u * 32 + lane < nv;
+        const bool in = u * 32 + lane < n;
         rr[u] = in ? rv : -CUDART_INF_F;
         if (in) {
           rmax = fmaxf(rmax, rv);
@@ -1737,7 +1586,7 @@ __global__ void __launch_bounds__(kHubThreads, kHubCtasPerSm) hub_kernel(HubPara
         const unsigned q = pos + __popc(bal[u] & ((1u << lane) - 1u));
         int j;
         float cv, av, hi, lo;
-        staged(k, j, cv, av);
+        gv.edge(eb + k, j, cv, av);
         score(cv, av, mv[u], hi, lo);
         const float al = edge_alpha<W>(cx, edge_w<W>(av));
         if (fits) p.cand[hd.cand0 + q] = make_float4(hi, lo, al, __int_as_float(k0 + k));
@@ -1753,10 +1602,10 @@ __global__ void __launch_bounds__(kHubThreads, kHubCtasPerSm) hub_kernel(HubPara
       su.mb = mb;
       p.stat[c * kHubWarps + w] = su;
     }
-    __syncwarp();  // every lane has read the slot before lane 0 refills it
     ++run;
     // the end of this CTA's run of the source: a ticket for its chunks; the
     // ticket that completes the source projects it
+    const int hn = c + 1 < c_end ? __ldg(p.chunk_hub + c + 1) : -1;
     if (hn != h) {
       __syncthreads();  // every warp's candidates and statistics of the run are written
       if (tid == 0) {
@@ -1769,29 +1618,10 @@ __global__ void __launch_bounds__(kHubThreads, kHubCtasPerSm) hub_kernel(HubPara
         hub_solve<BF16, W, WX>(p, h, hd, cx, r);
       }
       run = 0u;
-    }
-    h = hn;
-    hd = hdn;
-    k0 = k0n;
-    n = nn;
-  }
-  // every copy still in flight (after a wait gave up) lands before the CTA
-  // exits: bounded, and independent of the abort flag
-  if (lane == 0) {
-#pragma unroll
-    for (int sl = 0; sl < 2; ++sl) {
-      if (!(sst & (4u << sl))) continue;
-      const uint64_t w0 = globaltimer();
-      while (!mbar_try_wait(&bar[sl], (sst >> sl) & 1u)) {
-        if (globaltimer() - w0 > kWaitLimitNs) {
-          atomicOr(&p.status->err, kErrTimeout);
-          atomicCAS(&p.status->where, 0, 21);
-          break;
-        }
-      }
+      h = hn;
+      if (hn >= 0) hd = p.hubs[hn];
     }
   }
-  __syncwarp();
 }
 
 // ----------------------------------------------------------- the pass ----
@@ -2438,25 +2268,8 @@ static cudaError_t set_smem() {
                               (int)Layout<BF16>::kTotal);
 }
 
-// The hub kernel's staging: its dynamic shared memory, and the largest
-// carveout (two CTAs per SM share it).
-template <bool BF16, bool W, bool WX>
-static cudaError_t set_hub_smem() {
-  cudaError_t e = cudaFuncSetAttribute(hub_kernel<BF16, W, WX>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)HubStage<BF16>::kBytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(hub_kernel<BF16, W, WX>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  return e;
-}
-
 cudaError_t configure_pass_kernels() {
   const cudaError_t es[] = {
-      set_hub_smem<false, false, false>(), set_hub_smem<false, false, true>(),
-      set_hub_smem<false, true, false>(),  set_hub_smem<false, true, true>(),
-      set_hub_smem<true, false, false>(),  set_hub_smem<true, false, true>(),
-      set_hub_smem<true, true, false>(),   set_hub_smem<true, true, true>(),
       set_smem<false, false, false, false>(), set_smem<false, false, true, false>(),
       set_smem<false, true, false, false>(),  set_smem<false, true, true, false>(),
       set_smem<true, false, false, false>(),  set_smem<true, false, true, false>(),
@@ -2570,9 +2383,9 @@ static cudaError_t launch_hubs(const Problem& P, const float* gamma_dev, float g
   const int64_t g64 = P.nchunks < slots ? P.nchunks : slots;
   const dim3 grid((unsigned)(g64 > 0 ? g64 : 1)), block(kHubThreads);
   const bool bf16 = P.storage == DUALIP_EDGE_BF16;
-#define DUALIP_HUB(B, W)                                                                  \
-  (x_out ? launch_pdl(hub_kernel<B, W, true>, grid, block, HubStage<B>::kBytes, s, h) \
-         : launch_pdl(hub_kernel<B, W, false>, grid, block, HubStage<B>::kBytes, s, h))
+#define DUALIP_HUB(B, W) \
+  (x_out ? launch_pdl(hub_kernel<B, W, true>, grid, block, 0, s, h) \
+         : launch_pdl(hub_kernel<B, W, false>, grid, block, 0, s, h))
   if (bf16) return P.weighted ? DUALIP_HUB(true, true) : DUALIP_HUB(true, false);
   return P.weighted ? DUALIP_HUB(false, true) : DUALIP_HUB(false, false);
 #undef DUALIP_HUB
