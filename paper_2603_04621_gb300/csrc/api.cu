@@ -140,15 +140,9 @@ static cudaError_t sort_hub_edges(Problem& P, int64_t hub_edges, cudaStream_t s)
                              cudaMemcpyDeviceToHost, s)))
       return e;
   if ((e = cudaStreamSynchronize(s))) return e;
-  std::vector<uint32_t> perm((size_t)hub_edges), start((size_t)P.J + 1);
-  for (const HubDesc& hd : P.hub_host) {
-    const int32_t* d = dh.data() + hd.cand0;
-    uint32_t* pm = perm.data() + hd.cand0;
-    std::fill(start.begin(), start.end(), 0u);
-    for (int32_t k = 0; k < hd.deg; ++k) ++start[(size_t)d[k] + 1];  // ids were checked
-    for (int32_t j = 0; j < P.J; ++j) start[(size_t)j + 1] += start[j];
-    for (int32_t k = 0; k < hd.deg; ++k) pm[start[d[k]]++] = (uint32_t)k;
-  }
+  std::vector<uint32_t> perm((size_t)hub_edges), start;
+  for (const HubDesc& hd : P.hub_host)  // (the ids were range-checked at renumbering)
+    destination_order(dh.data() + hd.cand0, hd.deg, P.J, start, perm.data() + hd.cand0);
   int32_t* tdst = nullptr;
   char* tca = nullptr;
   if ((e = dev_alloc(P, &P.hub_perm, (size_t)hub_edges)) ||

@@ -221,6 +221,18 @@ inline void plan_hubs(const std::vector<int64_t>& tile_e, int64_t stage_e, int m
   }
 }
 
+// Destination order of a hub source's edges: a stable counting sort of its
+// renumbered ids d[0..n), each in [0, J).  perm[k] is the place in d of the
+// k-th edge in destination order (equal ids keep their order); start is
+// scratch, resized to J + 1.
+inline void destination_order(const int32_t* d, int32_t n, int32_t J,
+                              std::vector<uint32_t>& start, uint32_t* perm) {
+  start.assign((size_t)J + 1, 0u);
+  for (int32_t k = 0; k < n; ++k) ++start[(size_t)d[k] + 1];
+  for (int32_t j = 0; j < J; ++j) start[(size_t)j + 1] += start[(size_t)j];
+  for (int32_t k = 0; k < n; ++k) perm[start[(size_t)d[k]]++] = (uint32_t)k;
+}
+
 // Serving admission.  Resident footprint of a request (bytes): its edges
 // (4 bytes of dst plus the stored c and a), offsets (8 bytes and their 4-byte
 // low words), tiles and J-length arrays; the transient is the staging of host

@@ -86,6 +86,10 @@ int64_t plan_hubs_c(const int64_t* tile_e, int64_t nt, int64_t stage_e, int mb_s
   *big = b ? 1 : 0;
   return (int64_t)hubs.size();
 }
+void plan_destination_order(const int32_t* d, int32_t n, int32_t J, uint32_t* perm) {
+  std::vector<uint32_t> start;
+  dualip::destination_order(d, n, J, start, perm);
+}
 void plan_degree_order(const int64_t* off, int64_t I, int64_t* src_of, int64_t* off_st) {
   std::vector<int64_t> s, os;
   dualip::degree_order(std::vector<int64_t>(off, off + I + 1), s, os);
@@ -133,6 +137,9 @@ def plan(tmp_path_factory):
     L.plan_admission.argtypes = [i64, i64, i64, i64, ctypes.c_int]
     L.plan_admission.restype = ctypes.c_int
     L.plan_degree_order.argtypes = [p64, ctypes.c_int64, p64, p64]
+    L.plan_destination_order.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_void_p]
+    L.plan_destination_order.restype = None
     vp = ctypes.c_void_p
     L.plan_hubs_c.argtypes = [vp, i64, i64, ctypes.c_int, ctypes.c_int, i64, vp, vp, i64, vp,
                               i64, vp, vp]
@@ -363,3 +370,14 @@ def test_hub_sources_and_their_chunks(plan):
     mb, hubs, ch, big = hub_plan(plan, [0, 10, 3_000])
     assert len(hubs) == 0 and not big
 
+
+
+@pytest.mark.parametrize("n,J", [(0, 5), (1, 1), (1000, 7), (50_000, 1_000_000), (20_000, 300)])
+def test_destination_order_is_numpys_stable_argsort(plan, n, J):
+    """The hub sources' edge order: a stable sort of the renumbered ids, checked
+    against numpy's stable argsort, with repeated ids (small J) and sparse ones."""
+    rng = np.random.default_rng(n + J)
+    d = rng.integers(0, J, n).astype(np.int32)
+    perm = np.full(n, 0xFFFFFFFF, np.uint32)
+    plan.plan_destination_order(d.ctypes.data, n, J, perm.ctypes.data)
+    assert np.array_equal(perm.astype(np.int64), np.argsort(d, kind="stable"))
