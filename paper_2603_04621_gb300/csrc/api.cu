@@ -631,15 +631,8 @@ dualip_status dualip_create(const dualip_problem_desc* d, void* stream, dualip_p
   if (P.nhub > 0) {
     P.hub_host = hubs;
     P.hub_caller0.resize(hubs.size());
-    for (size_t k = 0; k < hubs.size(); ++k) {
-      int64_t g = hubs[k].e0;
-      if (seg) {  // the stored source whose segment starts at e0 (it is not empty)
-        const int64_t i = (int64_t)(std::upper_bound(off_s.begin(), off_s.end(), g) -
-                                    off_s.begin()) - 1;
-        g = off[src_of[i]];
-      }
-      P.hub_caller0[k] = g;
-    }
+    for (size_t k = 0; k < hubs.size(); ++k)
+      P.hub_caller0[k] = caller_segment_start(off_s, off, src_of, hubs[k].e0);
     if ((e = sort_hub_edges(P, hub_edges, s)))
       return bail(cuda_fail(e, "storing the hub sources in destination order"));
   }

@@ -221,6 +221,20 @@ inline void plan_hubs(const std::vector<int64_t>& tile_e, int64_t stage_e, int m
   }
 }
 
+// Where the segment of a non-empty stored source that starts at edge e0 starts
+// in the caller's edge order.  With degree order (src_of not empty) stored
+// source i is the caller's source src_of[i]; empty sources before it share
+// its offset, so the source is the last one whose offset is at most e0.
+inline int64_t caller_segment_start(const std::vector<int64_t>& off_stored,
+                                    const std::vector<int64_t>& off_caller,
+                                    const std::vector<int64_t>& src_of, int64_t e0) {
+  if (src_of.empty()) return e0;
+  const int64_t i =
+      (int64_t)(std::upper_bound(off_stored.begin(), off_stored.end(), e0) - off_stored.begin()) -
+      1;
+  return off_caller[(size_t)src_of[(size_t)i]];
+}
+
 // Destination order of a hub source's edges: a stable counting sort of its
 // renumbered ids d[0..n), each in [0, J).  perm[k] is the place in d of the
 // k-th edge in destination order (equal ids keep their order); start is

@@ -86,6 +86,12 @@ int64_t plan_hubs_c(const int64_t* tile_e, int64_t nt, int64_t stage_e, int mb_s
   *big = b ? 1 : 0;
   return (int64_t)hubs.size();
 }
+int64_t plan_caller_start(const int64_t* off_st, const int64_t* off, const int64_t* src_of,
+                          int64_t I, int64_t e0) {
+  std::vector<int64_t> s(src_of, src_of + I);
+  return dualip::caller_segment_start(std::vector<int64_t>(off_st, off_st + I + 1),
+                                      std::vector<int64_t>(off, off + I + 1), s, e0);
+}
 void plan_destination_order(const int32_t* d, int32_t n, int32_t J, uint32_t* perm) {
   std::vector<uint32_t> start;
   dualip::destination_order(d, n, J, start, perm);
@@ -140,6 +146,8 @@ def plan(tmp_path_factory):
     L.plan_destination_order.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_void_p]
     L.plan_destination_order.restype = None
+    L.plan_caller_start.argtypes = [p64, p64, p64, ctypes.c_int64, ctypes.c_int64]
+    L.plan_caller_start.restype = ctypes.c_int64
     vp = ctypes.c_void_p
     L.plan_hubs_c.argtypes = [vp, i64, i64, ctypes.c_int, ctypes.c_int, i64, vp, vp, i64, vp,
                               i64, vp, vp]
@@ -381,3 +389,21 @@ def test_destination_order_is_numpys_stable_argsort(plan, n, J):
     perm = np.full(n, 0xFFFFFFFF, np.uint32)
     plan.plan_destination_order(d.ctypes.data, n, J, perm.ctypes.data)
     assert np.array_equal(perm.astype(np.int64), np.argsort(d, kind="stable"))
+
+
+def test_caller_segment_start_skips_empty_sources(plan):
+    """A hub's segment in the caller's order, for sources stored in degree order:
+    every non-empty stored source maps to its caller's offset, also where empty
+    sources share its stored offset (they sort first)."""
+    rng = np.random.default_rng(8)
+    deg = rng.integers(0, 60, 3_000)
+    deg[rng.integers(0, 3_000, 400)] = 0
+    deg[[5, 700, 2_999]] = [90_000, 60_000, 75_000]
+    off = offsets(deg)
+    I = len(deg)
+    src, off_st = np.empty(I, np.int64), np.empty(I + 1, np.int64)
+    plan.plan_degree_order(_p(off), I, _p(src), _p(off_st))
+    for i in range(I):
+        if off_st[i + 1] > off_st[i]:
+            assert plan.plan_caller_start(_p(off_st), _p(off), _p(src), I,
+                                          int(off_st[i])) == off[src[i]]
